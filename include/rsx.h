@@ -1,0 +1,178 @@
+/*
+ * rsx.h -- C ABI of the GB300 P-RSoXS forward model (libprsoxs_gb300.so).
+ *
+ * The library simulates polarized resonant soft X-ray scattering from a
+ * voxel morphology: per-voxel uniaxial dielectric tensors, the induced
+ * polarisation p, its 3-D FFT, the far-field scatter projected on the Ewald
+ * sphere, and the average of the detector image over rotations of the
+ * beam's electric field, for a list of photon energies (Sec. 3.3 and
+ * Algorithm 1 of the paper; Algorithm 2 for the memory-minimising form).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Return value: RSX_OK (0) on success, a negative RSX_ERR_* code
+ *    otherwise.  rsx_last_error() then returns a message for the failing
+ *    call on this host thread.  A failing call writes none of its outputs.
+ *  - Real: float when the context was created with precision 32, double with
+ *    precision 64 (the paper's float4 / double4 builds, Sec. 4.1).  Complex
+ *    values are (re, im) pairs of Real.
+ *  - Grid: N = nx * ny * nz voxels, x fastest, then y, then z.
+ *  - Device pointers are CUDA device addresses on the current device, host
+ *    pointers are ordinary (pageable or pinned) host memory.  The caller owns
+ *    every buffer it passes; the library owns only what the context holds.
+ *  - stream: a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Work is enqueued on it in order; an entry point that writes
+ *    host memory synchronises the stream before it returns.
+ *  - Detector images are [ny][nx] Real in fftshift order: the pixel (iy, ix)
+ *    holds q = (2 pi (ix - nx/2) / (nx D), 2 pi (iy - ny/2) / (ny D)), with D
+ *    the voxel edge in nm and integer division.
+ *  - Supported sizes: nx and ny powers of two in [1, 4096], nz in [1, 65535],
+ *    1 <= n_components <= RSX_MAX_COMPONENTS.
+ */
+#ifndef RSX_H
+#define RSX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RSX_OK 0
+#define RSX_ERR_INVALID -1     /* bad argument, size, layout or value      */
+#define RSX_ERR_OOM -2         /* a device allocation failed                */
+#define RSX_ERR_CUDA -3        /* a CUDA call or kernel launch failed       */
+#define RSX_ERR_UNSUPPORTED -4 /* valid, but not built (e.g. size/precision) */
+#define RSX_ERR_STATE -5       /* morphology or optical constants not set   */
+
+#define RSX_HOST 0
+#define RSX_DEVICE 1
+
+#define RSX_MAX_COMPONENTS 32
+
+/* Frame in which p <- U^T p is applied (Sec. 3.3, Algorithm 1).
+ * RSX_FRAME_LITERAL: U^T rotates the components of p while the grid and the
+ *   unit vector r of Eq. (3Dscatter) stay in the material frame.
+ * RSX_FRAME_LAB: U^T is left out (|U^T v| = |v|), which is the same as
+ *   rotating r with p; the two differ at O((q/k)^2). */
+#define RSX_FRAME_LITERAL 0
+#define RSX_FRAME_LAB 1
+
+typedef struct rsx_config {
+  int nx, ny, nz;     /* voxel grid                                         */
+  int n_components;   /* c, the number of materials (Sec. 3.1)              */
+  double voxel_nm;    /* voxel edge D in nm (voxels are cubes, Sec. 3.1)    */
+  int precision;      /* 32 (float) or 64 (double)                          */
+  int algorithm;      /* 1: communication-minimising (Algorithm 1)          */
+                      /* 2: memory-minimising via N_t (Algorithms 2 and 3)  */
+  int frame;          /* RSX_FRAME_LITERAL or RSX_FRAME_LAB                 */
+  int validate;       /* nonzero: rsx_set_morphology rejects v or s outside */
+                      /* [0, 1] and non-finite angles (Sec. 3.1); the sum   */
+                      /* of v over components is never checked.             */
+} rsx_config;
+
+typedef struct rsx_context rsx_context;
+
+/* Create a context for one grid and material count.  Allocates the device
+ * workspace: 3 N complex for p, two nx*ny Real images, FFT twiddle tables
+ * and, for Algorithm 2, 6 N complex for N_t (Table 2).  *out receives the
+ * handle.  Errors: RSX_ERR_INVALID (sizes, precision, algorithm),
+ * RSX_ERR_OOM. */
+int rsx_create(const rsx_config* cfg, rsx_context** out);
+
+/* Free the context and all device memory it owns.  NULL is a no-op.  The
+ * caller must make sure no work of this context is still running. */
+int rsx_destroy(rsx_context* ctx);
+
+/* Message for the last failing call on this host thread ("" if none).  The
+ * string stays valid until the next rsx_* call on this thread. */
+const char* rsx_last_error(void);
+
+/* Device bytes rsx_create would allocate for cfg, morphology copy included
+ * (Tables 1 and 2).  Returns 0 for an invalid cfg. */
+size_t rsx_workspace_bytes(const rsx_config* cfg);
+
+/* Number of e-field angles in the inclusive list start:increment:end
+ * (degrees, Algorithm 1 "E_Angle [start, increment, end]"); 1 when rotation
+ * is 0.  Returns -1 for increment <= 0, end < start or non-finite input. */
+int rsx_angle_count(double start_deg, double increment_deg, double end_deg, int rotation);
+
+/* Morphology M (Sec. 4.1, Fig. 3): [c][nz][ny][nx] entries of 4 Real
+ * (v_frac, s, phi, theta), component-major; phi and theta in radians.
+ * where = RSX_HOST: copied into the context (one copy, Algorithm 1).
+ * where = RSX_DEVICE: borrowed, not copied; the pointer must stay valid and
+ *   unchanged until the last run that uses it has finished, and must be
+ *   aligned to 4 * sizeof(Real).
+ * With validate set, a value outside the ranges of Sec. 3.1 returns
+ * RSX_ERR_INVALID and leaves the previous morphology in place. */
+int rsx_set_morphology(rsx_context* ctx, const void* M, int where, void* stream);
+
+/* Optical constants (Sec. 3.2): energies_ev[n_energies] (> 0) and
+ * constants[n_energies][c][4] = (delta_par, beta_par, delta_perp, beta_perp),
+ * host memory, double.  n = 1 - delta + i beta along and across the
+ * extraordinary axis.  Copied. */
+int rsx_set_optical_constants(rsx_context* ctx, int n_energies, const double* energies_ev,
+                              const double* constants);
+
+/* The simulation (Algorithm 1, or Algorithm 2 when the context was made
+ * with algorithm 2): for each selected energy, the detector image averaged
+ * over the e-field angles start:increment:end (degrees; a single angle 0
+ * and no image rotation when rotation is 0).
+ * energy_idx[n_sel] selects energies by index (NULL: all, in order; this is
+ * the sharding hook: disjoint subsets give the matching rows bit for bit).
+ * out: [n_sel][ny][nx] Real, in host or device memory per `where`. */
+int rsx_run(rsx_context* ctx, double start_deg, double increment_deg, double end_deg,
+            int rotation, const int* energy_idx, int n_sel, void* out, int where,
+            void* stream);
+
+/* ---- per-phase device timers (the Polarization, FFT, Scatter3DEwalds and
+ * Rotation timers of the breakdowns in Sec. 6) -------------------------- */
+#define RSX_PHASE_POL_FFTX 0 /* polarisation fused with the x-FFT           */
+#define RSX_PHASE_FFTY 1     /* y-FFT                                         */
+#define RSX_PHASE_EWALD 2    /* pruned q_z transform + scatter + Ewald        */
+#define RSX_PHASE_ROTATE 3   /* detector rotation and accumulation            */
+#define RSX_PHASE_OTHER 4    /* geometry, averaging, validation, z/x FFTs     */
+#define RSX_N_PHASES 5
+
+/* enable != 0: every kernel the context launches from now on is bracketed by
+ * two CUDA events on its stream (a few microseconds each); 0 stops that. */
+int rsx_set_timing(rsx_context* ctx, int enable);
+
+/* Waits for the recorded events, writes the summed device time of each
+ * phase in ms to ms[RSX_N_PHASES] and the number of kernel launches to
+ * launches[RSX_N_PHASES] (either may be NULL), then clears the record. */
+int rsx_phase_times(rsx_context* ctx, double* ms, long long* launches);
+
+/* ---- single steps of the path (device buffers), for checking each row -- */
+
+/* Eqs. (ncorr), (nrot), (polarization) and p <- U^T p for one energy and
+ * e-field angle alpha (radians): p_out [3][nz][ny][nx] complex. */
+int rsx_polarization(rsx_context* ctx, int energy_index, double alpha_rad, void* p_out,
+                     void* stream);
+
+/* Forward, unnormalised 3-D DFT (sign exp(-i ...)) of each of the three
+ * complex fields in p [3][nz][ny][nx], in place. */
+int rsx_fft3d(rsx_context* ctx, void* p, void* stream);
+
+/* Eqs. (3Dscatter) and (Ewald) from a full p~ [3][nz][ny][nx] complex (FFT
+ * order): detector image img_out [ny][nx] Real, fftshift order, q_z
+ * interpolated linearly between the two bracketing bins. */
+int rsx_ewald(rsx_context* ctx, int energy_index, const void* p_tilde, void* img_out,
+              void* stream);
+
+/* Detector rotation (Sec. 4, Algorithm 1): acc[iy][ix] += img sampled at
+ * U(alpha) Q with bilinear weights, zero outside the grid. */
+int rsx_rotate_accumulate(rsx_context* ctx, const void* img, double alpha_rad, void* acc,
+                          void* stream);
+
+/* One pass of the hot path for one energy and angle: morphology to the
+ * unrotated detector image img_out [ny][nx] Real (fftshift order), through
+ * the fused polarisation + FFT kernels and the pruned q_z transform. */
+int rsx_scatter_angle(rsx_context* ctx, int energy_index, double alpha_rad, void* img_out,
+                      void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RSX_H */

@@ -1,0 +1,608 @@
+// C ABI of the GB300 P-RSoXS path (include/rsx.h): context lifetime,
+// argument checks and the host-side loops of Algorithm 1 (energies outer,
+// e-field angles inner), enqueuing the kernels of rsx_kernels.cu.
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rsx.h"
+#include "rsx_kernels.h"
+
+using rsx::Geo;
+using rsx::PolParams;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    return fail(RSX_ERR_OOM, "%s: out of device memory", what);
+  return fail(RSX_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define RSX_CK(call, what)                      \
+  do {                                          \
+    cudaError_t e_ = (call);                    \
+    if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+  } while (0)
+
+bool is_pow2(long long n) { return n >= 1 && (n & (n - 1)) == 0; }
+
+const double kPi = 3.14159265358979323846264338327950288;
+const double kHcEvNm = 1239.84198;  // lambda = hc / E
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+int check_config(const rsx_config* c) {
+  if (!c) return fail(RSX_ERR_INVALID, "config is NULL");
+  if (!is_pow2(c->nx) || c->nx > 4096 || !is_pow2(c->ny) || c->ny > 4096)
+    return fail(RSX_ERR_INVALID, "nx=%d, ny=%d: each must be a power of two in [1, 4096]", c->nx,
+                c->ny);
+  if (c->nz < 1 || c->nz > 65535) return fail(RSX_ERR_INVALID, "nz=%d outside [1, 65535]", c->nz);
+  if (c->n_components < 1 || c->n_components > RSX_MAX_COMPONENTS)
+    return fail(RSX_ERR_INVALID, "n_components=%d outside [1, %d]", c->n_components,
+                RSX_MAX_COMPONENTS);
+  if (!(c->voxel_nm > 0.0) || !isfinite(c->voxel_nm))
+    return fail(RSX_ERR_INVALID, "voxel_nm must be positive and finite");
+  if (c->precision != 32 && c->precision != 64)
+    return fail(RSX_ERR_INVALID, "precision=%d: must be 32 or 64", c->precision);
+  if (c->algorithm != 1 && c->algorithm != 2)
+    return fail(RSX_ERR_INVALID, "algorithm=%d: must be 1 or 2", c->algorithm);
+  if (c->frame != RSX_FRAME_LITERAL && c->frame != RSX_FRAME_LAB)
+    return fail(RSX_ERR_INVALID, "frame=%d: must be RSX_FRAME_LITERAL or RSX_FRAME_LAB", c->frame);
+  if (c->algorithm == 2) return fail(RSX_ERR_UNSUPPORTED, "algorithm 2 is not built yet");
+  return RSX_OK;
+}
+
+size_t complex_size(int precision) { return precision == 32 ? 8 : 16; }
+size_t real_size(int precision) { return precision == 32 ? 4 : 8; }
+size_t geo_size(int precision) {
+  return precision == 32 ? sizeof(Geo<float>) : sizeof(Geo<double>);
+}
+
+}  // namespace
+
+struct rsx_context {
+  rsx_config cfg{};
+  int dev = 0;
+  long long N = 0, npix = 0;
+  void* M_owned = nullptr;  // device copy of a host morphology
+  const void* M = nullptr;  // morphology in use (owned or borrowed)
+  std::vector<double> energies, constants;
+  void* p = nullptr;    // 3 N complex workspace
+  void* img = nullptr;  // one detector image
+  void* acc = nullptr;  // running sum of rotated images
+  void* geo = nullptr;  // per-pixel Ewald geometry of energy geo_energy
+  int geo_energy = -1;
+  void* twx = nullptr;
+  void* twy = nullptr;
+  void* twz = nullptr;
+  int* flag = nullptr;
+  // per-phase timing: event pairs recorded around launches while enabled
+  bool timing = false;
+  struct Rec {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+};
+
+namespace {
+
+void free_all(rsx_context* c) {
+  void* ptrs[] = {c->M_owned, c->p, c->img, c->acc, c->geo, c->twx, c->twy, c->twz, c->flag};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (auto& r : c->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
+  c->recs.clear();
+  c->pool.clear();
+}
+
+cudaEvent_t take_event(rsx_context* c) {
+  if (!c->pool.empty()) {
+    cudaEvent_t e = c->pool.back();
+    c->pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one kernel launch with events when timing is on.
+struct PhaseTimer {
+  rsx_context* c;
+  cudaStream_t s;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(rsx_context* c_, int phase_, cudaStream_t s_) : c(c_), s(s_), phase(phase_) {
+    if (c->timing && (a = take_event(c))) cudaEventRecord(a, s);
+  }
+  ~PhaseTimer() {
+    if (!a) return;
+    cudaEvent_t b = take_event(c);
+    if (!b) {
+      c->pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    c->recs.push_back({phase, a, b});
+  }
+};
+
+// exp(-2 pi i t / n), t < n, in the context precision.
+int upload_twiddles(rsx_context* c, int n, void** dst) {
+  const int prec = c->cfg.precision;
+  std::vector<double> tw(2 * (size_t)n);
+  for (int t = 0; t < n; ++t) {
+    const double a = -2.0 * kPi * (double)t / (double)n;
+    tw[2 * t] = cos(a);
+    tw[2 * t + 1] = sin(a);
+  }
+  RSX_CK(cudaMalloc(dst, complex_size(prec) * n), "twiddle table");
+  if (prec == 64) {
+    RSX_CK(cudaMemcpy(*dst, tw.data(), 16 * (size_t)n, cudaMemcpyHostToDevice), "twiddle upload");
+  } else {
+    std::vector<float> f(tw.begin(), tw.end());
+    RSX_CK(cudaMemcpy(*dst, f.data(), 8 * (size_t)n, cudaMemcpyHostToDevice), "twiddle upload");
+  }
+  return RSX_OK;
+}
+
+template <typename R>
+PolParams<R> make_params(const rsx_context* c, int ie, double alpha, int add_ref) {
+  PolParams<R> pp;
+  memset(&pp, 0, sizeof(pp));
+  const int nc = c->cfg.n_components;
+  const double* k = c->constants.data() + (size_t)ie * nc * 4;
+  for (int j = 0; j < nc; ++j) {
+    // eps = n - 1 = -delta + i beta (Sec. 3.2)
+    const double epr = -k[4 * j], epi = k[4 * j + 1];
+    const double eqr = -k[4 * j + 2], eqi = k[4 * j + 3];
+    const double tr = (epr + 2.0 * eqr) / 3.0, ti = (epi + 2.0 * eqi) / 3.0;
+    pp.tau[j][0] = (R)tr;
+    pp.tau[j][1] = (R)ti;
+    pp.dperp[j][0] = (R)(eqr - tr);
+    pp.dperp[j][1] = (R)(eqi - ti);
+    pp.dpar[j][0] = (R)(epr - eqr);
+    pp.dpar[j][1] = (R)(epi - eqi);
+  }
+  pp.ce = (R)cos(alpha);
+  pp.se = (R)sin(alpha);
+  pp.c = nc;
+  pp.literal = c->cfg.frame == RSX_FRAME_LITERAL;
+  pp.add_ref = add_ref;
+  return pp;
+}
+
+double wavenumber(double E) { return 2.0 * kPi / (kHcEvNm / E); }
+
+template <typename R>
+int ensure_geo(rsx_context* c, int ie, cudaStream_t s) {
+  if (c->geo_energy == ie) return RSX_OK;
+  PhaseTimer pt(c, RSX_PHASE_OTHER, s);
+  RSX_CK(rsx::launch_geometry<R>((Geo<R>*)c->geo, c->cfg.nx, c->cfg.ny, c->cfg.nz,
+                                 c->cfg.voxel_nm, wavenumber(c->energies[ie]), s),
+         "geometry kernel");
+  c->geo_energy = ie;
+  return RSX_OK;
+}
+
+template <typename R>
+int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  int rc = ensure_geo<R>(c, ie, s);
+  if (rc) return rc;
+  const PolParams<R> pp = make_params<R>(c, ie, alpha, 0);
+  {
+    PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
+    RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+           "polarisation + x-FFT kernel");
+  }
+  if (g.ny > 1) {
+    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+    RSX_CK(rsx::launch_col_fft<R>(c->p, g.ny, g.nx, g.nx, 3LL * g.nz, (long long)g.nx * g.ny,
+                                  c->twy, s),
+           "y-FFT kernel");
+  }
+  // The constant -(c-1) e' / (4 pi) left out of p before the FFT returns at
+  // q = 0 as N times itself (e' = x-hat in the literal frame, e otherwise).
+  const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
+  R dc[3];
+  if (g.frame == RSX_FRAME_LITERAL) {
+    dc[0] = (R)ref; dc[1] = (R)0; dc[2] = (R)0;
+  } else {
+    dc[0] = (R)(ref * cos(alpha)); dc[1] = (R)(ref * sin(alpha)); dc[2] = (R)0;
+  }
+  PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+  RSX_CK(rsx::launch_ewald<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, true, dc, img,
+                              s),
+         "Ewald kernel");
+  return RSX_OK;
+}
+
+int check_ready(const rsx_context* c) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (!c->M) return fail(RSX_ERR_STATE, "morphology not set");
+  if (c->energies.empty()) return fail(RSX_ERR_STATE, "optical constants not set");
+  return RSX_OK;
+}
+
+int check_energy(const rsx_context* c, int ie) {
+  if (ie < 0 || ie >= (int)c->energies.size())
+    return fail(RSX_ERR_INVALID, "energy index %d outside [0, %d)", ie, (int)c->energies.size());
+  return RSX_OK;
+}
+
+bool host_morphology_ok(const void* M, int prec, long long n) {
+  for (long long i = 0; i < n; ++i) {
+    double v, s, ph, th;
+    if (prec == 32) {
+      const float* f = (const float*)M + 4 * i;
+      v = f[0]; s = f[1]; ph = f[2]; th = f[3];
+    } else {
+      const double* d = (const double*)M + 4 * i;
+      v = d[0]; s = d[1]; ph = d[2]; th = d[3];
+    }
+    if (!(v >= 0.0 && v <= 1.0 && s >= 0.0 && s <= 1.0 && isfinite(ph) && isfinite(th)))
+      return false;
+  }
+  return true;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+// Every function below is declared extern "C" in rsx.h and keeps that linkage.
+
+const char* rsx_last_error(void) { return g_err.c_str(); }
+
+size_t rsx_workspace_bytes(const rsx_config* cfg) {
+  if (check_config(cfg) != RSX_OK) return 0;
+  const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  const long long npix = (long long)cfg->nx * cfg->ny;
+  const size_t R = real_size(cfg->precision), Cs = complex_size(cfg->precision);
+  size_t b = (size_t)cfg->n_components * N * 4 * R;  // morphology copy (Table 1: 4c N)
+  b += 3 * (size_t)N * Cs;                           // p_x, p_y, p_z (Table 1: 6 N)
+  b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
+  b += (size_t)npix * geo_size(cfg->precision);
+  b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
+  return b;
+}
+
+int rsx_angle_count(double start, double inc, double end, int rotation) {
+  if (!rotation) return 1;
+  if (!isfinite(start) || !isfinite(inc) || !isfinite(end) || !(inc > 0.0) || end < start)
+    return -1;
+  const double n = floor((end - start) / inc + 1e-6) + 1.0;
+  if (n > 1e7) return -1;
+  return (int)n;
+}
+
+int rsx_create(const rsx_config* cfg, rsx_context** out) {
+  if (!out) return fail(RSX_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  int rc = check_config(cfg);
+  if (rc) return rc;
+  rsx_context* c = new rsx_context();
+  c->cfg = *cfg;
+  c->N = (long long)cfg->nx * cfg->ny * cfg->nz;
+  c->npix = (long long)cfg->nx * cfg->ny;
+  cudaError_t e = cudaGetDevice(&c->dev);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaGetDevice");
+  }
+  const size_t R = real_size(cfg->precision), Cs = complex_size(cfg->precision);
+  struct {
+    void** dst;
+    size_t bytes;
+    const char* what;
+  } allocs[] = {
+      {&c->p, 3 * (size_t)c->N * Cs, "p workspace"},
+      {&c->img, (size_t)c->npix * R, "Ewald image"},
+      {&c->acc, (size_t)c->npix * R, "Ewald average"},
+      {&c->geo, (size_t)c->npix * geo_size(cfg->precision), "Ewald geometry"},
+      {(void**)&c->flag, sizeof(int), "validation flag"},
+  };
+  for (auto& a : allocs) {
+    e = cudaMalloc(a.dst, a.bytes);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, a.what);
+      free_all(c);
+      delete c;
+      return rc;
+    }
+  }
+  if ((rc = upload_twiddles(c, cfg->nx, &c->twx)) || (rc = upload_twiddles(c, cfg->ny, &c->twy)) ||
+      (rc = upload_twiddles(c, cfg->nz, &c->twz))) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return RSX_OK;
+}
+
+int rsx_destroy(rsx_context* c) {
+  if (!c) return RSX_OK;
+  DeviceGuard dg(c->dev);
+  free_all(c);
+  delete c;
+  return RSX_OK;
+}
+
+int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (!M) return fail(RSX_ERR_INVALID, "morphology pointer is NULL");
+  if (where != RSX_HOST && where != RSX_DEVICE)
+    return fail(RSX_ERR_INVALID, "where=%d: must be RSX_HOST or RSX_DEVICE", where);
+  DeviceGuard dg(c->dev);
+  if (!dg.ok) return fail(RSX_ERR_CUDA, "cannot select the context's device");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int prec = c->cfg.precision;
+  const long long n_entries = (long long)c->cfg.n_components * c->N;
+  const size_t bytes = (size_t)n_entries * 4 * real_size(prec);
+  if (where == RSX_HOST) {
+    if (c->cfg.validate && !host_morphology_ok(M, prec, n_entries))
+      return fail(RSX_ERR_INVALID, "morphology value outside 0<=v<=1, 0<=s<=1 or non-finite angle");
+    if (!c->M_owned) RSX_CK(cudaMalloc(&c->M_owned, bytes), "morphology copy");
+    RSX_CK(cudaMemcpyAsync(c->M_owned, M, bytes, cudaMemcpyHostToDevice, s), "morphology upload");
+    RSX_CK(cudaStreamSynchronize(s), "morphology upload");
+    c->M = c->M_owned;
+    return RSX_OK;
+  }
+  if (((uintptr_t)M) % (4 * real_size(prec)) != 0)
+    return fail(RSX_ERR_INVALID, "device morphology must be aligned to %d bytes",
+                (int)(4 * real_size(prec)));
+  if (c->cfg.validate) {
+    int h = 0;
+    RSX_CK(cudaMemsetAsync(c->flag, 0, sizeof(int), s), "validation");
+    RSX_CK(prec == 32 ? rsx::launch_validate<float>(M, n_entries, c->flag, s)
+                      : rsx::launch_validate<double>(M, n_entries, c->flag, s),
+           "validation kernel");
+    RSX_CK(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "validation");
+    RSX_CK(cudaStreamSynchronize(s), "validation");
+    if (h) return fail(RSX_ERR_INVALID, "morphology value outside 0<=v<=1, 0<=s<=1 or non-finite angle");
+  }
+  c->M = M;
+  return RSX_OK;
+}
+
+int rsx_set_optical_constants(rsx_context* c, int n, const double* E, const double* k) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (n < 1 || !E || !k) return fail(RSX_ERR_INVALID, "need n_energies >= 1 and non-NULL arrays");
+  const int nc = c->cfg.n_components;
+  for (int i = 0; i < n; ++i)
+    if (!(E[i] > 0.0) || !isfinite(E[i])) return fail(RSX_ERR_INVALID, "energy %d not positive", i);
+  for (long long i = 0; i < (long long)n * nc * 4; ++i)
+    if (!isfinite(k[i])) return fail(RSX_ERR_INVALID, "optical constant %lld not finite", i);
+  c->energies.assign(E, E + n);
+  c->constants.assign(k, k + (size_t)n * nc * 4);
+  c->geo_energy = -1;
+  return RSX_OK;
+}
+
+int rsx_polarization(rsx_context* c, int ie, double alpha, void* p_out, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_energy(c, ie))) return rc;
+  if (!p_out) return fail(RSX_ERR_INVALID, "p_out is NULL");
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const rsx_config& g = c->cfg;
+  if (g.precision == 32) {
+    RSX_CK(rsx::launch_pol_fftx<float>(c->M, g.nx, g.ny, g.nz, make_params<float>(c, ie, alpha, 1),
+                                       false, p_out, nullptr, s),
+           "polarisation kernel");
+  } else {
+    RSX_CK(rsx::launch_pol_fftx<double>(c->M, g.nx, g.ny, g.nz,
+                                        make_params<double>(c, ie, alpha, 1), false, p_out, nullptr,
+                                        s),
+           "polarisation kernel");
+  }
+  return RSX_OK;
+}
+
+namespace {
+template <typename R>
+int fft3d_impl(rsx_context* c, void* p, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  RSX_CK(rsx::launch_row_fft<R>(p, g.nx, 3LL * g.ny * g.nz, c->twx, s), "x-FFT kernel");
+  RSX_CK(rsx::launch_col_fft<R>(p, g.ny, g.nx, g.nx, 3LL * g.nz, (long long)g.nx * g.ny, c->twy, s),
+         "y-FFT kernel");
+  if (g.nz == 1) return RSX_OK;
+  if (is_pow2(g.nz) && g.nz <= 4096) {
+    RSX_CK(rsx::launch_col_fft<R>(p, g.nz, c->npix, c->npix, 3, c->N, c->twz, s), "z-FFT kernel");
+  } else {
+    RSX_CK(rsx::launch_dft_z<R>(p, c->p, g.nx, g.ny, g.nz, c->twz, s), "z-DFT kernel");
+    RSX_CK(cudaMemcpyAsync(p, c->p, 3 * (size_t)c->N * sizeof(R) * 2, cudaMemcpyDeviceToDevice, s),
+           "z-DFT copy");
+  }
+  return RSX_OK;
+}
+}  // namespace
+
+int rsx_fft3d(rsx_context* c, void* p, void* stream) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (!p) return fail(RSX_ERR_INVALID, "p is NULL");
+  if (p == c->p) return fail(RSX_ERR_INVALID, "p must be a caller buffer");
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  return c->cfg.precision == 32 ? fft3d_impl<float>(c, p, s) : fft3d_impl<double>(c, p, s);
+}
+
+int rsx_ewald(rsx_context* c, int ie, const void* pt, void* img, void* stream) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (c->energies.empty()) return fail(RSX_ERR_STATE, "optical constants not set");
+  int rc = check_energy(c, ie);
+  if (rc) return rc;
+  if (!pt || !img) return fail(RSX_ERR_INVALID, "NULL buffer");
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const rsx_config& g = c->cfg;
+  if (g.precision == 32) {
+    if ((rc = ensure_geo<float>(c, ie, s))) return rc;
+    const float dc[3] = {0, 0, 0};
+    RSX_CK(rsx::launch_ewald<float>(pt, g.nx, g.ny, g.nz, (const Geo<float>*)c->geo, c->twz, false,
+                                    dc, img, s),
+           "Ewald kernel");
+  } else {
+    if ((rc = ensure_geo<double>(c, ie, s))) return rc;
+    const double dc[3] = {0, 0, 0};
+    RSX_CK(rsx::launch_ewald<double>(pt, g.nx, g.ny, g.nz, (const Geo<double>*)c->geo, c->twz,
+                                     false, dc, img, s),
+           "Ewald kernel");
+  }
+  return RSX_OK;
+}
+
+int rsx_rotate_accumulate(rsx_context* c, const void* img, double alpha, void* acc, void* stream) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (!img || !acc) return fail(RSX_ERR_INVALID, "NULL buffer");
+  if (!isfinite(alpha)) return fail(RSX_ERR_INVALID, "alpha not finite");
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const rsx_config& g = c->cfg;
+  RSX_CK(g.precision == 32 ? rsx::launch_rotate_acc<float>(img, acc, g.nx, g.ny, alpha, true, s)
+                           : rsx::launch_rotate_acc<double>(img, acc, g.nx, g.ny, alpha, true, s),
+         "rotation kernel");
+  return RSX_OK;
+}
+
+int rsx_scatter_angle(rsx_context* c, int ie, double alpha, void* img, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_energy(c, ie))) return rc;
+  if (!img) return fail(RSX_ERR_INVALID, "img_out is NULL");
+  if (!isfinite(alpha)) return fail(RSX_ERR_INVALID, "alpha not finite");
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  return c->cfg.precision == 32 ? scatter_angle<float>(c, ie, alpha, img, s)
+                                : scatter_angle<double>(c, ie, alpha, img, s);
+}
+
+namespace {
+template <typename R>
+int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
+             const std::vector<int>& sel, void* out, int where, cudaStream_t s) {
+  const size_t img_bytes = (size_t)c->npix * sizeof(R);
+  for (size_t o = 0; o < sel.size(); ++o) {
+    const int ie = sel[o];
+    RSX_CK(cudaMemsetAsync(c->acc, 0, img_bytes, s), "clear average");
+    for (int a = 0; a < nang; ++a) {
+      const double alpha = rotation ? (start + inc * a) * (kPi / 180.0) : 0.0;
+      int rc = scatter_angle<R>(c, ie, alpha, c->img, s);
+      if (rc) return rc;
+      PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
+      RSX_CK(rsx::launch_rotate_acc<R>(c->img, c->acc, c->cfg.nx, c->cfg.ny, alpha, rotation != 0,
+                                       s),
+             "rotation kernel");
+    }
+    const double inv = 1.0 / nang;  // Ewald_Avg[i] / numRotation (Algorithm 1)
+    PhaseTimer pt(c, RSX_PHASE_OTHER, s);
+    if (where == RSX_DEVICE) {
+      RSX_CK(rsx::launch_scale<R>(c->acc, (char*)out + o * img_bytes, c->npix, inv, s),
+             "average kernel");
+    } else {
+      RSX_CK(rsx::launch_scale<R>(c->acc, c->acc, c->npix, inv, s), "average kernel");
+      RSX_CK(cudaMemcpyAsync((char*)out + o * img_bytes, c->acc, img_bytes, cudaMemcpyDeviceToHost,
+                             s),
+             "result download");
+    }
+  }
+  if (where == RSX_HOST) RSX_CK(cudaStreamSynchronize(s), "result download");
+  return RSX_OK;
+}
+}  // namespace
+
+int rsx_set_timing(rsx_context* c, int enable) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  c->timing = enable != 0;
+  return RSX_OK;
+}
+
+int rsx_phase_times(rsx_context* c, double* ms, long long* launches) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  DeviceGuard dg(c->dev);
+  double t[RSX_N_PHASES] = {0};
+  long long n[RSX_N_PHASES] = {0};
+  cudaError_t err = cudaSuccess;
+  for (auto& r : c->recs) {
+    float x = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&x, r.a, r.b);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    t[r.phase] += x;
+    n[r.phase] += 1;
+    c->pool.push_back(r.a);
+    c->pool.push_back(r.b);
+  }
+  c->recs.clear();
+  if (err != cudaSuccess) return cuda_fail(err, "phase timers");
+  for (int i = 0; i < RSX_N_PHASES; ++i) {
+    if (ms) ms[i] = t[i];
+    if (launches) launches[i] = n[i];
+  }
+  return RSX_OK;
+}
+
+int rsx_run(rsx_context* c, double start, double inc, double end, int rotation,
+            const int* energy_idx, int n_sel, void* out, int where, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if (!out) return fail(RSX_ERR_INVALID, "out is NULL");
+  if (where != RSX_HOST && where != RSX_DEVICE)
+    return fail(RSX_ERR_INVALID, "where=%d: must be RSX_HOST or RSX_DEVICE", where);
+  const int nang = rsx_angle_count(start, inc, end, rotation);
+  if (nang < 1) return fail(RSX_ERR_INVALID, "angle list [%g, %g, %g] is empty or invalid", start, inc, end);
+  std::vector<int> sel;
+  if (energy_idx) {
+    if (n_sel < 0) return fail(RSX_ERR_INVALID, "n_sel < 0");
+    for (int i = 0; i < n_sel; ++i) {
+      if ((rc = check_energy(c, energy_idx[i]))) return rc;
+      sel.push_back(energy_idx[i]);
+    }
+  } else {
+    for (int i = 0; i < (int)c->energies.size(); ++i) sel.push_back(i);
+  }
+  if (sel.empty()) return RSX_OK;
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  return c->cfg.precision == 32 ? run_impl<float>(c, start, inc, nang, rotation, sel, out, where, s)
+                                : run_impl<double>(c, start, inc, nang, rotation, sel, out, where, s);
+}
+

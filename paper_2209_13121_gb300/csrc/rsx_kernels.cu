@@ -1,0 +1,603 @@
+// CUDA kernels of the GB300 P-RSoXS path (sm_103a).
+//
+// Per energy and e-field angle the hot path runs four kernels:
+//   k_pol_fftx   Eqs. (ncorr), (nrot), (polarization) and p <- U^T p for a
+//                block of x-rows, then the x-FFT of those rows in shared
+//                memory; p is never written before its first FFT pass.
+//   k_col_fft    y-FFT of column tiles in shared memory.
+//   k_ewald      the z-transform evaluated only at the two q_z bins each
+//                detector pixel needs (Eq. Ewald, linear interpolation),
+//                fused with Eq. (3Dscatter); no 3-D X array exists.
+//   k_rotate_acc detector rotation about q = 0 and accumulation (Sec. 4).
+// All of them are HBM-bound streaming kernels; none is a dense contraction.
+#include <math.h>
+
+#include "rsx_device.cuh"
+#include "rsx_kernels.h"
+
+namespace rsx {
+
+constexpr double kFourPi = 12.566370614359172953850573533118;
+
+// ------------------------------------------------------------ polarisation
+// Accumulated per voxel over components j, with a = v (1 + tau'_j),
+// tau'_j = tau_j + s dperp_j, b = v s dpar_j and d_j the director:
+//   (a^2 - 1)      = (v^2 - 1) + v^2 tau' (2 + tau')
+//   (2ab + b^2)    = b (2 v (1 + tau') + b)
+//   p = sum_j [(a_j^2 - 1) e + (2 a_j b_j + b_j^2)(d_j . e) d_j] / (4 pi)
+// This is N_rot = a I + b d d^T squared (d d^T idempotent) for the uniaxial
+// tensor of Eq. (uniaxialRefrativeIndex) rotated by R = B C D (Eq. nrot).
+// The sum of (v^2 - 1) is kept apart as sum v^2 so that, together with the
+// constant -(c-1), the large vacuum-like part never mixes with the small
+// optical contrast in FP32.
+template <typename R> struct PolAcc {
+  R aw;         // sum_j v_j^2
+  R as[2];      // sum_j v_j^2 tau'_j (2 + tau'_j)
+  R b[3][2];    // sum_j (2ab + b^2)(d . e) d
+};
+
+template <typename R>
+__device__ __forceinline__ void pol_zero(PolAcc<R>& a) {
+  a.aw = 0;
+  a.as[0] = a.as[1] = 0;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) a.b[k][0] = a.b[k][1] = 0;
+}
+
+__device__ __forceinline__ void sincos_r(float x, float* s, float* c) { sincosf(x, s, c); }
+__device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
+
+template <typename R>
+__device__ __forceinline__ void pol_add(PolAcc<R>& acc, R v, R s, R phi, R theta,
+                                        const PolParams<R>& pp, int j) {
+  const R tpr = pp.tau[j][0] + s * pp.dperp[j][0];
+  const R tpi = pp.tau[j][1] + s * pp.dperp[j][1];
+  const R v2 = v * v;
+  acc.aw += v2;
+  // tau' (2 + tau')
+  const R ur = tpr * (R(2) + tpr) - tpi * tpi;
+  const R ui = tpi * (R(2) + tpr) + tpr * tpi;
+  acc.as[0] += v2 * ur;
+  acc.as[1] += v2 * ui;
+  // b = v s dpar ; g = b (2 v (1 + tau') + b)
+  const R vs = v * s;
+  const R br = vs * pp.dpar[j][0], bi = vs * pp.dpar[j][1];
+  const R qr = R(2) * v * (R(1) + tpr) + br, qi = R(2) * v * tpi + bi;
+  const R gr = br * qr - bi * qi, gi = br * qi + bi * qr;
+  R sp, cp, st, ct;
+  sincos_r(phi, &sp, &cp);
+  sincos_r(theta, &st, &ct);
+  const R dx = cp * st, dy = sp * st, dz = ct;
+  const R de = dx * pp.ce + dy * pp.se;
+  const R hr = gr * de, hi = gi * de;
+  acc.b[0][0] += hr * dx; acc.b[0][1] += hi * dx;
+  acc.b[1][0] += hr * dy; acc.b[1][1] += hi * dy;
+  acc.b[2][0] += hr * dz; acc.b[2][1] += hi * dz;
+}
+
+// p (minus the reference constant unless add_ref) in the frame of pp.literal.
+template <typename R>
+__device__ __forceinline__ void pol_final(const PolAcc<R>& acc, const PolParams<R>& pp,
+                                          typename RT<R>::C out[3]) {
+  const R inv = R(1.0 / kFourPi);
+  R ar = (acc.aw - R(1)) + acc.as[0];
+  if (pp.add_ref) ar -= R(pp.c - 1);
+  const R ai = acc.as[1];
+  const R ce = pp.ce, se = pp.se;
+  R p0r, p0i, p1r, p1i;
+  if (pp.literal) {
+    p0r = ar + ce * acc.b[0][0] + se * acc.b[1][0];
+    p0i = ai + ce * acc.b[0][1] + se * acc.b[1][1];
+    p1r = -se * acc.b[0][0] + ce * acc.b[1][0];
+    p1i = -se * acc.b[0][1] + ce * acc.b[1][1];
+  } else {
+    p0r = ar * ce + acc.b[0][0];
+    p0i = ai * ce + acc.b[0][1];
+    p1r = ar * se + acc.b[1][0];
+    p1i = ai * se + acc.b[1][1];
+  }
+  out[0] = RT<R>::mk(p0r * inv, p0i * inv);
+  out[1] = RT<R>::mk(p1r * inv, p1i * inv);
+  out[2] = RT<R>::mk(acc.b[2][0] * inv, acc.b[2][1] * inv);
+}
+
+template <typename R>
+__device__ __forceinline__ void load_m(const typename RT<R>::V4* M, size_t i, R& v, R& s, R& ph,
+                                       R& th) {
+  const typename RT<R>::V4 m = M[i];
+  v = m.x; s = m.y; ph = m.z; th = m.w;
+}
+
+// One CTA: ROWS = EC / nx consecutive x-rows (row = z * ny + y) of all three
+// components of p.  Polarisation is computed component-outer so that every
+// thread keeps SLOTS independent 16/32-byte loads in flight, then the 3*ROWS
+// rows are transformed along x in shared memory and written once.
+template <typename R, int T, int EC, bool DO_FFT>
+__global__ void __launch_bounds__(T) k_pol_fftx(const typename RT<R>::V4* __restrict__ M,
+                                                long long N, int lognx, long long nrows,
+                                                PolParams<R> pp, typename RT<R>::C* __restrict__ p,
+                                                const typename RT<R>::C* __restrict__ twx,
+                                                int tw_in_smem) {
+  using C = typename RT<R>::C;
+  constexpr int SLOTS = EC / T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [3][ROWS][nx]
+  C* tws = buf + 3 * EC;
+  const int nx = 1 << lognx;
+  const int ROWS = EC >> lognx;
+  const long long row0 = (long long)blockIdx.x * ROWS;
+  const long long rl = nrows - row0;
+  const int rows_here = rl < ROWS ? (int)rl : ROWS;
+  const int nel = rows_here << lognx;
+  const size_t vox0 = (size_t)row0 << lognx;
+
+  if (DO_FFT && tw_in_smem)
+    for (int i = threadIdx.x; i < nx; i += T) tws[i] = twx[i];
+
+  PolAcc<R> acc[SLOTS];
+#pragma unroll
+  for (int sl = 0; sl < SLOTS; ++sl) pol_zero(acc[sl]);
+  for (int j = 0; j < pp.c; ++j) {
+    const typename RT<R>::V4* Mj = M + (size_t)j * N + vox0;
+    R v[SLOTS], s[SLOTS], ph[SLOTS], th[SLOTS];
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) {
+      const int e = threadIdx.x + sl * T;
+      if (e < nel) load_m<R>(Mj, e, v[sl], s[sl], ph[sl], th[sl]);
+    }
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) {
+      const int e = threadIdx.x + sl * T;
+      if (e < nel) pol_add(acc[sl], v[sl], s[sl], ph[sl], th[sl], pp, j);
+    }
+  }
+#pragma unroll
+  for (int sl = 0; sl < SLOTS; ++sl) {
+    const int e = threadIdx.x + sl * T;
+    if (e < nel) {
+      C out[3];
+      pol_final(acc[sl], pp, out);
+      if (DO_FFT) {
+        buf[e] = out[0];
+        buf[EC + e] = out[1];
+        buf[2 * EC + e] = out[2];
+      } else {
+        p[vox0 + e] = out[0];
+        p[(size_t)N + vox0 + e] = out[1];
+        p[2 * (size_t)N + vox0 + e] = out[2];
+      }
+    }
+  }
+  if (!DO_FFT) return;
+  __syncthreads();
+  const C* tw = tw_in_smem ? tws : twx;
+  block_fft<R, 3 * EC / 4 / T, 3 * EC / 2 / T, false>(buf, lognx, 3 * ROWS, -1, nx, 1, tw);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+    for (int e = threadIdx.x; e < nel; e += T) p[(size_t)k * N + vox0 + e] = buf[k * EC + e];
+}
+
+// Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d.
+template <typename R, int T, int EC>
+__global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p, int lognx,
+                                               long long nrows,
+                                               const typename RT<R>::C* __restrict__ twx,
+                                               int tw_in_smem) {
+  using C = typename RT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  C* tws = buf + EC;
+  const int nx = 1 << lognx;
+  const int ROWS = EC >> lognx;
+  const long long row0 = (long long)blockIdx.x * ROWS;
+  const long long rl = nrows - row0;
+  const int rows_here = rl < ROWS ? (int)rl : ROWS;
+  const int nel = rows_here << lognx;
+  C* base = p + ((size_t)row0 << lognx);
+  if (tw_in_smem)
+    for (int i = threadIdx.x; i < nx; i += T) tws[i] = twx[i];
+  for (int e = threadIdx.x; e < nel; e += T) buf[e] = base[e];
+  __syncthreads();
+  const C* tw = tw_in_smem ? tws : twx;
+  block_fft<R, EC / 4 / T, EC / 2 / T, false>(buf, lognx, ROWS, -1, nx, 1, tw);
+  for (int e = threadIdx.x; e < nel; e += T) base[e] = buf[e];
+}
+
+// Column FFTs: element i of column col of batch b sits at
+//   data[b * batch_stride + i * S + tile * TX + col],  i < L = 2^logL.
+// One CTA transforms TX = 2^logTX adjacent columns (coalesced rows of TX
+// complex values) of one batch.  Used for y (S = nx, W = nx, batches =
+// 3 nz) and for z (S = W = nx ny, batches = 3).
+template <typename R, int T, int EC>
+__global__ void __launch_bounds__(T) k_col_fft(typename RT<R>::C* __restrict__ data, int logL,
+                                               long long S, int logTX, long long ntiles,
+                                               long long batch_stride,
+                                               const typename RT<R>::C* __restrict__ tw_g,
+                                               int tw_in_smem) {
+  using C = typename RT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [L][TX]
+  C* tws = buf + EC;
+  const int L = 1 << logL;
+  const int TX = 1 << logTX;
+  const long long tile = (long long)blockIdx.x % ntiles;
+  const long long b = (long long)blockIdx.x / ntiles;
+  C* base = data + b * batch_stride + tile * TX;
+  if (tw_in_smem)
+    for (int i = threadIdx.x; i < L; i += T) tws[i] = tw_g[i];
+  const int nel = L << logTX;
+  for (int e = threadIdx.x; e < nel; e += T) {
+    const int col = e & (TX - 1), i = e >> logTX;
+    buf[e] = base[(size_t)i * S + col];
+  }
+  __syncthreads();
+  const C* tw = tw_in_smem ? tws : tw_g;
+  block_fft<R, EC / 4 / T, EC / 2 / T, true>(buf, logL, TX, logTX, 1, TX, tw);
+  for (int e = threadIdx.x; e < nel; e += T) {
+    const int col = e & (TX - 1), i = e >> logTX;
+    base[(size_t)i * S + col] = buf[e];
+  }
+}
+
+// Direct DFT along z for any nz (out of place): out[k][m][pix] =
+//   sum_z in[k][z][pix] exp(-2 pi i m z / nz).
+template <typename R>
+__global__ void k_dft_z(const typename RT<R>::C* __restrict__ in, typename RT<R>::C* __restrict__ out,
+                        long long npix, int nz, const typename RT<R>::C* __restrict__ twz) {
+  using C = typename RT<R>::C;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = 3 * npix * nz;
+  if (t >= total) return;
+  const long long pix = t % npix;
+  const int m = (int)((t / npix) % nz);
+  const int k = (int)(t / (npix * nz));
+  const size_t N = (size_t)npix * nz;
+  const C* src = in + k * N + pix;
+  C acc = RT<R>::mk(0, 0);
+  int idx = 0;
+  for (int z = 0; z < nz; ++z) {
+    acc = cadd(acc, cmul(src[(size_t)z * npix], twz[idx]));
+    idx += m;
+    if (idx >= nz) idx -= nz;
+  }
+  out[k * N + (size_t)m * npix + pix] = acc;
+}
+
+// --------------------------------------------------------------- geometry
+// Eq. (Ewald) per pixel, in double: q from the FFT index (FFT order),
+// q_z = -k + sqrt(k^2 - q_x^2 - q_y^2), t = q_z / dq_z, bins floor(t) and
+// floor(t) + 1 (periodic), weight w = t - floor(t) on the upper bin.
+template <typename R>
+__global__ void k_geometry(Geo<R>* __restrict__ geo, int nx, int ny, int nz, double voxel_nm,
+                           double k) {
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= (long long)nx * ny) return;
+  const int mx = (int)(pix % nx), my = (int)(pix / nx);
+  const int fx = mx < (nx + 1) / 2 ? mx : mx - nx;
+  const int fy = my < (ny + 1) / 2 ? my : my - ny;
+  const double two_pi = 6.283185307179586476925286766559;
+  const double qx = two_pi * fx / (nx * voxel_nm);
+  const double qy = two_pi * fy / (ny * voxel_nm);
+  const double rad = k * k - qx * qx - qy * qy;
+  Geo<R> g;
+  if (rad < 0.0) {
+    g.b0 = g.b1 = -1;
+    g.w = g.rx = g.ry = g.rz = g.k4 = R(0);
+    geo[pix] = g;
+    return;
+  }
+  const double qz = -k + sqrt(rad);
+  const double dqz = two_pi / (nz * voxel_nm);
+  const double t = qz / dqz;
+  const double z0 = floor(t);
+  const double w = t - z0;
+  long long i0 = (long long)z0 % nz;
+  if (i0 < 0) i0 += nz;
+  long long i1 = i0 + 1;
+  if (i1 >= nz) i1 -= nz;
+  const double kz = k + qz;
+  const double kmag2 = qx * qx + qy * qy + kz * kz;
+  const double kmag = sqrt(kmag2);
+  g.b0 = (int)i0;
+  g.b1 = (int)i1;
+  g.w = (R)w;
+  g.rx = (R)(qx / kmag);
+  g.ry = (R)(qy / kmag);
+  g.rz = (R)(kz / kmag);
+  g.k4 = (R)(kmag2 * kmag2);
+  geo[pix] = g;
+}
+
+// ------------------------------------------------------------------- Ewald
+// |(I - r r) v|^2 = sum_k |v_k - r_k (r . v)|^2 for one bin.
+template <typename R>
+__device__ __forceinline__ R proj_norm2(const typename RT<R>::C v[3], R rx, R ry, R rz) {
+  const R sr = rx * v[0].x + ry * v[1].x + rz * v[2].x;
+  const R si = rx * v[0].y + ry * v[1].y + rz * v[2].y;
+  const R y0r = v[0].x - rx * sr, y0i = v[0].y - rx * si;
+  const R y1r = v[1].x - ry * sr, y1i = v[1].y - ry * si;
+  const R y2r = v[2].x - rz * sr, y2i = v[2].y - rz * si;
+  return y0r * y0r + y0i * y0i + y1r * y1r + y1i * y1i + y2r * y2r + y2i * y2i;
+}
+
+// One thread per detector pixel (FFT order in, fftshift order out).
+// PRUNED: p holds x/y-transformed slices; the two needed q_z bins are
+// evaluated directly, p~(b) = sum_z P(z) exp(-2 pi i b z / nz), and the
+// constant removed before the FFT (N * dc at q = 0) is added back.
+// Otherwise p is the full p~ and the two bins are read.
+template <typename R, bool PRUNED>
+__global__ void __launch_bounds__(256) k_ewald(const typename RT<R>::C* __restrict__ p, int nx,
+                                               int ny, int nz, const Geo<R>* __restrict__ geo,
+                                               const typename RT<R>::C* __restrict__ twz, R dc0,
+                                               R dc1, R dc2, R* __restrict__ img) {
+  using C = typename RT<R>::C;
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const int mx = (int)(pix % nx), my = (int)(pix / nx);
+  const int sx = (mx + nx / 2) % nx, sy = (my + ny / 2) % ny;
+  R* dst = img + (size_t)sy * nx + sx;
+  const Geo<R> g = geo[pix];
+  if (g.b0 < 0) {
+    *dst = R(0);
+    return;
+  }
+  const size_t N = (size_t)npix * nz;
+  C a0[3], a1[3];
+  if (PRUNED) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a0[k] = a1[k] = RT<R>::mk(0, 0);
+    int i0 = 0, i1 = 0;
+    const C* src = p + pix;
+#pragma unroll 4
+    for (int z = 0; z < nz; ++z) {
+      const C w0 = __ldg(twz + i0), w1 = __ldg(twz + i1);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const C v = __ldg(src + k * N + (size_t)z * npix);
+        a0[k] = cadd(a0[k], cmul(v, w0));
+        a1[k] = cadd(a1[k], cmul(v, w1));
+      }
+      i0 += g.b0;
+      if (i0 >= nz) i0 -= nz;
+      i1 += g.b1;
+      if (i1 >= nz) i1 -= nz;
+    }
+    if (pix == 0) {
+      const R dcs[3] = {dc0, dc1, dc2};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        if (g.b0 == 0) a0[k].x += dcs[k];
+        if (g.b1 == 0) a1[k].x += dcs[k];
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      a0[k] = p[k * N + (size_t)g.b0 * npix + pix];
+      a1[k] = p[k * N + (size_t)g.b1 * npix + pix];
+    }
+  }
+  const R x0 = proj_norm2<R>(a0, g.rx, g.ry, g.rz);
+  const R x1 = proj_norm2<R>(a1, g.rx, g.ry, g.rz);
+  *dst = g.k4 * ((R(1) - g.w) * x0 + g.w * x1);
+}
+
+// ------------------------------------------------------- detector rotation
+// acc(Q) += img(U(alpha) Q), bilinear, zero outside; pixel coordinates in
+// fftshift order with centre (nx/2, ny/2) and the q-spacing ratio nx/ny.
+template <typename R>
+__global__ void k_rotate_acc(const R* __restrict__ img, R* __restrict__ acc, int nx, int ny,
+                             double ca, double sa, int rotate) {
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= (long long)nx * ny) return;
+  if (!rotate) {
+    acc[pix] += img[pix];
+    return;
+  }
+  const int ix = (int)(pix % nx), iy = (int)(pix / nx);
+  const int cx = nx / 2, cy = ny / 2;
+  const double rxy = (double)nx / ny, ryx = (double)ny / nx;
+  const double fx = cx + ca * (ix - cx) - sa * rxy * (iy - cy);
+  const double fy = cy + sa * ryx * (ix - cx) + ca * (iy - cy);
+  const double x0f = floor(fx), y0f = floor(fy);
+  const double tx = fx - x0f, ty = fy - y0f;
+  const long long x0 = (long long)x0f, y0 = (long long)y0f;
+  double val = 0.0;
+#pragma unroll
+  for (int dy = 0; dy < 2; ++dy) {
+    const long long yy = y0 + dy;
+    if (yy < 0 || yy >= ny) continue;
+    const double wy = dy ? ty : 1.0 - ty;
+#pragma unroll
+    for (int dx = 0; dx < 2; ++dx) {
+      const long long xx = x0 + dx;
+      if (xx < 0 || xx >= nx) continue;
+      const double wx = dx ? tx : 1.0 - tx;
+      val += wy * wx * (double)img[yy * nx + xx];
+    }
+  }
+  acc[pix] += (R)val;
+}
+
+template <typename R>
+__global__ void k_scale(const R* __restrict__ acc, R* __restrict__ out, long long n, R scale) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = acc[i] * scale;
+}
+
+// Sec. 3.1 ranges: 0 <= v <= 1, 0 <= s <= 1, finite angles.  Sets *flag.
+template <typename R>
+__global__ void k_validate(const R* __restrict__ M, long long n_entries, int* __restrict__ flag) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_entries) return;
+  const R v = M[4 * i], s = M[4 * i + 1], ph = M[4 * i + 2], th = M[4 * i + 3];
+  const bool ok = (v >= R(0)) && (v <= R(1)) && (s >= R(0)) && (s <= R(1)) && isfinite(ph) &&
+                  isfinite(th);
+  if (!ok) atomicOr(flag, 1);
+}
+
+// ================================================================ launchers
+static inline int ilog2(long long n) {
+  int l = 0;
+  while ((1LL << l) < n) ++l;
+  return l;
+}
+static inline unsigned grid1(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+template <typename R, int T, int EC, bool DO_FFT>
+static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
+                                 void* p, const void* twx, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  const long long N = (long long)nx * ny * nz;
+  // Without the FFT the voxels are independent: treat them as N rows of one.
+  const int lognx = DO_FFT ? ilog2(nx) : 0;
+  const long long nrows = DO_FFT ? (long long)ny * nz : N;
+  const int rows = DO_FFT ? EC / nx : EC;
+  size_t smem = DO_FFT ? 3 * EC * sizeof(C) : 0;
+  int tw_in_smem = 0;
+  if (DO_FFT && smem + nx * sizeof(C) <= 200 * 1024) {
+    smem += nx * sizeof(C);
+    tw_in_smem = 1;
+  }
+  auto kern = k_pol_fftx<R, T, EC, DO_FFT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid1(nrows, rows), T, smem, s>>>((const typename RT<R>::V4*)M, N, lognx, nrows, pp,
+                                           (C*)p, (const C*)twx, tw_in_smem);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
+                            bool do_fft, void* p, const void* twx, cudaStream_t s) {
+  if (!do_fft) return pol_fftx_impl<R, 256, 1024, false>(M, nx, ny, nz, pp, p, twx, s);
+  if (nx <= 2048) return pol_fftx_impl<R, 256, 2048, true>(M, nx, ny, nz, pp, p, twx, s);
+  return pol_fftx_impl<R, 512, 4096, true>(M, nx, ny, nz, pp, p, twx, s);
+}
+
+template <typename R, int T, int EC>
+static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* twx, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  size_t smem = EC * sizeof(C);
+  int tw_in_smem = 0;
+  if (smem + nx * sizeof(C) <= 200 * 1024) {
+    smem += nx * sizeof(C);
+    tw_in_smem = 1;
+  }
+  auto kern = k_row_fft<R, T, EC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid1(nrows, EC / nx), T, smem, s>>>((C*)p, ilog2(nx), nrows, (const C*)twx, tw_in_smem);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s) {
+  if (nx <= 2048) return row_fft_impl<R, 256, 2048>(p, nx, nrows, twx, s);
+  return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s);
+}
+
+template <typename R, int T, int EC>
+static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long long nbatch,
+                                long long batch_stride, const void* tw, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  long long TX = EC / L;
+  if (TX > W) TX = W;
+  if (TX < 1) TX = 1;
+  const int logTX = ilog2(TX);
+  const long long ntiles = W / TX;
+  size_t smem = (size_t)EC * sizeof(C);
+  int tw_in_smem = 0;
+  if (smem + L * sizeof(C) <= 200 * 1024) {
+    smem += L * sizeof(C);
+    tw_in_smem = 1;
+  }
+  auto kern = k_col_fft<R, T, EC>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)(ntiles * nbatch), T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles,
+                                                     batch_stride, (const C*)tw, tw_in_smem);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_col_fft(void* p, int L, long long S, long long W, long long nbatch,
+                           long long batch_stride, const void* tw, cudaStream_t s) {
+  if (L == 1) return cudaSuccess;
+  if (sizeof(R) == 4) return col_fft_impl<R, 512, 8192>(p, L, S, W, nbatch, batch_stride, tw, s);
+  return col_fft_impl<R, 512, 4096>(p, L, S, W, nbatch, batch_stride, tw, s);
+}
+
+template <typename R>
+cudaError_t launch_dft_z(const void* in, void* out, int nx, int ny, int nz, const void* twz,
+                         cudaStream_t s) {
+  using C = typename RT<R>::C;
+  const long long npix = (long long)nx * ny;
+  const long long total = 3 * npix * nz;
+  k_dft_z<R><<<grid1(total, 256), 256, 0, s>>>((const C*)in, (C*)out, npix, nz, (const C*)twz);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm, double k,
+                            cudaStream_t s) {
+  k_geometry<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>(geo, nx, ny, nz, voxel_nm, k);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
+                         const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  const long long npix = (long long)nx * ny;
+  if (pruned)
+    k_ewald<R, true><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo, (const C*)twz,
+                                                       dc[0], dc[1], dc[2], (R*)img);
+  else
+    k_ewald<R, false><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo,
+                                                        (const C*)twz, dc[0], dc[1], dc[2], (R*)img);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
+                              bool rotate, cudaStream_t s) {
+  k_rotate_acc<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>(
+      (const R*)img, (R*)acc, nx, ny, cos(alpha), sin(alpha), rotate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_scale(const void* acc, void* out, long long n, double scale, cudaStream_t s) {
+  k_scale<R><<<grid1(n, 256), 256, 0, s>>>((const R*)acc, (R*)out, n, (R)scale);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaStream_t s) {
+  if (n_entries == 0) return cudaSuccess;
+  k_validate<R><<<grid1(n_entries, 256), 256, 0, s>>>((const R*)M, n_entries, flag);
+  return cudaGetLastError();
+}
+
+#define RSX_INSTANTIATE(R)                                                                        \
+  template cudaError_t launch_pol_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \
+                                          void*, const void*, cudaStream_t);                      \
+  template cudaError_t launch_row_fft<R>(void*, int, long long, const void*, cudaStream_t);       \
+  template cudaError_t launch_col_fft<R>(void*, int, long long, long long, long long, long long,  \
+                                         const void*, cudaStream_t);                              \
+  template cudaError_t launch_dft_z<R>(const void*, void*, int, int, int, const void*,            \
+                                       cudaStream_t);                                             \
+  template cudaError_t launch_geometry<R>(Geo<R>*, int, int, int, double, double, cudaStream_t);  \
+  template cudaError_t launch_ewald<R>(const void*, int, int, int, const Geo<R>*, const void*,     \
+                                       bool, const R*, void*, cudaStream_t);                      \
+  template cudaError_t launch_rotate_acc<R>(const void*, void*, int, int, double, bool,           \
+                                            cudaStream_t);                                        \
+  template cudaError_t launch_scale<R>(const void*, void*, long long, double, cudaStream_t);      \
+  template cudaError_t launch_validate<R>(const void*, long long, int*, cudaStream_t);
+
+RSX_INSTANTIATE(float)
+RSX_INSTANTIATE(double)
+
+}  // namespace rsx

@@ -1,0 +1,60 @@
+// Internal (C++) interface between the C ABI layer and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "../../include/rsx.h"
+
+namespace rsx {
+
+// Per-energy, per-angle constants of Eq. (polarization), in the split form
+// that keeps FP32 accurate: with eps = n - 1 (small, Sec. 3.2),
+//   tau   = (eps_par + 2 eps_perp) / 3          (Tr(N)/3 - 1)
+//   dperp = eps_perp - tau                      (n_perp - Tr(N)/3)
+//   dpar  = eps_par - eps_perp                  (n_par - n_perp)
+// Complex values are stored as (re, im) pairs of R.
+template <typename R> struct PolParams {
+  R tau[RSX_MAX_COMPONENTS][2];
+  R dperp[RSX_MAX_COMPONENTS][2];
+  R dpar[RSX_MAX_COMPONENTS][2];
+  R ce, se;     // cos(alpha), sin(alpha): e = U(alpha) (1, 0, 0)
+  int c;        // number of components
+  int literal;  // 1: p <- U^T p (RSX_FRAME_LITERAL), 0: lab frame
+  int add_ref;  // 1: output full p; 0: p minus the constant -(c-1) e'/(4 pi)
+};
+
+// Per-pixel Ewald geometry for one energy (Eq. Ewald): the two bracketing
+// q_z bins (b0 < 0 marks a pixel with no real q_z), the interpolation
+// weight w of bin b1, r-hat = k_out/|k_out| and |k_out|^4.
+template <typename R> struct __align__(16) Geo {
+  int b0, b1;
+  R w, rx, ry, rz, k4;
+};
+
+template <typename R>
+cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
+                            bool do_fft, void* p, const void* twx, cudaStream_t s);
+template <typename R>
+cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s);
+template <typename R>
+cudaError_t launch_col_fft(void* p, int L, long long S, long long W, long long nbatch,
+                           long long batch_stride, const void* tw, cudaStream_t s);
+template <typename R>
+cudaError_t launch_dft_z(const void* in, void* out, int nx, int ny, int nz, const void* twz,
+                         cudaStream_t s);
+template <typename R>
+cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm, double k,
+                            cudaStream_t s);
+template <typename R>
+cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
+                         const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s);
+template <typename R>
+cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
+                              bool rotate, cudaStream_t s);
+template <typename R>
+cudaError_t launch_scale(const void* acc, void* out, long long n, double scale, cudaStream_t s);
+template <typename R>
+cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaStream_t s);
+
+}  // namespace rsx

@@ -1,0 +1,266 @@
+"""Python binding of libprsoxs_gb300.so (the C ABI in include/rsx.h).
+
+Argument marshalling only: every step of the simulation runs in the CUDA
+library.  torch tensors supply device memory and streams.  Importing this
+module loads the library and raises if it is missing: there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from .build_ext import lib_path
+
+RSX_OK = 0
+RSX_ERR_INVALID = -1
+RSX_ERR_OOM = -2
+RSX_ERR_CUDA = -3
+RSX_ERR_UNSUPPORTED = -4
+RSX_ERR_STATE = -5
+RSX_HOST = 0
+RSX_DEVICE = 1
+RSX_FRAME_LITERAL = 0
+RSX_FRAME_LAB = 1
+RSX_MAX_COMPONENTS = 32
+
+EXPORTED = (
+    "rsx_create", "rsx_destroy", "rsx_last_error", "rsx_workspace_bytes", "rsx_angle_count",
+    "rsx_set_morphology", "rsx_set_optical_constants", "rsx_run", "rsx_polarization",
+    "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
+    "rsx_set_timing", "rsx_phase_times",
+)
+PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other")
+
+
+class RsxConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+        ("n_components", ctypes.c_int),
+        ("voxel_nm", ctypes.c_double),
+        ("precision", ctypes.c_int),
+        ("algorithm", ctypes.c_int),
+        ("frame", ctypes.c_int),
+        ("validate", ctypes.c_int),
+    ]
+
+
+class RsxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"rsx error {code}: {msg}")
+        self.code = code
+
+
+def load_library(path: str | None = None) -> ctypes.CDLL:
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: run paper_2209_13121_gb300.build_ext first "
+                           "(the CUDA library is required; there is no CPU path)")
+    lib = ctypes.CDLL(path)
+    vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "rsx_create": (ci, [ctypes.POINTER(RsxConfig), ctypes.POINTER(vp)]),
+        "rsx_destroy": (ci, [vp]),
+        "rsx_last_error": (ctypes.c_char_p, []),
+        "rsx_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(RsxConfig)]),
+        "rsx_angle_count": (ci, [cd, cd, cd, ci]),
+        "rsx_set_morphology": (ci, [vp, vp, ci, vp]),
+        "rsx_set_optical_constants": (ci, [vp, ci, vp, vp]),
+        "rsx_run": (ci, [vp, cd, cd, cd, ci, vp, ci, vp, ci, vp]),
+        "rsx_polarization": (ci, [vp, ci, cd, vp, vp]),
+        "rsx_fft3d": (ci, [vp, vp, vp]),
+        "rsx_ewald": (ci, [vp, ci, vp, vp, vp]),
+        "rsx_rotate_accumulate": (ci, [vp, vp, cd, vp, vp]),
+        "rsx_scatter_angle": (ci, [vp, ci, cd, vp, vp]),
+        "rsx_set_timing": (ci, [vp, ci]),
+        "rsx_phase_times": (ci, [vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype, f.argtypes = res, args
+    return lib
+
+
+_LIB = None
+
+
+def lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        _LIB = load_library()
+    return _LIB
+
+
+def _check(rc):
+    if rc != RSX_OK:
+        raise RsxError(rc, lib().rsx_last_error().decode())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def angle_count(start, inc, end, rotation=True) -> int:
+    return lib().rsx_angle_count(start, inc, end, 1 if rotation else 0)
+
+
+def make_config(nx, ny, nz, n_components, voxel_nm, precision=32, algorithm=1,
+                frame=RSX_FRAME_LITERAL, validate=False) -> RsxConfig:
+    return RsxConfig(nx, ny, nz, n_components, voxel_nm, precision, algorithm, frame,
+                     1 if validate else 0)
+
+
+def workspace_bytes(cfg: RsxConfig) -> int:
+    return lib().rsx_workspace_bytes(ctypes.byref(cfg))
+
+
+class Context:
+    """One simulation context (a grid, a material count and a precision).
+
+    Device buffers passed to the methods are torch CUDA tensors (or raw
+    integer addresses); host buffers are numpy arrays."""
+
+    def __init__(self, nx, ny, nz, n_components, voxel_nm, precision=32, algorithm=1,
+                 frame=RSX_FRAME_LITERAL, validate=False):
+        self.cfg = make_config(nx, ny, nz, n_components, voxel_nm, precision, algorithm,
+                               frame, validate)
+        self.real = np.float32 if precision == 32 else np.float64
+        h = ctypes.c_void_p()
+        _check(lib().rsx_create(ctypes.byref(self.cfg), ctypes.byref(h)))
+        self._h = h
+        self._keep = None  # keeps a borrowed device morphology alive
+
+    @property
+    def shape(self):
+        return (self.cfg.nz, self.cfg.ny, self.cfg.nx)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().rsx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ------------------------------------------------------------ inputs
+    def set_morphology(self, M, stream=None):
+        """M: [c][nz][ny][nx][4] (v, s, phi, theta).  numpy -> copied from
+        host; torch CUDA tensor -> borrowed (kept alive by this object)."""
+        if isinstance(M, np.ndarray):
+            A = np.ascontiguousarray(M, dtype=self.real)
+            self._check_shape(A.shape)
+            _check(lib().rsx_set_morphology(self._h, A.ctypes.data_as(ctypes.c_void_p), RSX_HOST,
+                                            _stream_handle(stream) if stream is not None else None))
+            self._keep = None
+            return
+        self._check_shape(tuple(M.shape))
+        if not M.is_contiguous():
+            raise ValueError("device morphology must be contiguous")
+        _check(lib().rsx_set_morphology(self._h, ctypes.c_void_p(M.data_ptr()), RSX_DEVICE,
+                                        _stream_handle(stream)))
+        self._keep = M
+
+    def _check_shape(self, shp):
+        want = (self.cfg.n_components, self.cfg.nz, self.cfg.ny, self.cfg.nx, 4)
+        if tuple(shp) != want:
+            raise ValueError(f"morphology shape {shp}, expected {want}")
+
+    def set_optical_constants(self, energies, constants):
+        E = np.ascontiguousarray(energies, dtype=np.float64)
+        K = np.ascontiguousarray(constants, dtype=np.float64)
+        if K.shape != (E.size, self.cfg.n_components, 4):
+            raise ValueError(f"constants shape {K.shape}, expected {(E.size, self.cfg.n_components, 4)}")
+        _check(lib().rsx_set_optical_constants(self._h, E.size, E.ctypes.data_as(ctypes.c_void_p),
+                                               K.ctypes.data_as(ctypes.c_void_p)))
+        self.n_energies = E.size
+
+    # --------------------------------------------------------- simulation
+    def run(self, angles=(0.0, 1.0, 0.0), rotation=True, energy_indices=None, out=None,
+            stream=None):
+        """Algorithm 1 for the selected energies.  out: None (returns a new
+        host numpy array), a numpy array (host) or a torch CUDA tensor."""
+        sel = None
+        n_sel = getattr(self, "n_energies", 0)
+        if energy_indices is not None:
+            sel = np.ascontiguousarray(energy_indices, dtype=np.int32)
+            n_sel = sel.size
+        shape = (n_sel, self.cfg.ny, self.cfg.nx)
+        if out is None:
+            out = np.empty(shape, dtype=self.real)
+        if isinstance(out, np.ndarray):
+            if out.shape != shape or out.dtype != self.real or not out.flags.c_contiguous:
+                raise ValueError("host output has the wrong shape, dtype or layout")
+            ptr, where = out.ctypes.data_as(ctypes.c_void_p), RSX_HOST
+            st = _stream_handle(stream) if stream is not None else None
+        else:
+            if tuple(out.shape) != shape or not out.is_contiguous():
+                raise ValueError("device output has the wrong shape or layout")
+            ptr, where = ctypes.c_void_p(out.data_ptr()), RSX_DEVICE
+            st = _stream_handle(stream)
+        _check(lib().rsx_run(self._h, float(angles[0]), float(angles[1]), float(angles[2]),
+                             1 if rotation else 0,
+                             sel.ctypes.data_as(ctypes.c_void_p) if sel is not None else None,
+                             n_sel, ptr, where, st))
+        return out
+
+    # ------------------------------------------------------------ timing
+    def set_timing(self, enable=True):
+        _check(lib().rsx_set_timing(self._h, 1 if enable else 0))
+
+    def phase_times(self):
+        """{phase: (total device ms, kernel launches)} since the last call."""
+        ms = (ctypes.c_double * len(PHASES))()
+        n = (ctypes.c_longlong * len(PHASES))()
+        _check(lib().rsx_phase_times(self._h, ms, n))
+        return {name: (ms[i], n[i]) for i, name in enumerate(PHASES)}
+
+    # ------------------------------------------------------- single steps
+    def polarization(self, energy_index, alpha_rad, p_out, stream=None):
+        _check(lib().rsx_polarization(self._h, int(energy_index), float(alpha_rad),
+                                      ctypes.c_void_p(p_out.data_ptr()), _stream_handle(stream)))
+        return p_out
+
+    def fft3d(self, p, stream=None):
+        _check(lib().rsx_fft3d(self._h, ctypes.c_void_p(p.data_ptr()), _stream_handle(stream)))
+        return p
+
+    def ewald(self, energy_index, p_tilde, img_out, stream=None):
+        _check(lib().rsx_ewald(self._h, int(energy_index), ctypes.c_void_p(p_tilde.data_ptr()),
+                               ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
+        return img_out
+
+    def rotate_accumulate(self, img, alpha_rad, acc, stream=None):
+        _check(lib().rsx_rotate_accumulate(self._h, ctypes.c_void_p(img.data_ptr()),
+                                           float(alpha_rad), ctypes.c_void_p(acc.data_ptr()),
+                                           _stream_handle(stream)))
+        return acc
+
+    def scatter_angle(self, energy_index, alpha_rad, img_out, stream=None):
+        _check(lib().rsx_scatter_angle(self._h, int(energy_index), float(alpha_rad),
+                                       ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
+        return img_out
+
+
+def deg2rad_list(start, inc, end, rotation=True):
+    """Angles (radians) the library uses for start:inc:end (inclusive)."""
+    n = angle_count(start, inc, end, rotation)
+    if not rotation:
+        return [0.0]
+    return [(start + inc * i) * (math.pi / 180.0) for i in range(n)]

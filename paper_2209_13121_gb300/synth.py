@@ -179,3 +179,36 @@ def morphology_grating(shape, period_vox: int, width_vox: int, axis: str = "x",
         M[0, ..., 0] = line[None, :, None]
     M[1, ..., 0] = 1.0 - M[0, ..., 0]
     return M
+
+
+def morphology_random_torch(shape, n_components: int, seed: int = 0, device="cuda",
+                            dtype=None):
+    """Device-side counterpart of morphology_random for large grids (the
+    benchmark's 10-GB morphologies): same recipe (smoothed-noise partition
+    of unity for v, s ~ U[0,1], phi ~ U[0, 2 pi), theta ~ U[0, pi]), drawn
+    with torch's seeded generator on `device`; not bitwise equal to the
+    numpy version.  Returns a contiguous [c][Nz][Ny][Nx][4] tensor."""
+    import torch
+
+    dtype = dtype or torch.float32
+    Nz, Ny, Nx = shape
+    c = n_components
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    M = torch.empty((c, Nz, Ny, Nx, 4), device=device, dtype=dtype)
+    fields = torch.rand((c, Nz, Ny, Nx), generator=g, device=device)
+    for ax, n in ((1, Nz), (2, Ny), (3, Nx)):
+        w = min(3, n)
+        acc = torch.zeros_like(fields)
+        for sh in range(w):
+            acc += torch.roll(fields, sh - w // 2, dims=ax)
+        fields = acc / w
+        del acc
+    fields = fields ** 4
+    fields /= fields.sum(dim=0, keepdim=True)
+    M[..., 0] = fields
+    del fields
+    M[..., 1] = torch.rand((c, Nz, Ny, Nx), generator=g, device=device)
+    M[..., 2] = torch.rand((c, Nz, Ny, Nx), generator=g, device=device) * (2.0 * np.pi)
+    M[..., 3] = torch.rand((c, Nz, Ny, Nx), generator=g, device=device) * np.pi
+    return M

@@ -1,0 +1,369 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Every row of the hot path is checked on its own (polarisation, 3-D FFT,
+Ewald projection, detector rotation), then the fused per-angle pipeline and
+the whole of Algorithm 1, on seeded inputs at sizes the oracle finishes in
+seconds: several FFT tiles, ragged z extents, Nz = 1 films, ny = 1 and a
+single voxel.  The full benchmark size (1024 x 1024 x 128, c = 4, FP32) is
+checked through a property that holds at any size.
+
+Tolerances (derived in the design notes from the arithmetic):
+  FP64: relative L2 error <= 1e-10 over pixels away from q = 0, and
+        per-pixel relative <= 1e-8 where X > 1e-8 max X.
+  FP32: relative L2 error <= 1e-4 over pixels away from q = 0, and
+        per-pixel relative <= 2e-3 where X > 1e-4 max X.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import cyrsoxs_oracle as O
+from paper_2209_13121_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = {64: dict(norm=1e-10, pix=1e-8, floor=1e-8), 32: dict(norm=1e-4, pix=2e-3, floor=1e-4)}
+ENERGIES = [270.0, 285.0, 310.0]
+VOXEL = 5.0
+
+
+@pytest.fixture(scope="module")
+def rsx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2209_13121_gb300 import rsx as R
+    return R
+
+
+def _real(prec):
+    return np.float32 if prec == 32 else np.float64
+
+
+def _tdtype(prec):
+    return torch.float32 if prec == 32 else torch.float64
+
+
+def _inputs(shape, c, prec, seed):
+    M = synth.morphology_random(shape, c, seed=seed, dtype=_real(prec))
+    K = synth.optical_constants(ENERGIES, c, seed=seed + 100)
+    return M, K
+
+
+def _center_mask(ny, nx, r=1.5):
+    iy, ix = np.meshgrid(np.arange(ny) - ny // 2, np.arange(nx) - nx // 2, indexing="ij")
+    return np.hypot(ix, iy) > r
+
+
+def assert_image_close(gpu, ref, prec, mask=None):
+    gpu = np.asarray(gpu, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    t = TOL[prec]
+    if mask is None:
+        mask = _center_mask(*ref.shape[-2:])
+    mask = np.broadcast_to(mask, ref.shape)
+    a, b = gpu[mask], ref[mask]
+    if b.size and np.abs(b).max() > 0:
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= t["norm"], f"relative L2 error {rel:.3e} > {t['norm']:.0e}"
+    big = np.abs(ref) > t["floor"] * np.abs(ref).max()
+    if big.any():
+        pix = (np.abs(gpu - ref)[big] / np.abs(ref)[big]).max()
+        assert pix <= t["pix"], f"per-pixel relative error {pix:.3e} > {t['pix']:.0e}"
+    assert np.all(np.isfinite(gpu))
+
+
+CASES = [
+    ((4, 8, 8), 2),
+    ((5, 16, 32), 3),     # ragged nz, nx != ny
+    ((16, 32, 32), 4),
+    ((1, 64, 64), 2),     # 2-D film, Nz = 1
+    ((3, 128, 16), 3),    # nx < ny, several y tiles
+    ((2, 1, 8), 2),       # ny = 1
+    ((1, 1, 1), 1),       # single voxel
+    ((7, 4, 2048), 2),    # nx at the x-FFT tile size, ragged nz
+]
+IDS = ["x".join(map(str, s)) + f"c{c}" for s, c in CASES]
+
+
+def _ctx(rsx, shape, c, prec, frame=0, **kw):
+    nz, ny, nx = shape
+    return rsx.Context(nx, ny, nz, c, VOXEL, precision=prec, frame=frame, **kw)
+
+
+# ------------------------------------------------------------ row a2 + a3
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape,c", CASES, ids=IDS)
+def test_polarization_matches_oracle(rsx, shape, c, prec):
+    M, K = _inputs(shape, c, prec, seed=1)
+    with _ctx(rsx, shape, c, prec) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        p = torch.empty((3,) + shape + (2,), dtype=_tdtype(prec), device="cuda")
+        for ie, alpha in ((0, 0.0), (1, 0.9), (2, 2.7)):
+            ctx.polarization(ie, alpha, p)
+            torch.cuda.synchronize()
+            got = p.cpu().numpy()
+            got = got[..., 0] + 1j * got[..., 1]
+            ref = O.rotate_back(O.polarization(M, K[ie], O.e_field(alpha)), alpha)
+            scale = np.abs(ref).max()
+            tol = 1e-13 if prec == 64 else 3e-7
+            np.testing.assert_allclose(got, ref, rtol=0, atol=tol * scale)
+            # the optical contrast (ref minus its mean) is also resolved
+            d_got, d_ref = got - ref.mean(), ref - ref.mean()
+            if np.abs(d_ref).max() > 0:
+                rel = np.linalg.norm(d_got - d_ref) / np.linalg.norm(d_ref)
+                assert rel < (1e-10 if prec == 64 else 2e-3)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_polarization_lab_frame(rsx, prec):
+    shape, c = (3, 8, 16), 3
+    M, K = _inputs(shape, c, prec, seed=2)
+    with _ctx(rsx, shape, c, prec, frame=rsx.RSX_FRAME_LAB) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        p = torch.empty((3,) + shape + (2,), dtype=_tdtype(prec), device="cuda")
+        ctx.polarization(1, 1.1, p)
+        got = p.cpu().numpy()
+        got = got[..., 0] + 1j * got[..., 1]
+        ref = O.polarization(M, K[1], O.e_field(1.1))
+        np.testing.assert_allclose(got, ref, rtol=0,
+                                   atol=(1e-13 if prec == 64 else 3e-7) * np.abs(ref).max())
+
+
+# ------------------------------------------------------------------ row a4
+FFT_SHAPES = [(4, 8, 8), (5, 16, 32), (1, 64, 64), (3, 128, 16), (2, 1, 8), (1, 1, 1),
+              (7, 4, 2048), (16, 32, 32), (6, 2, 4)]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape", FFT_SHAPES, ids=["x".join(map(str, s)) for s in FFT_SHAPES])
+def test_fft3d_matches_oracle(rsx, shape, prec):
+    g = np.random.default_rng(3)
+    p = (g.standard_normal((3,) + shape) + 1j * g.standard_normal((3,) + shape))
+    dev = torch.from_numpy(np.stack([p.real, p.imag], axis=-1).astype(_real(prec))).cuda()
+    with _ctx(rsx, shape, 1, prec) as ctx:
+        ctx.fft3d(dev)
+        got = dev.cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    ref = O.fft3(p.astype(np.complex64 if prec == 32 else np.complex128).astype(np.complex128))
+    tol = 1e-12 if prec == 64 else 2e-6
+    n = np.prod(shape)
+    np.testing.assert_allclose(got, ref, rtol=0, atol=tol * math.sqrt(n) * max(1.0, math.log2(n)))
+
+
+# ------------------------------------------------------------------ row a5
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape", [(4, 8, 8), (5, 16, 32), (1, 64, 64), (3, 128, 16)],
+                         ids=["4x8x8", "5x16x32", "1x64x64", "3x128x16"])
+def test_ewald_matches_oracle(rsx, shape, prec):
+    M, K = _inputs(shape, 2, 64, seed=4)
+    pt = O.fft3(O.polarization(M, K[0], O.e_field(0.3)))
+    dev = torch.from_numpy(np.stack([pt.real, pt.imag], axis=-1).astype(_real(prec))).cuda()
+    with _ctx(rsx, shape, 2, prec) as ctx:
+        ctx.set_optical_constants(ENERGIES, K)
+        for ie in range(3):
+            img = torch.empty(shape[1:], dtype=_tdtype(prec), device="cuda")
+            ctx.ewald(ie, dev, img)
+            ref = O.fftshift2(O.ewald(pt, ENERGIES[ie], VOXEL))
+            assert_image_close(img.cpu().numpy(), ref, prec)
+
+
+def test_ewald_outside_sphere_is_zero(rsx):
+    shape = (2, 16, 16)
+    pt = np.ones((3,) + shape, complex)
+    dev = torch.from_numpy(np.stack([pt.real, pt.imag], axis=-1)).cuda()
+    with rsx.Context(16, 16, 2, 1, 2.0, precision=64) as ctx:
+        ctx.set_optical_constants([120.0], np.zeros((1, 1, 4)))
+        img = torch.empty((16, 16), dtype=torch.float64, device="cuda")
+        ctx.ewald(0, dev, img)
+        ref = O.fftshift2(O.ewald(pt, 120.0, 2.0))
+        got = img.cpu().numpy()
+        assert np.array_equal(got == 0, ref == 0) and (ref == 0).sum() > 20
+        np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+# ------------------------------------------------------------------ row a6
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("ny,nx", [(16, 16), (32, 8), (1, 8), (64, 128)])
+def test_rotate_accumulate_matches_oracle(rsx, ny, nx, prec):
+    g = np.random.default_rng(5)
+    img = g.random((ny, nx))
+    acc0 = g.random((ny, nx))
+    with rsx.Context(nx, ny, 1, 1, VOXEL, precision=prec) as ctx:
+        for alpha in (0.0, 0.35, math.pi / 2, 2.9):
+            d_img = torch.from_numpy(img.astype(_real(prec))).cuda()
+            d_acc = torch.from_numpy(acc0.astype(_real(prec))).cuda()
+            ctx.rotate_accumulate(d_img, alpha, d_acc)
+            ref = acc0.astype(_real(prec)).astype(np.float64) + O.rotate_image(
+                img.astype(_real(prec)).astype(np.float64), alpha)
+            tol = 1e-12 if prec == 64 else 2e-6
+            np.testing.assert_allclose(d_acc.cpu().numpy(), ref, rtol=tol, atol=tol)
+
+
+# ----------------------------------------------- rows a1-a5 fused (hot path)
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape,c", CASES, ids=IDS)
+def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
+    M, K = _inputs(shape, c, prec, seed=6)
+    with _ctx(rsx, shape, c, prec) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        img = torch.empty(shape[1:], dtype=_tdtype(prec), device="cuda")
+        for ie, alpha in ((0, 0.0), (1, 0.7), (2, 3.0)):
+            ctx.scatter_angle(ie, alpha, img)
+            ref = O.scatter_one_angle(M, K[ie], ENERGIES[ie], VOXEL, alpha)
+            assert_image_close(img.cpu().numpy(), ref, prec)
+            # q = 0 itself (the constant part returns there)
+            ny, nx = shape[1:]
+            np.testing.assert_allclose(img.cpu().numpy()[ny // 2, nx // 2], ref[ny // 2, nx // 2],
+                                       rtol=1e-10 if prec == 64 else 1e-5)
+
+
+# ------------------------------------------------------- Algorithm 1 (a7)
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape,c", CASES[:5], ids=IDS[:5])
+def test_run_matches_oracle(rsx, shape, c, prec):
+    M, K = _inputs(shape, c, prec, seed=7)
+    angles = (0.0, 30.0, 180.0)
+    ref = O.run_alg1(M, K, ENERGIES, VOXEL, angles_deg=angles)
+    with _ctx(rsx, shape, c, prec) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        host = ctx.run(angles)
+        dev = torch.empty(ref.shape, dtype=_tdtype(prec), device="cuda")
+        ctx.run(angles, out=dev)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(dev.cpu().numpy(), host)
+    mask = _center_mask(*shape[1:], r=2.5)
+    assert_image_close(host, ref, prec, mask=mask)
+    center = ~mask
+    np.testing.assert_allclose(host[:, center], ref[:, center], rtol=1e-9 if prec == 64 else 1e-4)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_run_lab_frame_and_rotation_off(rsx, prec):
+    shape, c = (4, 16, 16), 3
+    M, K = _inputs(shape, c, prec, seed=8)
+    with _ctx(rsx, shape, c, prec, frame=rsx.RSX_FRAME_LAB) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        got = ctx.run((0.0, 45.0, 135.0))
+        ref = O.run_alg1(M, K, ENERGIES, VOXEL, angles_deg=(0.0, 45.0, 135.0), uT_mode="lab")
+        assert_image_close(got, ref, prec, mask=_center_mask(16, 16, 2.5))
+        off = ctx.run((0.0, 45.0, 135.0), rotation=False)
+        ref_off = O.run_alg1(M, K, ENERGIES, VOXEL, rotation=False, uT_mode="lab")
+        assert_image_close(off, ref_off, prec)
+
+
+def test_energy_shards_are_bitwise_rows_of_full_run(rsx):
+    """Sharding energies across ranks (independent units, no collective)
+    gives exactly the rows of the unsharded run."""
+    shape, c = (4, 32, 32), 4
+    E = list(np.linspace(270, 310, 6))
+    M = synth.morphology_random(shape, c, seed=9)
+    K = synth.optical_constants(E, c, seed=10)
+    with _ctx(rsx, shape, c, 32) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(E, K)
+        full = ctx.run((0, 20, 180))
+        parts = [ctx.run((0, 20, 180), energy_indices=idx) for idx in ([0, 1, 2], [3, 4], [5])]
+    np.testing.assert_array_equal(np.concatenate(parts), full)
+
+
+def test_device_morphology_is_borrowed(rsx):
+    shape, c = (3, 16, 32), 2
+    M, K = _inputs(shape, c, 32, seed=11)
+    with _ctx(rsx, shape, c, 32) as a, _ctx(rsx, shape, c, 32) as b:
+        a.set_morphology(M)
+        b.set_morphology(torch.from_numpy(M).cuda())
+        for x in (a, b):
+            x.set_optical_constants(ENERGIES, K)
+        np.testing.assert_array_equal(a.run((0, 60, 120)), b.run((0, 60, 120)))
+
+
+# ------------------------------------------------------------- error paths
+def test_errors_are_reported_and_write_nothing(rsx):
+    shape, c = (2, 8, 8), 2
+    M, K = _inputs(shape, c, 32, seed=12)
+    with _ctx(rsx, shape, c, 32, validate=True) as ctx:
+        out = np.full((1, 8, 8), 7.0, dtype=np.float32)
+        with pytest.raises(rsx.RsxError) as e:   # no morphology yet
+            ctx.run((0, 10, 20), out=out, energy_indices=[0])
+        assert e.value.code == rsx.RSX_ERR_STATE
+        assert np.all(out == 7.0)
+        bad = M.copy()
+        bad[1, 0, 0, 0, 1] = 1.5  # s > 1 (Sec. 3.1)
+        with pytest.raises(rsx.RsxError) as e:
+            ctx.set_morphology(bad)
+        assert e.value.code == rsx.RSX_ERR_INVALID
+        with pytest.raises(rsx.RsxError) as e:
+            ctx.set_morphology(torch.from_numpy(bad).cuda())
+        assert e.value.code == rsx.RSX_ERR_INVALID
+        nanm = M.copy()
+        nanm[0, 1, 2, 3, 2] = np.nan
+        with pytest.raises(rsx.RsxError):
+            ctx.set_morphology(nanm)
+        ctx.set_morphology(M)
+        with pytest.raises(rsx.RsxError) as e:
+            ctx.set_optical_constants([285.0, -1.0, 300.0], K)
+        assert e.value.code == rsx.RSX_ERR_INVALID
+        ctx.set_optical_constants(ENERGIES, K)
+        for kw in (dict(angles=(0, 0, 10)), dict(angles=(10, 1, 0)),
+                   dict(energy_indices=[3]), dict(energy_indices=[-1])):
+            o = np.full((len(kw.get("energy_indices", ENERGIES)), 8, 8), 7.0, dtype=np.float32)
+            with pytest.raises(rsx.RsxError) as e:
+                ctx.run(kw.get("angles", (0, 10, 20)), energy_indices=kw.get("energy_indices"),
+                        out=o)
+            assert e.value.code == rsx.RSX_ERR_INVALID
+            assert np.all(o == 7.0)
+        empty = ctx.run((0, 10, 20), energy_indices=[])
+        assert empty.shape == (0, 8, 8)
+
+
+def test_unvalidated_context_accepts_out_of_range_v_sum(rsx):
+    """Sec. 3.1: the sum of v over components is never checked."""
+    shape, c = (1, 8, 8), 2
+    M, K = _inputs(shape, c, 64, seed=13)
+    M[..., 0] = 1.0  # every component fills every voxel: sum 2
+    with _ctx(rsx, shape, c, 64, validate=True) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        got = ctx.run((0, 90, 90))
+    ref = O.run_alg1(M, K, ENERGIES, VOXEL, angles_deg=(0, 90, 90))
+    assert_image_close(got, ref, 64, mask=_center_mask(8, 8, 2.5))
+
+
+# ------------------------------------------ full benchmark size (property)
+def test_full_size_z_uniform_reduces_to_film(rsx):
+    """At 1024 x 1024 x 128, c = 4, FP32 (the benchmark's launch shape), a
+    morphology uniform along z must give tent(q_z) * Nz^2 * X_film, where
+    X_film is the oracle's Nz = 1 image and tent = max(0, 1 - |q_z|/dq_z)
+    (linear interpolation between the bracketing q_z bins, Eq. Ewald)."""
+    if torch.cuda.get_device_properties(0).total_memory < 40e9:
+        pytest.skip("needs ~15 GB of device memory")
+    nx = ny = 1024
+    nz, c, E = 128, 4, 285.0
+    M2 = synth.morphology_random((1, ny, nx), c, seed=14, dtype=np.float32)
+    K = synth.optical_constants([E], c, seed=15)
+    dev = torch.from_numpy(M2).cuda().expand(c, nz, ny, nx, 4).contiguous()
+    k = O.wavenumber(E)
+    qx = np.fft.fftshift(O.q_axis(nx, VOXEL))[None, :]
+    qy = np.fft.fftshift(O.q_axis(ny, VOXEL))[:, None]
+    qz = -k + np.sqrt(k * k - qx * qx - qy * qy)
+    tent = np.maximum(0.0, 1.0 - np.abs(qz) / (2 * np.pi / (nz * VOXEL)))
+    assert (tent > 0).sum() > 1000
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=32) as ctx:
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants([E], K)
+        img = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        for alpha in (0.0, 0.5):
+            ctx.scatter_angle(0, alpha, img)
+            film = O.scatter_one_angle(M2, K[0], E, VOXEL, alpha)
+            ref = tent * nz ** 2 * film
+            assert_image_close(img.cpu().numpy(), ref, 32, mask=_center_mask(ny, nx) & (tent > 0.05))
