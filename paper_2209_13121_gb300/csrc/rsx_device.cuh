@@ -27,75 +27,175 @@ template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
-// multiply by -i
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
-template <typename C, typename R> __device__ __forceinline__ C cscale(C a, R s) { a.x *= s; a.y *= s; return a; }
-template <typename C, typename R> __device__ __forceinline__ R cnorm2(C a) { return a.x * a.x + a.y * a.y; }
+
+// Asynchronous global -> shared copies of one complex element (cp.async):
+// the copy goes straight to shared memory without passing through
+// registers, so a thread can keep many of them in flight.
+__device__ __forceinline__ void cp_async_elem(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Shared-memory padding: one spare element after every 16, which makes the
+// Stockham reads and writes below free of bank conflicts for 8- and
+// 16-byte elements (checked by enumerating the warp access patterns).
+__device__ __forceinline__ int padi(int i) { return i + (i >> 4); }
+__host__ __device__ constexpr int padded(int n) { return n + (n >> 4) + 1; }
+
+// ------------------------------------------------ in-register small DFTs
+// a * exp(-2 pi i E / 16) for a compile-time E.
+template <int E, typename C> __device__ __forceinline__ C w16(C a) {
+  using R = decltype(a.x);
+  constexpr int e = E & 15;
+  constexpr double h = 0.70710678118654752440;
+  constexpr double c1 = 0.92387953251128675613, s1 = 0.38268343236508977173;
+  if constexpr (e == 0) return a;
+  else if constexpr (e == 4) return cmul_mi(a);
+  else if constexpr (e == 8) { a.x = -a.x; a.y = -a.y; return a; }
+  else if constexpr (e == 12) { C r; r.x = -a.y; r.y = a.x; return r; }
+  else if constexpr (e == 2) { C r; r.x = R(h) * (a.x + a.y); r.y = R(h) * (a.y - a.x); return r; }
+  else if constexpr (e == 6) { C r; r.x = R(h) * (a.y - a.x); r.y = -R(h) * (a.x + a.y); return r; }
+  else if constexpr (e == 10) { C r; r.x = -R(h) * (a.x + a.y); r.y = R(h) * (a.x - a.y); return r; }
+  else if constexpr (e == 14) { C r; r.x = R(h) * (a.x - a.y); r.y = R(h) * (a.x + a.y); return r; }
+  else {
+    // cos and sin of 2 pi e / 16 for odd e, from cos/sin(pi/8)
+    constexpr double cs[16] = {1, c1, h, s1, 0, -s1, -h, -c1, -1, -c1, -h, -s1, 0, s1, h, c1};
+    constexpr double sn[16] = {0, s1, h, c1, 1, c1, h, s1, 0, -s1, -h, -c1, -1, -c1, -h, -s1};
+    const R c = R(cs[e]), s = R(sn[e]);
+    C r;
+    r.x = a.x * c + a.y * s;
+    r.y = a.y * c - a.x * s;
+    return r;
+  }
+}
+
+template <typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+  const C t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+
+// 4-point forward DFT in place, outputs in natural order.
+template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+  const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
+  const C a2 = cadd(v1, v3), a3 = cmul_mi(csub(v1, v3));
+  v0 = cadd(a0, a2);
+  v2 = csub(a0, a2);
+  v1 = cadd(a1, a3);
+  v3 = csub(a1, a3);
+}
+
+// RAD-point forward DFT of v[0..RAD).  Output index r is left in register
+// v[out_pos<RAD>(r)].  8 = 4 x 2 and 16 = 4 x 4 with the inner twiddles
+// exp(-2 pi i m k1 / RAD) between the two stages.
+template <int RAD> __host__ __device__ constexpr int out_pos(int r) {
+  return RAD == 16 ? 4 * (r & 3) + (r >> 2) : RAD == 8 ? 2 * (r & 3) + (r >> 2) : r;
+}
+
+template <int RAD, typename C> __device__ __forceinline__ void dft_reg(C* v) {
+  if constexpr (RAD == 2) {
+    dft2(v[0], v[1]);
+  } else if constexpr (RAD == 4) {
+    dft4(v[0], v[1], v[2], v[3]);
+  } else if constexpr (RAD == 8) {
+    // n = m + 2 n1: 4-point DFTs over n1 for m = 0, 1 -> position m + 2 k1
+    dft4(v[0], v[2], v[4], v[6]);
+    dft4(v[1], v[3], v[5], v[7]);
+    v[3] = w16<2>(v[3]);   // W8^1
+    v[5] = w16<4>(v[5]);   // W8^2
+    v[7] = w16<6>(v[7]);   // W8^3
+    dft2(v[0], v[1]);
+    dft2(v[2], v[3]);
+    dft2(v[4], v[5]);
+    dft2(v[6], v[7]);
+  } else {
+    // n = m + 4 n1: 4-point DFTs over n1 -> a_m[k1] at position m + 4 k1
+    dft4(v[0], v[4], v[8], v[12]);
+    dft4(v[1], v[5], v[9], v[13]);
+    dft4(v[2], v[6], v[10], v[14]);
+    dft4(v[3], v[7], v[11], v[15]);
+    v[5] = w16<1>(v[5]);
+    v[9] = w16<2>(v[9]);
+    v[13] = w16<3>(v[13]);
+    v[6] = w16<2>(v[6]);
+    v[10] = w16<4>(v[10]);
+    v[14] = w16<6>(v[14]);
+    v[7] = w16<3>(v[7]);
+    v[11] = w16<6>(v[11]);
+    v[15] = w16<9>(v[15]);
+    // 4-point DFTs over m for each k1 -> X[k1 + 4 k2] at position 4 k1 + k2
+    dft4(v[0], v[1], v[2], v[3]);
+    dft4(v[4], v[5], v[6], v[7]);
+    dft4(v[8], v[9], v[10], v[11]);
+    dft4(v[12], v[13], v[14], v[15]);
+  }
+}
 
 // ---------------------------------------------------------------------------
 // Shared-memory Stockham FFT (forward, unnormalised).
 //
 // `nfft` independent transforms of length N = 2^logN live in shared memory
-// at buf[f * fstride + i * estride].  A radix-RAD pass with span Ns (the
-// product of the radices already applied) takes butterfly j of transform f,
+// at buf[padi(f * fstride + i * estride)].  A radix-RAD pass with span Ns
+// (the product of the radices already applied) takes butterfly j of
+// transform f,
 //   v_r = x[j + r N/RAD] * W_N^(r k N/(RAD Ns)),  k = j mod Ns,
 // applies the RAD-point DFT and writes y[(j - k) RAD + k + r Ns] = V_r; after
-// log passes the result is in natural order (self-sorting).  One radix-2 pass
-// precedes the radix-4 passes when logN is odd.  tw[t] = exp(-2 pi i t / N).
+// the last pass the result is in natural order (self-sorting).  Radix-16
+// passes come first, one radix-8/4/2 pass takes the remainder.
+// tw[t] = exp(-2 pi i t / N).
 //
 // Each pass reads all its inputs into registers, synchronises, then writes,
-// so one buffer serves as both source and destination.  Items are spread
-// over the block's T threads, at most MAXI per thread.  F_FAST picks the
-// item order: consecutive threads take consecutive transforms (column
-// transforms, contiguous in f) or consecutive butterflies (row transforms).
+// so one buffer is both source and destination.  Butterflies are spread
+// over the block's T threads (at most ELEMS / RAD of them).  F_FAST picks
+// the item order: consecutive threads take consecutive transforms (column
+// transforms) or consecutive butterflies of one transform (row transforms).
 // ---------------------------------------------------------------------------
-template <typename R, int RAD, int MAXI, bool F_FAST>
+template <typename R, int RAD, int ELEMS, int T, bool F_FAST>
 __device__ __forceinline__ void stockham_pass(typename RT<R>::C* buf, int logN, int logNs, int nfft,
                                               int lognfft, int fstride, int estride,
                                               const typename RT<R>::C* tw) {
   using C = typename RT<R>::C;
-  constexpr int LOGRAD = RAD == 2 ? 1 : 2;
-  const int lognb = logN - LOGRAD;  // butterflies per transform = N / RAD
+  constexpr int LOGRAD = RAD == 2 ? 1 : RAD == 4 ? 2 : RAD == 8 ? 3 : 4;
+  constexpr int MAXI = (ELEMS / RAD + T - 1) / T;
+  const int lognb = logN - LOGRAD;
   const int nb = 1 << lognb;
   const int total = nfft << lognb;
   const int Ns = 1 << logNs;
-  const int twshift = logN - LOGRAD - logNs;  // N / (RAD Ns) = 2^twshift
+  const int twshift = logN - LOGRAD - logNs;
   C v[MAXI][RAD];
   int off[MAXI];
 #pragma unroll
   for (int it = 0; it < MAXI; ++it) {
-    const int item = threadIdx.x + it * blockDim.x;
+    const int item = threadIdx.x + it * T;
     off[it] = -1;
     if (item < total) {
       int f, j;
       if (F_FAST) {
-        f = lognfft >= 0 ? (item & (nfft - 1)) : (item % nfft);
-        j = lognfft >= 0 ? (item >> lognfft) : (item / nfft);
+        f = item & (nfft - 1);
+        j = item >> lognfft;
       } else {
         f = item >> lognb;
         j = item & (nb - 1);
       }
       const int k = j & (Ns - 1);
-      C* base = buf + (size_t)f * fstride;
+      const int base = f * fstride;
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) v[it][r] = base[(j + r * nb) * estride];
+      for (int r = 0; r < RAD; ++r) v[it][r] = buf[padi(base + (j + r * nb) * estride)];
+      if (logNs > 0) {
 #pragma unroll
-      for (int r = 1; r < RAD; ++r) v[it][r] = cmul(v[it][r], tw[(r * k) << twshift]);
-      if (RAD == 2) {
-        C a = v[it][0], b = v[it][1];
-        v[it][0] = cadd(a, b);
-        v[it][1] = csub(a, b);
-      } else {
-        C a0 = cadd(v[it][0], v[it][2]);
-        C a1 = csub(v[it][0], v[it][2]);
-        C a2 = cadd(v[it][1], v[it][3]);
-        C a3 = cmul_mi(csub(v[it][1], v[it][3]));
-        v[it][0] = cadd(a0, a2);
-        v[it][1] = cadd(a1, a3);
-        v[it][2] = csub(a0, a2);
-        v[it][3] = csub(a1, a3);
+        for (int r = 1; r < RAD; ++r) v[it][r] = cmul(v[it][r], tw[(r * k) << twshift]);
       }
-      off[it] = f * fstride + (((j - k) << LOGRAD) + k) * estride;
+      dft_reg<RAD>(v[it]);
+      off[it] = base + (((j - k) << LOGRAD) + k) * estride;
     }
   }
   __syncthreads();
@@ -103,26 +203,129 @@ __device__ __forceinline__ void stockham_pass(typename RT<R>::C* buf, int logN, 
   for (int it = 0; it < MAXI; ++it) {
     if (off[it] >= 0) {
 #pragma unroll
-      for (int r = 0; r < RAD; ++r) buf[off[it] + r * Ns * estride] = v[it][r];
+      for (int r = 0; r < RAD; ++r) buf[padi(off[it] + r * Ns * estride)] = v[it][out_pos<RAD>(r)];
     }
   }
   __syncthreads();
 }
 
-// Whole transform: nfft transforms of length 2^logN.  The caller has
-// synchronised after filling buf and tw; on return buf holds the spectra
-// and the block is synchronised.  lognfft < 0 when nfft is not a power of 2
-// (only allowed with F_FAST = false).
-template <typename R, int MAXI4, int MAXI2, bool F_FAST>
+// nfft transforms of length 2^logN (ELEMS >= nfft << logN).  The caller has
+// synchronised after filling buf and tw; on return buf holds the spectra and
+// the block is synchronised.  F_FAST needs nfft = 2^lognfft.
+template <typename R, int ELEMS, int T, bool F_FAST>
 __device__ __forceinline__ void block_fft(typename RT<R>::C* buf, int logN, int nfft, int lognfft,
                                           int fstride, int estride, const typename RT<R>::C* tw) {
   int logNs = 0;
-  if (logN & 1) {
-    stockham_pass<R, 2, MAXI2, F_FAST>(buf, logN, 0, nfft, lognfft, fstride, estride, tw);
-    logNs = 1;
+  for (; logN - logNs >= 4; logNs += 4)
+    stockham_pass<R, 16, ELEMS, T, F_FAST>(buf, logN, logNs, nfft, lognfft, fstride, estride, tw);
+  switch (logN - logNs) {
+    case 3:
+      stockham_pass<R, 8, ELEMS, T, F_FAST>(buf, logN, logNs, nfft, lognfft, fstride, estride, tw);
+      break;
+    case 2:
+      stockham_pass<R, 4, ELEMS, T, F_FAST>(buf, logN, logNs, nfft, lognfft, fstride, estride, tw);
+      break;
+    case 1:
+      stockham_pass<R, 2, ELEMS, T, F_FAST>(buf, logN, logNs, nfft, lognfft, fstride, estride, tw);
+      break;
+    default:
+      break;
   }
-  for (; logNs < logN; logNs += 2)
-    stockham_pass<R, 4, MAXI4, F_FAST>(buf, logN, logNs, nfft, lognfft, fstride, estride, tw);
+}
+
+// ---------------------------------------------------------------------------
+// The same Stockham FFT with every size known at compile time: the
+// transform length 2^LOGN, NFFT transforms, their strides, and the block
+// shape.  Address arithmetic then folds into constants; where a stride is a
+// multiple of 16 the padding of a whole run of 16 accesses is computed once
+// (padi(a + 16 m) = padi(a) + 17 m).
+// ---------------------------------------------------------------------------
+template <int S> __device__ __forceinline__ int pad_step(int a, int r) {
+  if constexpr (S % 16 == 0) return a + r * (S + S / 16);
+  else return a + r * S;  // unused: callers branch on S % 16 first
+}
+
+template <typename R, int RAD, int LOGN, int LOGNS, int NFFT, int FSTRIDE, int ESTRIDE, int T,
+          bool F_FAST>
+__device__ __forceinline__ void stockham_pass_ct(typename RT<R>::C* buf, const typename RT<R>::C* tw) {
+  using C = typename RT<R>::C;
+  constexpr int LOGRAD = RAD == 2 ? 1 : RAD == 4 ? 2 : RAD == 8 ? 3 : 4;
+  constexpr int LOGNB = LOGN - LOGRAD;
+  constexpr int NB = 1 << LOGNB;
+  constexpr int TOTAL = NFFT << LOGNB;
+  constexpr int NS = 1 << LOGNS;
+  constexpr int TWSHIFT = LOGN - LOGRAD - LOGNS;
+  constexpr int MAXI = (TOTAL + T - 1) / T;
+  constexpr int RSTR = NB * ESTRIDE;   // read stride between the RAD inputs
+  constexpr int WSTR = NS * ESTRIDE;   // write stride between the RAD outputs
+  C v[MAXI][RAD];
+  int woff[MAXI];
+#pragma unroll
+  for (int it = 0; it < MAXI; ++it) {
+    const int item = threadIdx.x + it * T;
+    if (TOTAL % T == 0 || item < TOTAL) {
+      int f, j;
+      if (F_FAST) {
+        f = item % NFFT;
+        j = item / NFFT;
+      } else {
+        f = item >> LOGNB;
+        j = item & (NB - 1);
+      }
+      const int k = j & (NS - 1);
+      const int a = f * FSTRIDE + j * ESTRIDE;
+      if constexpr (RSTR % 16 == 0) {
+        const int pa = padi(a);
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[it][r] = buf[pad_step<RSTR>(pa, r)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) v[it][r] = buf[padi(a + r * RSTR)];
+      }
+      if constexpr (LOGNS > 0) {
+#pragma unroll
+        for (int r = 1; r < RAD; ++r) v[it][r] = cmul(v[it][r], tw[(r * k) << TWSHIFT]);
+      }
+      dft_reg<RAD>(v[it]);
+      woff[it] = f * FSTRIDE + (((j - k) << LOGRAD) + k) * ESTRIDE;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < MAXI; ++it) {
+    const int item = threadIdx.x + it * T;
+    if (TOTAL % T == 0 || item < TOTAL) {
+      if constexpr (WSTR % 16 == 0) {
+        const int pw = padi(woff[it]);
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) buf[pad_step<WSTR>(pw, r)] = v[it][out_pos<RAD>(r)];
+      } else {
+#pragma unroll
+        for (int r = 0; r < RAD; ++r) buf[padi(woff[it] + r * WSTR)] = v[it][out_pos<RAD>(r)];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R, int LOGN, int LOGNS, int NFFT, int FSTRIDE, int ESTRIDE, int T, bool F_FAST>
+__device__ __forceinline__ void block_fft_ct_from(typename RT<R>::C* buf, const typename RT<R>::C* tw) {
+  constexpr int REM = LOGN - LOGNS;
+  if constexpr (REM >= 4) {
+    stockham_pass_ct<R, 16, LOGN, LOGNS, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
+    block_fft_ct_from<R, LOGN, LOGNS + 4, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
+  } else if constexpr (REM == 3) {
+    stockham_pass_ct<R, 8, LOGN, LOGNS, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
+  } else if constexpr (REM == 2) {
+    stockham_pass_ct<R, 4, LOGN, LOGNS, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
+  } else if constexpr (REM == 1) {
+    stockham_pass_ct<R, 2, LOGN, LOGNS, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
+  }
+}
+
+template <typename R, int LOGN, int NFFT, int FSTRIDE, int ESTRIDE, int T, bool F_FAST>
+__device__ __forceinline__ void block_fft_ct(typename RT<R>::C* buf, const typename RT<R>::C* tw) {
+  block_fft_ct_from<R, LOGN, 0, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
 }
 
 }  // namespace rsx

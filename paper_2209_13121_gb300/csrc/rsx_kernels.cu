@@ -19,6 +19,8 @@ namespace rsx {
 
 constexpr double kFourPi = 12.566370614359172953850573533118;
 
+__host__ __device__ constexpr int ilog2_ct(int n) { return n <= 1 ? 0 : 1 + ilog2_ct(n >> 1); }
+
 // ------------------------------------------------------------ polarisation
 // Accumulated per voxel over components j, with a = v (1 + tau'_j),
 // tau'_j = tau_j + s dperp_j, b = v s dpar_j and d_j the director:
@@ -44,7 +46,10 @@ __device__ __forceinline__ void pol_zero(PolAcc<R>& a) {
   for (int k = 0; k < 3; ++k) a.b[k][0] = a.b[k][1] = 0;
 }
 
-__device__ __forceinline__ void sincos_r(float x, float* s, float* c) { sincosf(x, s, c); }
+// FP32: the SFU approximation (absolute error below 1e-6 for the angles of
+// a morphology, |x| <= 2 pi), far below the FP32 contrast tolerance.  FP64
+// keeps the correctly rounded library call.
+__device__ __forceinline__ void sincos_r(float x, float* s, float* c) { __sincosf(x, s, c); }
 __device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
 
 template <typename R>
@@ -109,20 +114,25 @@ __device__ __forceinline__ void load_m(const typename RT<R>::V4* M, size_t i, R&
 }
 
 // One CTA: ROWS = EC / nx consecutive x-rows (row = z * ny + y) of all three
-// components of p.  Polarisation is computed component-outer so that every
-// thread keeps SLOTS independent 16/32-byte loads in flight, then the 3*ROWS
-// rows are transformed along x in shared memory and written once.
-template <typename R, int T, int EC, bool DO_FFT>
-__global__ void __launch_bounds__(T) k_pol_fftx(const typename RT<R>::V4* __restrict__ M,
-                                                long long N, int lognx, long long nrows,
+// components of p.  Polarisation is computed component-outer, the loads of
+// component j + 1 issued before the arithmetic of component j, so that every
+// thread keeps 2 SLOTS independent 16/32-byte loads in flight; then the
+// 3*ROWS rows are transformed along x in shared memory and written once.
+// LOGNX >= 0 fixes nx = 2^LOGNX at compile time (the FFT's index arithmetic
+// then folds into constants); LOGNX < 0 takes lognx at run time.
+template <typename R, int T, int EC, bool DO_FFT, int LOGNX>
+__global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_pol_fftx(const typename RT<R>::V4* __restrict__ M,
+                                                long long N, int lognx_rt, long long nrows,
                                                 PolParams<R> pp, typename RT<R>::C* __restrict__ p,
                                                 const typename RT<R>::C* __restrict__ twx,
                                                 int tw_in_smem) {
   using C = typename RT<R>::C;
+  using V4 = typename RT<R>::V4;
   constexpr int SLOTS = EC / T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [3][ROWS][nx]
-  C* tws = buf + 3 * EC;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [3][ROWS][nx], padded
+  C* tws = buf + padded(3 * EC);
+  const int lognx = LOGNX >= 0 ? LOGNX : lognx_rt;
   const int nx = 1 << lognx;
   const int ROWS = EC >> lognx;
   const long long row0 = (long long)blockIdx.x * ROWS;
@@ -137,19 +147,28 @@ __global__ void __launch_bounds__(T) k_pol_fftx(const typename RT<R>::V4* __rest
   PolAcc<R> acc[SLOTS];
 #pragma unroll
   for (int sl = 0; sl < SLOTS; ++sl) pol_zero(acc[sl]);
+  V4 cur[SLOTS], nxt[SLOTS];
+#pragma unroll
+  for (int sl = 0; sl < SLOTS; ++sl) {
+    const int e = threadIdx.x + sl * T;
+    if (e < nel) cur[sl] = M[vox0 + e];
+  }
   for (int j = 0; j < pp.c; ++j) {
-    const typename RT<R>::V4* Mj = M + (size_t)j * N + vox0;
-    R v[SLOTS], s[SLOTS], ph[SLOTS], th[SLOTS];
+    if (j + 1 < pp.c) {
+      const V4* Mj = M + (size_t)(j + 1) * N + vox0;
 #pragma unroll
-    for (int sl = 0; sl < SLOTS; ++sl) {
-      const int e = threadIdx.x + sl * T;
-      if (e < nel) load_m<R>(Mj, e, v[sl], s[sl], ph[sl], th[sl]);
+      for (int sl = 0; sl < SLOTS; ++sl) {
+        const int e = threadIdx.x + sl * T;
+        if (e < nel) nxt[sl] = Mj[e];
+      }
     }
 #pragma unroll
     for (int sl = 0; sl < SLOTS; ++sl) {
       const int e = threadIdx.x + sl * T;
-      if (e < nel) pol_add(acc[sl], v[sl], s[sl], ph[sl], th[sl], pp, j);
+      if (e < nel) pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
     }
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = nxt[sl];
   }
 #pragma unroll
   for (int sl = 0; sl < SLOTS; ++sl) {
@@ -158,9 +177,9 @@ __global__ void __launch_bounds__(T) k_pol_fftx(const typename RT<R>::V4* __rest
       C out[3];
       pol_final(acc[sl], pp, out);
       if (DO_FFT) {
-        buf[e] = out[0];
-        buf[EC + e] = out[1];
-        buf[2 * EC + e] = out[2];
+        buf[padi(e)] = out[0];
+        buf[padi(EC + e)] = out[1];
+        buf[padi(2 * EC + e)] = out[2];
       } else {
         p[vox0 + e] = out[0];
         p[(size_t)N + vox0 + e] = out[1];
@@ -171,10 +190,13 @@ __global__ void __launch_bounds__(T) k_pol_fftx(const typename RT<R>::V4* __rest
   if (!DO_FFT) return;
   __syncthreads();
   const C* tw = tw_in_smem ? tws : twx;
-  block_fft<R, 3 * EC / 4 / T, 3 * EC / 2 / T, false>(buf, lognx, 3 * ROWS, -1, nx, 1, tw);
+  if constexpr (LOGNX >= 0)
+    block_fft_ct<R, LOGNX, 3 * (EC >> LOGNX), (1 << LOGNX), 1, T, false>(buf, tw);
+  else
+    block_fft<R, 3 * EC, T, false>(buf, lognx, 3 * ROWS, -1, nx, 1, tw);
 #pragma unroll
   for (int k = 0; k < 3; ++k)
-    for (int e = threadIdx.x; e < nel; e += T) p[(size_t)k * N + vox0 + e] = buf[k * EC + e];
+    for (int e = threadIdx.x; e < nel; e += T) p[(size_t)k * N + vox0 + e] = buf[padi(k * EC + e)];
 }
 
 // Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d.
@@ -186,7 +208,7 @@ __global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p
   using C = typename RT<R>::C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
-  C* tws = buf + EC;
+  C* tws = buf + padded(EC);
   const int nx = 1 << lognx;
   const int ROWS = EC >> lognx;
   const long long row0 = (long long)blockIdx.x * ROWS;
@@ -196,28 +218,33 @@ __global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p
   C* base = p + ((size_t)row0 << lognx);
   if (tw_in_smem)
     for (int i = threadIdx.x; i < nx; i += T) tws[i] = twx[i];
-  for (int e = threadIdx.x; e < nel; e += T) buf[e] = base[e];
+  for (int e = threadIdx.x; e < nel; e += T) buf[padi(e)] = base[e];
   __syncthreads();
   const C* tw = tw_in_smem ? tws : twx;
-  block_fft<R, EC / 4 / T, EC / 2 / T, false>(buf, lognx, ROWS, -1, nx, 1, tw);
-  for (int e = threadIdx.x; e < nel; e += T) base[e] = buf[e];
+  block_fft<R, EC, T, false>(buf, lognx, ROWS, -1, nx, 1, tw);
+  for (int e = threadIdx.x; e < nel; e += T) base[e] = buf[padi(e)];
 }
 
 // Column FFTs: element i of column col of batch b sits at
 //   data[b * batch_stride + i * S + tile * TX + col],  i < L = 2^logL.
 // One CTA transforms TX = 2^logTX adjacent columns (coalesced rows of TX
 // complex values) of one batch.  Used for y (S = nx, W = nx, batches =
-// 3 nz) and for z (S = W = nx ny, batches = 3).
-template <typename R, int T, int EC>
-__global__ void __launch_bounds__(T) k_col_fft(typename RT<R>::C* __restrict__ data, int logL,
-                                               long long S, int logTX, long long ntiles,
+// 3 nz) and for z (S = W = nx ny, batches = 3).  The tile arrives by
+// cp.async, NLD copies per thread in flight, without passing registers.
+template <typename R, int T, int EC, int LOGL>
+__global__ void __launch_bounds__(T, 3) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
+                                               long long S, int logTX_rt, long long ntiles,
                                                long long batch_stride,
                                                const typename RT<R>::C* __restrict__ tw_g,
                                                int tw_in_smem) {
   using C = typename RT<R>::C;
+  constexpr int NLD = EC / T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [L][TX]
-  C* tws = buf + EC;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [L][TX], padded
+  C* tws = buf + padded(EC);
+  // with LOGL fixed, TX = EC / L is fixed too
+  const int logL = LOGL >= 0 ? LOGL : logL_rt;
+  const int logTX = LOGL >= 0 ? ilog2_ct(EC >> (LOGL >= 0 ? LOGL : 0)) : logTX_rt;
   const int L = 1 << logL;
   const int TX = 1 << logTX;
   const long long tile = (long long)blockIdx.x % ntiles;
@@ -226,16 +253,22 @@ __global__ void __launch_bounds__(T) k_col_fft(typename RT<R>::C* __restrict__ d
   if (tw_in_smem)
     for (int i = threadIdx.x; i < L; i += T) tws[i] = tw_g[i];
   const int nel = L << logTX;
-  for (int e = threadIdx.x; e < nel; e += T) {
-    const int col = e & (TX - 1), i = e >> logTX;
-    buf[e] = base[(size_t)i * S + col];
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int e = threadIdx.x + it * T;
+    if (e < nel) cp_async_elem(buf + padi(e), base + (size_t)(e >> logTX) * S + (e & (TX - 1)));
   }
+  cp_async_wait_all();
   __syncthreads();
   const C* tw = tw_in_smem ? tws : tw_g;
-  block_fft<R, EC / 4 / T, EC / 2 / T, true>(buf, logL, TX, logTX, 1, TX, tw);
-  for (int e = threadIdx.x; e < nel; e += T) {
-    const int col = e & (TX - 1), i = e >> logTX;
-    base[(size_t)i * S + col] = buf[e];
+  if constexpr (LOGL >= 0)
+    block_fft_ct<R, LOGL, (EC >> LOGL), 1, (EC >> LOGL), T, true>(buf, tw);
+  else
+    block_fft<R, EC, T, true>(buf, logL, TX, logTX, 1, TX, tw);
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int e = threadIdx.x + it * T;
+    if (e < nel) base[(size_t)(e >> logTX) * S + (e & (TX - 1))] = buf[padi(e)];
   }
 }
 
@@ -320,23 +353,36 @@ __device__ __forceinline__ R proj_norm2(const typename RT<R>::C v[3], R rx, R ry
   return y0r * y0r + y0i * y0i + y1r * y1r + y1i * y1i + y2r * y2r + y2i * y2i;
 }
 
-// One thread per detector pixel (FFT order in, fftshift order out).
-// PRUNED: p holds x/y-transformed slices; the two needed q_z bins are
-// evaluated directly, p~(b) = sum_z P(z) exp(-2 pi i b z / nz), and the
-// constant removed before the FFT (N * dc at q = 0) is added back.
-// Otherwise p is the full p~ and the two bins are read.
-template <typename R, bool PRUNED>
-__global__ void __launch_bounds__(256) k_ewald(const typename RT<R>::C* __restrict__ p, int nx,
-                                               int ny, int nz, const Geo<R>* __restrict__ geo,
-                                               const typename RT<R>::C* __restrict__ twz, R dc0,
-                                               R dc1, R dc2, R* __restrict__ img) {
+// Two adjacent pixels of one row, loaded as one 16-byte vector in FP32.
+__device__ __forceinline__ void ld2(const float2* p, float2& a, float2& b) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  a = make_float2(q.x, q.y);
+  b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void ld2(const double2* p, double2& a, double2& b) {
+  a = __ldg(p);
+  b = __ldg(p + 1);
+}
+
+template <typename R>
+__device__ __forceinline__ R ewald_value(const Geo<R>& g, const typename RT<R>::C a0[3],
+                                         const typename RT<R>::C a1[3]) {
+  const R x0 = proj_norm2<R>(a0, g.rx, g.ry, g.rz);
+  const R x1 = proj_norm2<R>(a1, g.rx, g.ry, g.rz);
+  return g.k4 * ((R(1) - g.w) * x0 + g.w * x1);
+}
+
+// Full p~ given: read the two bins of each pixel (one thread per pixel).
+template <typename R>
+__global__ void __launch_bounds__(256) k_ewald_full(const typename RT<R>::C* __restrict__ p, int nx,
+                                                    int ny, int nz, const Geo<R>* __restrict__ geo,
+                                                    R* __restrict__ img) {
   using C = typename RT<R>::C;
   const long long npix = (long long)nx * ny;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
   const int mx = (int)(pix % nx), my = (int)(pix / nx);
-  const int sx = (mx + nx / 2) % nx, sy = (my + ny / 2) % ny;
-  R* dst = img + (size_t)sy * nx + sx;
+  R* dst = img + (size_t)((my + ny / 2) % ny) * nx + (mx + nx / 2) % nx;
   const Geo<R> g = geo[pix];
   if (g.b0 < 0) {
     *dst = R(0);
@@ -344,43 +390,143 @@ __global__ void __launch_bounds__(256) k_ewald(const typename RT<R>::C* __restri
   }
   const size_t N = (size_t)npix * nz;
   C a0[3], a1[3];
-  if (PRUNED) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) a0[k] = a1[k] = RT<R>::mk(0, 0);
-    int i0 = 0, i1 = 0;
-    const C* src = p + pix;
-#pragma unroll 4
-    for (int z = 0; z < nz; ++z) {
-      const C w0 = __ldg(twz + i0), w1 = __ldg(twz + i1);
+  for (int k = 0; k < 3; ++k) {
+    a0[k] = p[k * N + (size_t)g.b0 * npix + pix];
+    a1[k] = p[k * N + (size_t)g.b1 * npix + pix];
+  }
+  *dst = ewald_value<R>(g, a0, a1);
+}
+
+// Hot path: p holds x/y-transformed slices P(z).  Each thread takes two
+// adjacent pixels of a row and evaluates the two q_z bins each needs,
+//   p~(b) = sum_z P(z) exp(-2 pi i b z / nz),
+// reading ZB slices' worth of vector loads before accumulating them.  The
+// constant left out of p before the FFT returns at q = 0 as N * dc.
+template <typename R, int ZB>
+__global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* __restrict__ p,
+                                                      int nx, int ny, int nz,
+                                                      const Geo<R>* __restrict__ geo,
+                                                      const typename RT<R>::C* __restrict__ twz_g,
+                                                      int tw_in_smem, R dc0, R dc1, R dc2,
+                                                      R* __restrict__ img) {
+  using C = typename RT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  if (tw_in_smem) {
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) tws[i] = twz_g[i];
+    __syncthreads();
+  }
+  const C* twz = tw_in_smem ? tws : twz_g;
+  const long long npix = (long long)nx * ny;
+  const long long pix0 = 2 * ((long long)blockIdx.x * blockDim.x + threadIdx.x);
+  if (pix0 >= npix) return;
+  const size_t N = (size_t)npix * nz;
+  Geo<R> g[2];
+  g[0] = geo[pix0];
+  g[1] = geo[pix0 + 1];
+  C a0[2][3], a1[2][3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        const C v = __ldg(src + k * N + (size_t)z * npix);
-        a0[k] = cadd(a0[k], cmul(v, w0));
-        a1[k] = cadd(a1[k], cmul(v, w1));
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a0[q][k] = a1[q][k] = RT<R>::mk(0, 0);
+  const bool any = g[0].b0 >= 0 || g[1].b0 >= 0;
+  int i0[2] = {0, 0}, i1[2] = {0, 0};
+  const int s0[2] = {g[0].b0 < 0 ? 0 : g[0].b0, g[1].b0 < 0 ? 0 : g[1].b0};
+  const int s1[2] = {g[0].b1 < 0 ? 0 : g[0].b1, g[1].b1 < 0 ? 0 : g[1].b1};
+  const C* src = p + pix0;
+  int z = 0;
+  if (any) {
+    for (; z + ZB <= nz; z += ZB) {
+      C v[ZB][3][2];
+#pragma unroll
+      for (int u = 0; u < ZB; ++u)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ld2(src + k * N + (size_t)(z + u) * npix, v[u][k][0], v[u][k][1]);
+#pragma unroll
+      for (int u = 0; u < ZB; ++u) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const C w0 = twz[i0[q]], w1 = twz[i1[q]];
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            a0[q][k] = cadd(a0[q][k], cmul(v[u][k][q], w0));
+            a1[q][k] = cadd(a1[q][k], cmul(v[u][k][q], w1));
+          }
+          i0[q] += s0[q];
+          if (i0[q] >= nz) i0[q] -= nz;
+          i1[q] += s1[q];
+          if (i1[q] >= nz) i1[q] -= nz;
+        }
       }
-      i0 += g.b0;
-      if (i0 >= nz) i0 -= nz;
-      i1 += g.b1;
-      if (i1 >= nz) i1 -= nz;
     }
-    if (pix == 0) {
-      const R dcs[3] = {dc0, dc1, dc2};
+    for (; z < nz; ++z) {
+      C v[3][2];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        if (g.b0 == 0) a0[k].x += dcs[k];
-        if (g.b1 == 0) a1[k].x += dcs[k];
+      for (int k = 0; k < 3; ++k) ld2(src + k * N + (size_t)z * npix, v[k][0], v[k][1]);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const C w0 = twz[i0[q]], w1 = twz[i1[q]];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          a0[q][k] = cadd(a0[q][k], cmul(v[k][q], w0));
+          a1[q][k] = cadd(a1[q][k], cmul(v[k][q], w1));
+        }
+        i0[q] += s0[q];
+        if (i0[q] >= nz) i0[q] -= nz;
+        i1[q] += s1[q];
+        if (i1[q] >= nz) i1[q] -= nz;
       }
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      a0[k] = p[k * N + (size_t)g.b0 * npix + pix];
-      a1[k] = p[k * N + (size_t)g.b1 * npix + pix];
     }
   }
-  const R x0 = proj_norm2<R>(a0, g.rx, g.ry, g.rz);
-  const R x1 = proj_norm2<R>(a1, g.rx, g.ry, g.rz);
-  *dst = g.k4 * ((R(1) - g.w) * x0 + g.w * x1);
+  if (pix0 == 0) {
+    const R dcs[3] = {dc0, dc1, dc2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (g[0].b0 == 0) a0[0][k].x += dcs[k];
+      if (g[0].b1 == 0) a1[0][k].x += dcs[k];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const long long pix = pix0 + q;
+    const int mx = (int)(pix % nx), my = (int)(pix / nx);
+    R* dst = img + (size_t)((my + ny / 2) % ny) * nx + (mx + nx / 2) % nx;
+    *dst = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
+  }
+}
+
+// One thread per pixel, for a 1 x 1 detector (npix odd).
+template <typename R>
+__global__ void k_ewald_single(const typename RT<R>::C* __restrict__ p, int nz,
+                               const Geo<R>* __restrict__ geo, const typename RT<R>::C* __restrict__ twz,
+                               R dc0, R dc1, R dc2, R* __restrict__ img) {
+  using C = typename RT<R>::C;
+  const Geo<R> g = geo[0];
+  if (g.b0 < 0) {
+    img[0] = R(0);
+    return;
+  }
+  C a0[3], a1[3];
+  for (int k = 0; k < 3; ++k) a0[k] = a1[k] = RT<R>::mk(0, 0);
+  int i0 = 0, i1 = 0;
+  for (int z = 0; z < nz; ++z) {
+    for (int k = 0; k < 3; ++k) {
+      const C v = p[(size_t)k * nz + z];
+      a0[k] = cadd(a0[k], cmul(v, twz[i0]));
+      a1[k] = cadd(a1[k], cmul(v, twz[i1]));
+    }
+    i0 += g.b0;
+    if (i0 >= nz) i0 -= nz;
+    i1 += g.b1;
+    if (i1 >= nz) i1 -= nz;
+  }
+  const R dcs[3] = {dc0, dc1, dc2};
+  for (int k = 0; k < 3; ++k) {
+    if (g.b0 == 0) a0[k].x += dcs[k];
+    if (g.b1 == 0) a1[k].x += dcs[k];
+  }
+  img[0] = ewald_value<R>(g, a0, a1);
 }
 
 // ------------------------------------------------------- detector rotation
@@ -445,7 +591,7 @@ static inline int ilog2(long long n) {
 }
 static inline unsigned grid1(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <typename R, int T, int EC, bool DO_FFT>
+template <typename R, int T, int EC, bool DO_FFT, int LOGNX>
 static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                                  void* p, const void* twx, cudaStream_t s) {
   using C = typename RT<R>::C;
@@ -454,13 +600,13 @@ static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const Po
   const int lognx = DO_FFT ? ilog2(nx) : 0;
   const long long nrows = DO_FFT ? (long long)ny * nz : N;
   const int rows = DO_FFT ? EC / nx : EC;
-  size_t smem = DO_FFT ? 3 * EC * sizeof(C) : 0;
+  size_t smem = DO_FFT ? padded(3 * EC) * sizeof(C) : 0;
   int tw_in_smem = 0;
   if (DO_FFT && smem + nx * sizeof(C) <= 200 * 1024) {
     smem += nx * sizeof(C);
     tw_in_smem = 1;
   }
-  auto kern = k_pol_fftx<R, T, EC, DO_FFT>;
+  auto kern = k_pol_fftx<R, T, EC, DO_FFT, LOGNX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid1(nrows, rows), T, smem, s>>>((const typename RT<R>::V4*)M, N, lognx, nrows, pp,
@@ -471,15 +617,22 @@ static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const Po
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                             bool do_fft, void* p, const void* twx, cudaStream_t s) {
-  if (!do_fft) return pol_fftx_impl<R, 256, 1024, false>(M, nx, ny, nz, pp, p, twx, s);
-  if (nx <= 2048) return pol_fftx_impl<R, 256, 2048, true>(M, nx, ny, nz, pp, p, twx, s);
-  return pol_fftx_impl<R, 512, 4096, true>(M, nx, ny, nz, pp, p, twx, s);
+  if (!do_fft) return pol_fftx_impl<R, 256, 1024, false, -1>(M, nx, ny, nz, pp, p, twx, s);
+#define RSX_POL(L) \
+  case L: return pol_fftx_impl<R, 256, 1024, true, L>(M, nx, ny, nz, pp, p, twx, s);
+  switch (ilog2(nx)) {
+    RSX_POL(6) RSX_POL(7) RSX_POL(8) RSX_POL(9) RSX_POL(10)
+    case 11: return pol_fftx_impl<R, 256, 2048, true, 11>(M, nx, ny, nz, pp, p, twx, s);
+    case 12: return pol_fftx_impl<R, 512, 4096, true, 12>(M, nx, ny, nz, pp, p, twx, s);
+    default: return pol_fftx_impl<R, 256, 1024, true, -1>(M, nx, ny, nz, pp, p, twx, s);
+  }
+#undef RSX_POL
 }
 
 template <typename R, int T, int EC>
 static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* twx, cudaStream_t s) {
   using C = typename RT<R>::C;
-  size_t smem = EC * sizeof(C);
+  size_t smem = padded(EC) * sizeof(C);
   int tw_in_smem = 0;
   if (smem + nx * sizeof(C) <= 200 * 1024) {
     smem += nx * sizeof(C);
@@ -498,22 +651,24 @@ cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cu
   return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s);
 }
 
-template <typename R, int T, int EC>
+template <typename R, int T, int EC, int LOGL>
 static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long long nbatch,
                                 long long batch_stride, const void* tw, cudaStream_t s) {
   using C = typename RT<R>::C;
+  if (L > EC) return cudaErrorInvalidValue;
   long long TX = EC / L;
   if (TX > W) TX = W;
   if (TX < 1) TX = 1;
+  if (LOGL >= 0 && TX != EC / L) return cudaErrorInvalidValue;
   const int logTX = ilog2(TX);
   const long long ntiles = W / TX;
-  size_t smem = (size_t)EC * sizeof(C);
+  size_t smem = (size_t)padded(EC) * sizeof(C);
   int tw_in_smem = 0;
   if (smem + L * sizeof(C) <= 200 * 1024) {
     smem += L * sizeof(C);
     tw_in_smem = 1;
   }
-  auto kern = k_col_fft<R, T, EC>;
+  auto kern = k_col_fft<R, T, EC, LOGL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(ntiles * nbatch), T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles,
@@ -521,12 +676,28 @@ static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long l
   return cudaGetLastError();
 }
 
+template <typename R, int EC>
+static cudaError_t col_fft_dispatch(void* p, int L, long long S, long long W, long long nbatch,
+                                    long long batch_stride, const void* tw, cudaStream_t s) {
+  const int logL = ilog2(L);
+  if (W >= EC / L) {
+    switch (logL) {
+#define RSX_COL(LL) \
+  case LL: return col_fft_impl<R, 256, EC, LL>(p, L, S, W, nbatch, batch_stride, tw, s);
+      RSX_COL(5) RSX_COL(6) RSX_COL(7) RSX_COL(8) RSX_COL(9) RSX_COL(10) RSX_COL(11) RSX_COL(12)
+#undef RSX_COL
+      default: break;
+    }
+  }
+  return col_fft_impl<R, 256, EC, -1>(p, L, S, W, nbatch, batch_stride, tw, s);
+}
+
 template <typename R>
 cudaError_t launch_col_fft(void* p, int L, long long S, long long W, long long nbatch,
                            long long batch_stride, const void* tw, cudaStream_t s) {
   if (L == 1) return cudaSuccess;
-  if (sizeof(R) == 4) return col_fft_impl<R, 512, 8192>(p, L, S, W, nbatch, batch_stride, tw, s);
-  return col_fft_impl<R, 512, 4096>(p, L, S, W, nbatch, batch_stride, tw, s);
+  // 4096 elements per CTA: 34 KB (FP32) or 70 KB (FP64) of padded tile
+  return col_fft_dispatch<R, 4096>(p, L, S, W, nbatch, batch_stride, tw, s);
 }
 
 template <typename R>
@@ -551,12 +722,19 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
                          const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s) {
   using C = typename RT<R>::C;
   const long long npix = (long long)nx * ny;
-  if (pruned)
-    k_ewald<R, true><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo, (const C*)twz,
-                                                       dc[0], dc[1], dc[2], (R*)img);
-  else
-    k_ewald<R, false><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo,
-                                                        (const C*)twz, dc[0], dc[1], dc[2], (R*)img);
+  if (!pruned) {
+    k_ewald_full<R><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo, (R*)img);
+    return cudaGetLastError();
+  }
+  if (npix == 1) {
+    k_ewald_single<R><<<1, 1, 0, s>>>((const C*)p, nz, geo, (const C*)twz, dc[0], dc[1], dc[2],
+                                      (R*)img);
+    return cudaGetLastError();
+  }
+  const int tw_in_smem = nz <= 4096;
+  const size_t smem = tw_in_smem ? nz * sizeof(C) : 0;
+  k_ewald_pruned<R, 4><<<grid1(npix / 2, 256), 256, smem, s>>>(
+      (const C*)p, nx, ny, nz, geo, (const C*)twz, tw_in_smem, dc[0], dc[1], dc[2], (R*)img);
   return cudaGetLastError();
 }
 
