@@ -171,6 +171,35 @@ int rsx_rotate_accumulate(rsx_context* ctx, const void* img, double alpha_rad, v
 int rsx_scatter_angle(rsx_context* ctx, int energy_index, double alpha_rad, void* img_out,
                       void* stream);
 
+/* ---- allocation-free variant of rsx_scatter_angle --------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that cannot allocate device memory themselves (code running inside another
+ * framework's memory pool, or hosts where cudaMalloc is not allowed after
+ * start-up) and so cannot create a context.  It computes the same unrotated
+ * detector image as rsx_scatter_angle for one energy and one e-field angle,
+ * in FP32, and calls no cudaMalloc, cudaFree or allocating library routine:
+ * its working memory (p, the Ewald geometry and the FFT twiddles) is one
+ * fixed array of about 26 MiB inside the library, which every GPU that loads
+ * the library holds until the process exits.
+ *  - Limits: nx and ny powers of two <= 4096, nz <= 4096,
+ *    nx*ny*nz <= RSX_NOALLOC_MAX_VOXELS and nx*ny <= RSX_NOALLOC_MAX_PIXELS;
+ *    larger grids return RSX_ERR_INVALID with a message.
+ *  - M: device, [c][nz][ny][nx] float4 (v, s, phi, theta), 16-byte aligned.
+ *    constants: host, [c][4] double (delta_par, beta_par, delta_perp,
+ *    beta_perp) at energy_ev.  img_out: device, [ny][nx] float, fftshift
+ *    order.  frame: RSX_FRAME_LITERAL or RSX_FRAME_LAB.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same array and leaves its contents behind (each
+ *    call rewrites everything it reads).  Calls whose GPU work overlaps (on
+ *    different streams or threads) race on it: serialise them. */
+#define RSX_NOALLOC_MAX_VOXELS (1 << 20)
+#define RSX_NOALLOC_MAX_PIXELS (1 << 16)
+int rsx_scatter_angle_noalloc(const void* M, int nx, int ny, int nz, int n_components,
+                              double voxel_nm, double energy_ev, const double* constants,
+                              double alpha_rad, int frame, void* img_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

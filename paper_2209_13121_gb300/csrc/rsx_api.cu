@@ -90,6 +90,11 @@ size_t geo_size(int precision) {
 
 }  // namespace
 
+namespace rsx {
+// Lets other translation units of the library report through rsx_last_error.
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace rsx
+
 struct rsx_context {
   rsx_config cfg{};
   int dev = 0;

@@ -32,6 +32,9 @@ template <typename R> struct __align__(16) Geo {
   R w, rx, ry, rz, k4;
 };
 
+// Sets the message returned by rsx_last_error() on this host thread.
+void set_last_error(const char* msg);
+
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                             bool do_fft, void* p, const void* twx, cudaStream_t s);

@@ -31,8 +31,10 @@ EXPORTED = (
     "rsx_create", "rsx_destroy", "rsx_last_error", "rsx_workspace_bytes", "rsx_angle_count",
     "rsx_set_morphology", "rsx_set_optical_constants", "rsx_run", "rsx_polarization",
     "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
-    "rsx_set_timing", "rsx_phase_times",
+    "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc",
 )
+NOALLOC_MAX_VOXELS = 1 << 20
+NOALLOC_MAX_PIXELS = 1 << 16
 PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other")
 
 
@@ -77,6 +79,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "rsx_scatter_angle": (ci, [vp, ci, cd, vp, vp]),
         "rsx_set_timing": (ci, [vp, ci]),
         "rsx_phase_times": (ci, [vp, vp, vp]),
+        "rsx_scatter_angle_noalloc": (ci, [vp, ci, ci, ci, ci, cd, cd, vp, cd, ci, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -256,6 +259,24 @@ class Context:
         _check(lib().rsx_scatter_angle(self._h, int(energy_index), float(alpha_rad),
                                        ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
         return img_out
+
+
+def scatter_angle_noalloc(M, energy_ev, constants, alpha_rad, img_out, voxel_nm,
+                          frame=RSX_FRAME_LITERAL, stream=None):
+    """rsx_scatter_angle_noalloc: the unrotated FP32 detector image for one
+    energy and angle, without any device allocation (fixed in-library
+    scratch; see include/rsx.h for the size limits).  M: contiguous float32
+    CUDA tensor [c][nz][ny][nx][4]; constants: [c][4]; img_out: float32 CUDA
+    tensor [ny][nx]."""
+    c, nz, ny, nx, four = M.shape
+    if four != 4 or not M.is_contiguous() or tuple(img_out.shape) != (ny, nx):
+        raise ValueError("M must be [c][nz][ny][nx][4] contiguous and img_out [ny][nx]")
+    K = np.ascontiguousarray(constants, dtype=np.float64).reshape(c, 4)
+    _check(lib().rsx_scatter_angle_noalloc(
+        ctypes.c_void_p(M.data_ptr()), nx, ny, nz, c, float(voxel_nm), float(energy_ev),
+        K.ctypes.data_as(ctypes.c_void_p), float(alpha_rad), int(frame),
+        ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
+    return img_out
 
 
 def deg2rad_list(start, inc, end, rotation=True):
