@@ -35,6 +35,9 @@ WORKLOADS = {
     # Sec. 6.2 material scaling (2048^2 x 64)
     "p2-2048": dict(shape=(64, 2048, 2048), c=4, angles=(0.0, 2.0, 180.0)),
     "p0-small": dict(shape=(16, 128, 128), c=4, angles=(0.0, 2.0, 180.0)),
+    # P1's lateral size with a shorter stack: the same kernel shapes in ~3 GB,
+    # small enough for full ncu captures
+    "p1-1024-z32": dict(shape=(32, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0)),
 }
 VOXEL_NM = 5.0
 METRIC = "P-RSoXS Algorithm 1 voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s')"
@@ -144,9 +147,12 @@ def run_ours(args):
     real = 4 if prec == 32 else 8
     n_ang = rsx.angle_count(*W["angles"])
     n_steps = args.warmup + args.steps
-    # 150 energies over 270..320 eV (Sec. 6.1); rank r takes every ws-th.
+    # 150 energies over 270..320 eV (Sec. 6.1), sharded across ranks with no
+    # data-path collective; each step is one energy of this rank's shard.
+    from paper_2209_13121_gb300.shard import energy_shard
     energies_all = synth.energies_uniform(150)
-    mine = [energies_all[(rank + ws * i) % 150] for i in range(n_steps)]
+    shard = energy_shard(150, rank, ws, "strided")
+    mine = [energies_all[shard[i % len(shard)]] for i in range(n_steps)]
     K = synth.optical_constants(mine, c, seed=2)
     M = synth.morphology_random_torch((nz, ny, nx), c, seed=1, device="cuda",
                                       dtype=torch.float32 if prec == 32 else torch.float64)

@@ -106,6 +106,7 @@ struct rsx_context {
   void* img = nullptr;  // one detector image
   void* acc = nullptr;  // running sum of rotated images
   void* geo = nullptr;  // per-pixel Ewald geometry of energy geo_energy
+  void* bins = nullptr; // 3 components x 2 q_z bins per pixel (fused y/z path)
   int geo_energy = -1;
   void* twx = nullptr;
   void* twy = nullptr;
@@ -124,7 +125,8 @@ struct rsx_context {
 namespace {
 
 void free_all(rsx_context* c) {
-  void* ptrs[] = {c->M_owned, c->p, c->img, c->acc, c->geo, c->twx, c->twy, c->twz, c->flag};
+  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,
+                  c->bins,    c->twx, c->twy, c->twz, c->flag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -237,12 +239,6 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
            "polarisation + x-FFT kernel");
   }
-  if (g.ny > 1) {
-    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-    RSX_CK(rsx::launch_col_fft<R>(c->p, g.ny, g.nx, g.nx, 3LL * g.nz, (long long)g.nx * g.ny,
-                                  c->twy, s),
-           "y-FFT kernel");
-  }
   // The constant -(c-1) e' / (4 pi) left out of p before the FFT returns at
   // q = 0 as N times itself (e' = x-hat in the literal frame, e otherwise).
   const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
@@ -251,6 +247,24 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     dc[0] = (R)ref; dc[1] = (R)0; dc[2] = (R)0;
   } else {
     dc[0] = (R)(ref * cos(alpha)); dc[1] = (R)(ref * sin(alpha)); dc[2] = (R)0;
+  }
+  if (rsx::yz_fused_supported<R>(g.nx, g.ny, g.nz)) {
+    {
+      PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+      RSX_CK(rsx::launch_fft_y_zbins<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twy,
+                                        c->twz, c->bins, s),
+             "y-FFT + q_z kernel");
+    }
+    PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+    RSX_CK(rsx::launch_ewald_bins<R>(c->bins, g.nx, g.ny, (const Geo<R>*)c->geo, dc, img, s),
+           "Ewald kernel");
+    return RSX_OK;
+  }
+  if (g.ny > 1) {
+    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+    RSX_CK(rsx::launch_col_fft<R>(c->p, g.ny, g.nx, g.nx, 3LL * g.nz, (long long)g.nx * g.ny,
+                                  c->twy, s),
+           "y-FFT kernel");
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
   RSX_CK(rsx::launch_ewald<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, true, dc, img,
@@ -304,6 +318,7 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
   b += 3 * (size_t)N * Cs;                           // p_x, p_y, p_z (Table 1: 6 N)
   b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
   b += (size_t)npix * geo_size(cfg->precision);
+  b += 6 * (size_t)npix * Cs;                        // two q_z bins x 3 components
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
   return b;
 }
@@ -341,6 +356,7 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
       {&c->img, (size_t)c->npix * R, "Ewald image"},
       {&c->acc, (size_t)c->npix * R, "Ewald average"},
       {&c->geo, (size_t)c->npix * geo_size(cfg->precision), "Ewald geometry"},
+      {&c->bins, 6 * (size_t)c->npix * Cs, "q_z bins"},
       {(void**)&c->flag, sizeof(int), "validation flag"},
   };
   for (auto& a : allocs) {

@@ -529,6 +529,136 @@ __global__ void k_ewald_single(const typename RT<R>::C* __restrict__ p, int nz,
   img[0] = ewald_value<R>(g, a0, a1);
 }
 
+// ------------------------------------------- y-FFT fused with the pruned z
+// One CTA owns a tile of TX = EC / ny adjacent x-columns of one component
+// for every z.  For each slice it transforms the tile along y in shared
+// memory and adds its contribution to the two q_z bins each pixel needs,
+//   acc_b += P(z) exp(-2 pi i b z / nz),  b = b0, b0 + 1,
+// keeping the accumulators in registers across the slices, so the
+// y-transformed data never go back to memory.  Slices arrive by cp.async
+// NBUF - 1 ahead of the one being transformed.  Output: bins[k][2][npix]
+// (FFT order), combined into the image by k_ewald_bins.
+template <typename R, int T, int EC, int LOGL, int NBUF>
+__global__ void __launch_bounds__(T, 2) k_fft_y_zbins(const typename RT<R>::C* __restrict__ p,
+                                                      int nx, int nz,
+                                                      const Geo<R>* __restrict__ geo,
+                                                      const typename RT<R>::C* __restrict__ twy_g,
+                                                      const typename RT<R>::C* __restrict__ twz_g,
+                                                      typename RT<R>::C* __restrict__ bins) {
+  using C = typename RT<R>::C;
+  constexpr int L = 1 << LOGL;
+  constexpr int TX = EC >> LOGL;
+  constexpr int LOGTX = ilog2_ct(TX);
+  constexpr int NE = EC / T;
+  constexpr int PB = padded(EC);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // NBUF tiles [L][TX], padded
+  C* twy = buf + NBUF * PB;
+  C* twz = twy + L;
+  const int ntiles = nx / TX;
+  const int tile = blockIdx.x % ntiles;
+  const int k = blockIdx.x / ntiles;
+  const size_t npix = (size_t)nx * L;
+  const size_t N = npix * nz;
+  const C* src = p + k * N + (size_t)tile * TX;
+
+  for (int i = threadIdx.x; i < L; i += T) twy[i] = twy_g[i];
+  for (int i = threadIdx.x; i < nz; i += T) twz[i] = twz_g[i];
+
+  auto issue = [&](int z, int slot) {
+    C* dst = buf + slot * PB;
+    const C* s = src + (size_t)z * npix;
+#pragma unroll
+    for (int it = 0; it < NE; ++it) {
+      const int e = threadIdx.x + it * T;
+      cp_async_elem(dst + padi(e), s + (size_t)(e >> LOGTX) * nx + (e & (TX - 1)));
+    }
+  };
+
+  // the lower bin of each owned pixel lives in shared memory, its running
+  // twiddle index and the two accumulators in registers
+  int* b0s = reinterpret_cast<int*>(twz + nz);
+  int i0[NE];
+  C a0[NE], a1[NE];
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = threadIdx.x + it * T;
+    const size_t pix = (size_t)(e >> LOGTX) * nx + (size_t)tile * TX + (e & (TX - 1));
+    const int g = geo[pix].b0;
+    b0s[e] = g < 0 ? 0 : g;
+    i0[it] = 0;
+    a0[it] = a1[it] = RT<R>::mk(0, 0);
+  }
+#pragma unroll
+  for (int z = 0; z < NBUF - 1; ++z) {
+    if (z < nz) issue(z, z);
+    cp_async_commit();
+  }
+  for (int z = 0; z < nz; ++z) {
+    cp_async_wait<NBUF - 2>();
+    __syncthreads();  // slice z landed for all threads; slot (z-1) % NBUF is free
+    if (z + NBUF - 1 < nz) issue(z + NBUF - 1, (z + NBUF - 1) % NBUF);
+    cp_async_commit();
+    C* cur = buf + (z % NBUF) * PB;
+    block_fft_ct<R, LOGL, TX, 1, TX, T, true>(cur, twy);
+    const C wz = twz[z];
+#pragma unroll
+    for (int it = 0; it < NE; ++it) {
+      const int e = threadIdx.x + it * T;
+      const C v = cur[padi(e)];
+      const C w0 = twz[i0[it]];
+      const C w1 = cmul(w0, wz);  // exp(-2 pi i (b0 + 1) z / nz)
+      a0[it] = cadd(a0[it], cmul(v, w0));
+      a1[it] = cadd(a1[it], cmul(v, w1));
+      i0[it] += b0s[e];
+      if (i0[it] >= nz) i0[it] -= nz;
+    }
+  }
+  C* out0 = bins + (size_t)(2 * k) * npix;
+  C* out1 = out0 + npix;
+#pragma unroll
+  for (int it = 0; it < NE; ++it) {
+    const int e = threadIdx.x + it * T;
+    const size_t pix = (size_t)(e >> LOGTX) * nx + (size_t)tile * TX + (e & (TX - 1));
+    out0[pix] = a0[it];
+    out1[pix] = a1[it];
+  }
+}
+
+// Eqs. (3Dscatter) and (Ewald) from the two accumulated bins per pixel, with
+// the constant removed before the FFT added back at q = 0.
+template <typename R>
+__global__ void __launch_bounds__(256) k_ewald_bins(const typename RT<R>::C* __restrict__ bins, int nx,
+                                                    int ny, const Geo<R>* __restrict__ geo, R dc0,
+                                                    R dc1, R dc2, R* __restrict__ img) {
+  using C = typename RT<R>::C;
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const int mx = (int)(pix % nx), my = (int)(pix / nx);
+  R* dst = img + (size_t)((my + ny / 2) % ny) * nx + (mx + nx / 2) % nx;
+  const Geo<R> g = geo[pix];
+  if (g.b0 < 0) {
+    *dst = R(0);
+    return;
+  }
+  C a0[3], a1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    a0[k] = bins[(size_t)(2 * k) * npix + pix];
+    a1[k] = bins[(size_t)(2 * k + 1) * npix + pix];
+  }
+  if (pix == 0) {
+    const R dcs[3] = {dc0, dc1, dc2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (g.b0 == 0) a0[k].x += dcs[k];
+      if (g.b1 == 0) a1[k].x += dcs[k];
+    }
+  }
+  *dst = ewald_value<R>(g, a0, a1);
+}
+
 // ------------------------------------------------------- detector rotation
 // acc(Q) += img(U(alpha) Q), bilinear, zero outside; pixel coordinates in
 // fftshift order with centre (nx/2, ny/2) and the q-spacing ratio nx/ny.
@@ -738,6 +868,56 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
   return cudaGetLastError();
 }
 
+template <typename R, int T, int EC, int LOGL, int NBUF>
+static cudaError_t yz_impl(const void* p, int nx, int nz, const Geo<R>* geo, const void* twy,
+                           const void* twz, void* bins, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  constexpr int L = 1 << LOGL;
+  constexpr int TX = EC / L;
+  const size_t smem = ((size_t)NBUF * padded(EC) + L + nz) * sizeof(C) + EC * sizeof(int);
+  auto kern = k_fft_y_zbins<R, T, EC, LOGL, NBUF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)((nx / TX) * 3), T, smem, s>>>((const C*)p, nx, nz, geo, (const C*)twy,
+                                                 (const C*)twz, (C*)bins);
+  return cudaGetLastError();
+}
+
+template <typename R>
+bool yz_fused_supported(int nx, int ny, int nz) {
+  constexpr int EC = 2048;
+  if (ny < 32 || ny > EC || nz > 4096) return false;
+  return nx >= EC / ny;
+}
+
+template <typename R>
+cudaError_t launch_fft_y_zbins(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
+                               const void* twy, const void* twz, void* bins, cudaStream_t s) {
+  if (!yz_fused_supported<R>(nx, ny, nz)) return cudaErrorInvalidValue;
+  constexpr int EC = 2048;
+  constexpr int NB = sizeof(R) == 4 ? 3 : 2;
+  switch (ilog2(ny)) {
+#define RSX_YZ(LL) \
+  case LL: return yz_impl<R, 256, EC, LL, NB>(p, nx, nz, geo, twy, twz, bins, s);
+    RSX_YZ(5) RSX_YZ(6) RSX_YZ(7) RSX_YZ(8) RSX_YZ(9) RSX_YZ(10) RSX_YZ(11)
+#undef RSX_YZ
+    case 12:
+      if constexpr (EC >= 4096) return yz_impl<R, 256, EC, 12, NB>(p, nx, nz, geo, twy, twz, bins, s);
+      return cudaErrorInvalidValue;
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+template <typename R>
+cudaError_t launch_ewald_bins(const void* bins, int nx, int ny, const Geo<R>* geo, const R dc[3],
+                              void* img, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  k_ewald_bins<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>((const C*)bins, nx, ny, geo, dc[0],
+                                                                 dc[1], dc[2], (R*)img);
+  return cudaGetLastError();
+}
+
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s) {
@@ -773,7 +953,12 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
   template cudaError_t launch_rotate_acc<R>(const void*, void*, int, int, double, bool,           \
                                             cudaStream_t);                                        \
   template cudaError_t launch_scale<R>(const void*, void*, long long, double, cudaStream_t);      \
-  template cudaError_t launch_validate<R>(const void*, long long, int*, cudaStream_t);
+  template cudaError_t launch_validate<R>(const void*, long long, int*, cudaStream_t);          \
+  template bool yz_fused_supported<R>(int, int, int);                                             \
+  template cudaError_t launch_fft_y_zbins<R>(const void*, int, int, int, const Geo<R>*,           \
+                                             const void*, const void*, void*, cudaStream_t);      \
+  template cudaError_t launch_ewald_bins<R>(const void*, int, int, const Geo<R>*, const R*, void*, \
+                                            cudaStream_t);
 
 RSX_INSTANTIATE(float)
 RSX_INSTANTIATE(double)

@@ -52,6 +52,15 @@ cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm
 template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
                          const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s);
+// y-FFT fused with the pruned z transform (sizes where it is built) and the
+// image from its per-pixel bins.
+template <typename R> bool yz_fused_supported(int nx, int ny, int nz);
+template <typename R>
+cudaError_t launch_fft_y_zbins(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
+                               const void* twy, const void* twz, void* bins, cudaStream_t s);
+template <typename R>
+cudaError_t launch_ewald_bins(const void* bins, int nx, int ny, const Geo<R>* geo, const R dc[3],
+                              void* img, cudaStream_t s);
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s);

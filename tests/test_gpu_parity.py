@@ -86,6 +86,9 @@ CASES = [
     ((2, 1, 8), 2),       # ny = 1
     ((1, 1, 1), 1),       # single voxel
     ((7, 4, 2048), 2),    # nx at the x-FFT tile size, ragged nz
+    ((6, 32, 128), 3),    # fused y-FFT + q_z kernel, ragged nz
+    ((9, 128, 64), 2),    # fused, odd nz
+    ((3, 256, 32), 4),    # fused, tall tile
 ]
 IDS = ["x".join(map(str, s)) + f"c{c}" for s, c in CASES]
 
