@@ -40,7 +40,7 @@ WORKLOADS = {
     "p1-1024-z32": dict(shape=(32, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0)),
 }
 VOXEL_NM = 5.0
-METRIC = "P-RSoXS Algorithm 1 voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s')"
+METRIC = "P-RSoXS voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s')"
 UNIT = "Gvoxel-angle/s"
 
 
@@ -116,12 +116,6 @@ def _dist():
     return ws, rank, local
 
 
-def _alg_bytes_pol_fftx(c, real):
-    """Algorithmic bytes per voxel of the polarisation + x-FFT kernel: read
-    the morphology (4 Real per component), write p once (3 complex)."""
-    return c * 4 * real + 3 * 2 * real
-
-
 def run_ours(args):
     import numpy as np
     import torch
@@ -156,7 +150,7 @@ def run_ours(args):
     K = synth.optical_constants(mine, c, seed=2)
     M = synth.morphology_random_torch((nz, ny, nx), c, seed=1, device="cuda",
                                       dtype=torch.float32 if prec == 32 else torch.float64)
-    ctx = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec)
+    ctx = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm)
     ctx.set_morphology(M)
     ctx.set_optical_constants(mine, K)
     out = torch.empty((1, ny, nx), device="cuda", dtype=M.dtype)
@@ -199,9 +193,20 @@ def run_ours(args):
     # roofline of the dominant kernel (polarisation + x-FFT), timed live
     top = max(phases, key=lambda k: phases[k][0])
     peak, peak_kind = _peaks()
-    bytes_per_voxel = {"pol_fftx": _alg_bytes_pol_fftx(c, real), "ffty": 3 * 2 * 2 * real,
-                       "ewald": 3 * 2 * real, "rotate": 0, "other": 0}[top]
+    cplx = 2 * real
+    if args.algorithm == 3:
+        # per energy: copy N_t (5 fields) + x-FFT; y-FFT; q_z bins (read 5 fields)
+        per_voxel = {"pol_fftx": 4 * 5 * cplx, "ffty": 2 * 5 * cplx, "ewald": 5 * cplx,
+                     "rotate": 0, "other": 0, "nt": c * 4 * real + 5 * cplx}
+    else:
+        src_bytes = c * 4 * real if args.algorithm == 1 else 5 * cplx  # M, or N_t's 5 entries
+        per_voxel = {"pol_fftx": src_bytes + 3 * cplx, "ffty": 2 * 3 * cplx, "ewald": 3 * cplx,
+                     "rotate": 0, "other": 0, "nt": c * 4 * real + 5 * cplx}
+    bytes_per_voxel = per_voxel[top]
     t_ms, n_l = phases[top]
+    if args.algorithm == 3 and top == "ewald":
+        # the ewald phase mixes one q_z reduction per energy with light per-angle kernels
+        n_l = args.steps
     achieved = (bytes_per_voxel * N * n_l) / (t_ms / 1e3) / 1e9 if bytes_per_voxel else None
     traffic = _traffic_from_profiles(args.workload, top, prec)
 
@@ -212,7 +217,7 @@ def run_ours(args):
         Mh.copy_(M)
         Mh_np = Mh.numpy()
         host_out = np.empty((1, ny, nx), dtype=np.float32 if prec == 32 else np.float64)
-        ctx_h = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec)
+        ctx_h = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm)
         ctx_h.set_optical_constants(mine, K)
         del M
         ctx.close()
@@ -247,7 +252,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
-            "config": {"workload": f"{args.workload}: Algorithm 1, {nx}x{ny}x{nz} voxels, "
+            "config": {"workload": f"{args.workload}: Algorithm {args.algorithm}, {nx}x{ny}x{nz} voxels, "
                                    f"c={c}, 91 e-field angles 0:2:180 per energy, one energy "
                                    f"per step (of 150 over 270-320 eV)",
                        "voxels": N, "components": c, "angles_per_energy": n_ang,
@@ -344,6 +349,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="p1-1024", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", type=int, default=32, choices=[32, 64])
+    ap.add_argument("--algorithm", type=int, default=1, choices=[1, 2, 3],
+                    help="1: Algorithm 1 (headline); 2: Algorithm 2 (N_t); 3: Algorithm 2 "
+                         "restated by linearity (five FFTs per energy), reported beside")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -65,6 +65,9 @@ typedef struct rsx_config {
   int precision;      /* 32 (float) or 64 (double)                          */
   int algorithm;      /* 1: communication-minimising (Algorithm 1)          */
                       /* 2: memory-minimising via N_t (Algorithms 2 and 3)  */
+                      /* 3: Algorithm 2 restated by linearity: p~(alpha) =  */
+                      /*    cos a FFT(N_t x) + sin a FFT(N_t y), five FFTs  */
+                      /*    per energy instead of three per angle (exact)   */
   int frame;          /* RSX_FRAME_LITERAL or RSX_FRAME_LAB                 */
   int validate;       /* nonzero: rsx_set_morphology rejects v or s outside */
                       /* [0, 1] and non-finite angles (Sec. 3.1); the sum   */
@@ -99,7 +102,10 @@ int rsx_angle_count(double start_deg, double increment_deg, double end_deg, int 
 
 /* Morphology M (Sec. 4.1, Fig. 3): [c][nz][ny][nx] entries of 4 Real
  * (v_frac, s, phi, theta), component-major; phi and theta in radians.
- * where = RSX_HOST: copied into the context (one copy, Algorithm 1).
+ * where = RSX_HOST: Algorithm 1 copies it into the context once.  Algorithms
+ *   2 and 3 borrow it and stream one component at a time to the GPU for each
+ *   energy (Algorithm 3 of the paper), so it must stay valid until the last
+ *   run; pinned memory lets the copies overlap the N_t kernel.
  * where = RSX_DEVICE: borrowed, not copied; the pointer must stay valid and
  *   unchanged until the last run that uses it has finished, and must be
  *   aligned to 4 * sizeof(Real).
@@ -132,7 +138,8 @@ int rsx_run(rsx_context* ctx, double start_deg, double increment_deg, double end
 #define RSX_PHASE_EWALD 2    /* pruned q_z transform + scatter + Ewald        */
 #define RSX_PHASE_ROTATE 3   /* detector rotation and accumulation            */
 #define RSX_PHASE_OTHER 4    /* geometry, averaging, validation, z/x FFTs     */
-#define RSX_N_PHASES 5
+#define RSX_PHASE_NT 5       /* N_t of Algorithm 3 (Algorithm 2 contexts)     */
+#define RSX_N_PHASES 6
 
 /* enable != 0: every kernel the context launches from now on is bracketed by
  * two CUDA events on its stream (a few microseconds each); 0 stops that. */
@@ -144,6 +151,14 @@ int rsx_set_timing(rsx_context* ctx, int enable);
 int rsx_phase_times(rsx_context* ctx, double* ms, long long* launches);
 
 /* ---- single steps of the path (device buffers), for checking each row -- */
+
+/* Algorithm 3 (NrComputation, Sec. 4.3) for one energy, in a context made
+ * with algorithm 2 or 3: N_t = sum_j (N_rot^j N_rot^j - I) / (4 pi), written as
+ * nt_out[5][nz][ny][nx] complex = entries xx, xy, yy, xz, yz (N_t is
+ * complex symmetric; zz is never used because e lies in the x-y plane).
+ * A host morphology is streamed per component, as in Algorithm 3.
+ * RSX_ERR_STATE for an algorithm 1 context. */
+int rsx_nt(rsx_context* ctx, int energy_index, void* nt_out, void* stream);
 
 /* Eqs. (ncorr), (nrot), (polarization) and p <- U^T p for one energy and
  * e-field angle alpha (radians): p_out [3][nz][ny][nx] complex. */

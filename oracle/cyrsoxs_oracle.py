@@ -15,6 +15,9 @@ Every step follows the paper in its own order and notation:
   Sec. 3.3 step 5  scatter                             Eq. (3Dscatter)
   Sec. 3.3 step 6  Ewald projection + interpolation    Eq. (Ewald)
   Sec. 4           detector rotation and average      Algorithm 1
+  Sec. 4.3         N_t per energy, p = N_t . e         Algorithms 2 and 3
+  linearity        p~(alpha) from FFTs of N_t's columns  (exact restatement
+                   of Algorithm 2: e(alpha) = cos a x + sin a y, FFT linear)
 
 Readings of points the paper leaves open (the design notes list the same):
 
@@ -277,6 +280,81 @@ def run_alg1(M, constants, energies, voxel_nm, angles_deg=(0.0, 1.0, 0.0),
         acc = np.zeros((Ny, Nx))
         for a in alphas:
             img = scatter_one_angle(M, constants[i], energies[i], voxel_nm, a, uT_mode)
+            acc += rotate_image(img, a) if rotation else img
+        out[o] = acc / len(alphas)
+    return out
+
+
+# ------------------------------------------------------ Sec. 4.3 (Alg. 2, 3)
+def nr_computation(M: np.ndarray, nt: np.ndarray, chunk: int = 1 << 18) -> np.ndarray:
+    """Algorithm 3 (NrComputation): per voxel, loop over the components and
+    accumulate N_t += (N_r^j N_r^j - I) / (4 pi), with N_r^j from Eqs. (ncorr)
+    and (nrot).  Returns N_t as [Nz][Ny][Nx][3][3] complex128."""
+    c = M.shape[0]
+    grid = M.shape[1:4]
+    nvox = int(np.prod(grid))
+    Mf = M.reshape(c, nvox, 4)
+    Nt = np.zeros((nvox, 3, 3), dtype=np.complex128)
+    I3 = np.eye(3)
+    for j in range(c):
+        N = refractive_tensor(*[float(x) for x in nt[j]])
+        for lo in range(0, nvox, chunk):
+            hi = min(nvox, lo + chunk)
+            blk = Mf[j, lo:hi].astype(np.float64)
+            N_rot = rotated_tensor(effective_tensor(N, blk[:, 0], blk[:, 1]),
+                                   euler_R(blk[:, 2], blk[:, 3]))
+            Nt[lo:hi] += (N_rot @ N_rot - I3[None]) / (4.0 * math.pi)
+    return Nt.reshape(grid + (3, 3))
+
+
+def polarization_from_nt(Nt: np.ndarray, e: np.ndarray) -> np.ndarray:
+    """Algorithm 2: p(x) = N_t(x) . e_rot, returned as [3][Nz][Ny][Nx]."""
+    return np.moveaxis(Nt @ e, -1, 0)
+
+
+def run_alg2(M, constants, energies, voxel_nm, angles_deg=(0.0, 1.0, 0.0),
+             rotation=True, uT_mode="literal", energy_indices=None):
+    """Algorithm 2: N_t computed once per energy (Algorithm 3), then per
+    e-field angle p = N_t . e, p <- U^T p, FFT, Ewald, rotation, average."""
+    alphas = angle_list(*angles_deg, rotation=rotation)
+    sel = range(len(energies)) if energy_indices is None else energy_indices
+    Ny, Nx = M.shape[2], M.shape[3]
+    out = np.zeros((len(sel), Ny, Nx))
+    for o, i in enumerate(sel):
+        Nt = nr_computation(M, constants[i])
+        acc = np.zeros((Ny, Nx))
+        for a in alphas:
+            p = polarization_from_nt(Nt, e_field(a))
+            if uT_mode == "literal":
+                p = rotate_back(p, a)
+            img = fftshift2(ewald(fft3(p), energies[i], voxel_nm))
+            acc += rotate_image(img, a) if rotation else img
+        out[o] = acc / len(alphas)
+    return out
+
+
+# ------------------------------------- linearity restatement of Algorithm 2
+def run_linear(M, constants, energies, voxel_nm, angles_deg=(0.0, 1.0, 0.0),
+               rotation=True, uT_mode="literal", energy_indices=None):
+    """Algorithm 2 rewritten with the linearity of p in e and of the FFT:
+    e(alpha) = cos(alpha) x + sin(alpha) y, so
+        p~(alpha) = FFT(N_t x) cos(alpha) + FFT(N_t y) sin(alpha),
+    then U^T, Eqs. (3Dscatter), (Ewald), rotation and average as before.
+    The two FFT'd columns of N_t are formed once per energy."""
+    alphas = angle_list(*angles_deg, rotation=rotation)
+    sel = range(len(energies)) if energy_indices is None else energy_indices
+    Ny, Nx = M.shape[2], M.shape[3]
+    out = np.zeros((len(sel), Ny, Nx))
+    for o, i in enumerate(sel):
+        Nt = nr_computation(M, constants[i])
+        Fx = fft3(np.moveaxis(Nt[..., :, 0], -1, 0))   # FFT of N_t x-hat
+        Fy = fft3(np.moveaxis(Nt[..., :, 1], -1, 0))   # FFT of N_t y-hat
+        acc = np.zeros((Ny, Nx))
+        for a in alphas:
+            pt = math.cos(a) * Fx + math.sin(a) * Fy
+            if uT_mode == "literal":
+                pt = rotate_back(pt, a)
+            img = fftshift2(ewald(pt, energies[i], voxel_nm))
             acc += rotate_image(img, a) if rotation else img
         out[o] = acc / len(alphas)
     return out

@@ -74,11 +74,10 @@ int check_config(const rsx_config* c) {
     return fail(RSX_ERR_INVALID, "voxel_nm must be positive and finite");
   if (c->precision != 32 && c->precision != 64)
     return fail(RSX_ERR_INVALID, "precision=%d: must be 32 or 64", c->precision);
-  if (c->algorithm != 1 && c->algorithm != 2)
-    return fail(RSX_ERR_INVALID, "algorithm=%d: must be 1 or 2", c->algorithm);
+  if (c->algorithm < 1 || c->algorithm > 3)
+    return fail(RSX_ERR_INVALID, "algorithm=%d: must be 1, 2 or 3", c->algorithm);
   if (c->frame != RSX_FRAME_LITERAL && c->frame != RSX_FRAME_LAB)
     return fail(RSX_ERR_INVALID, "frame=%d: must be RSX_FRAME_LITERAL or RSX_FRAME_LAB", c->frame);
-  if (c->algorithm == 2) return fail(RSX_ERR_UNSUPPORTED, "algorithm 2 is not built yet");
   return RSX_OK;
 }
 
@@ -106,7 +105,21 @@ struct rsx_context {
   void* img = nullptr;  // one detector image
   void* acc = nullptr;  // running sum of rotated images
   void* geo = nullptr;  // per-pixel Ewald geometry of energy geo_energy
-  void* bins = nullptr; // 3 components x 2 q_z bins per pixel (fused y/z path)
+  // Algorithm 2: N_t of energy nt_energy (5 complex per voxel); a host
+  // morphology stays on the host and is streamed per component in chunks
+  // through two staging buffers on a copy stream.
+  void* nt = nullptr;
+  int nt_energy = -1;
+  const void* M_host = nullptr;
+  void* stage[2] = {nullptr, nullptr};
+  long long stage_vox = 0;
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_copied[2] = {nullptr, nullptr}, ev_used[2] = {nullptr, nullptr};
+  // linearity fast path (algorithm 3): FFT'd N_t entries and their two q_z
+  // bins per pixel for energy bins_energy
+  void* ft = nullptr;
+  void* bins5 = nullptr;
+  int bins_energy = -1;
   int geo_energy = -1;
   void* twx = nullptr;
   void* twy = nullptr;
@@ -125,8 +138,7 @@ struct rsx_context {
 namespace {
 
 void free_all(rsx_context* c) {
-  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,
-                  c->bins,    c->twx, c->twy, c->twz, c->flag};
+  void* ptrs[] = {c->M_owned, c->p, c->img, c->acc, c->geo, c->twx, c->twy, c->twz, c->flag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -136,6 +148,15 @@ void free_all(rsx_context* c) {
   for (cudaEvent_t e : c->pool) cudaEventDestroy(e);
   c->recs.clear();
   c->pool.clear();
+  for (int b = 0; b < 2; ++b) {
+    if (c->stage[b]) cudaFree(c->stage[b]);
+    if (c->ev_copied[b]) cudaEventDestroy(c->ev_copied[b]);
+    if (c->ev_used[b]) cudaEventDestroy(c->ev_used[b]);
+  }
+  if (c->nt) cudaFree(c->nt);
+  if (c->ft) cudaFree(c->ft);
+  if (c->bins5) cudaFree(c->bins5);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
 }
 
 cudaEvent_t take_event(rsx_context* c) {
@@ -228,13 +249,96 @@ int ensure_geo(rsx_context* c, int ie, cudaStream_t s) {
   return RSX_OK;
 }
 
+// Algorithm 3 for energy ie into c->nt (once per energy): from the
+// device-resident morphology in one pass, or streamed from the host one
+// component at a time in chunks of stage_vox voxels, the copy of chunk i + 1
+// (copy stream) overlapping the accumulation of chunk i (stream s).
+template <typename R>
+int ensure_nt(rsx_context* c, int ie, cudaStream_t s) {
+  if (c->nt_energy == ie) return RSX_OK;
+  const PolParams<R> pp = make_params<R>(c, ie, 0.0, 0);
+  PhaseTimer pt(c, RSX_PHASE_NT, s);
+  if (!c->M_host) {
+    RSX_CK(rsx::launch_nt_all<R>(c->M, c->N, pp, c->nt, s), "N_t kernel");
+    c->nt_energy = ie;
+    return RSX_OK;
+  }
+  const size_t entry = 4 * sizeof(R);
+  const long long N = c->N, CH = c->stage_vox;
+  const long long nchunk = (N + CH - 1) / CH;
+  // the copy stream starts after everything already queued on s
+  RSX_CK(cudaEventRecord(c->ev_used[0], s), "N_t stream");
+  RSX_CK(cudaEventRecord(c->ev_used[1], s), "N_t stream");
+  long long step = 0;
+  for (int j = 0; j < c->cfg.n_components; ++j) {
+    for (long long ch = 0; ch < nchunk; ++ch, ++step) {
+      const int b = (int)(step & 1);
+      const long long off = ch * CH, n = (off + CH <= N) ? CH : N - off;
+      const char* src = (const char*)c->M_host + ((size_t)j * N + off) * entry;
+      RSX_CK(cudaStreamWaitEvent(c->copy_stream, c->ev_used[b], 0), "N_t stream");
+      RSX_CK(cudaMemcpyAsync(c->stage[b], src, (size_t)n * entry, cudaMemcpyHostToDevice,
+                             c->copy_stream),
+             "morphology stream");
+      RSX_CK(cudaEventRecord(c->ev_copied[b], c->copy_stream), "N_t stream");
+      RSX_CK(cudaStreamWaitEvent(s, c->ev_copied[b], 0), "N_t stream");
+      RSX_CK(rsx::launch_nt_comp<R>(c->stage[b], off, n, N, j, j == 0, pp, c->nt, s),
+             "N_t kernel");
+      RSX_CK(cudaEventRecord(c->ev_used[b], s), "N_t stream");
+    }
+  }
+  c->nt_energy = ie;
+  return RSX_OK;
+}
+
+// Linearity fast path, once per energy: FFT (x and y) of N_t's five
+// entries, then their two q_z bins per pixel.
+template <typename R>
+int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
+  if (c->bins_energy == ie) return RSX_OK;
+  const rsx_config& g = c->cfg;
+  int rc = ensure_geo<R>(c, ie, s);
+  if (rc) return rc;
+  if ((rc = ensure_nt<R>(c, ie, s))) return rc;
+  const size_t bytes = 5 * (size_t)c->N * 2 * sizeof(R);
+  {
+    PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
+    RSX_CK(cudaMemcpyAsync(c->ft, c->nt, bytes, cudaMemcpyDeviceToDevice, s), "N_t copy");
+    RSX_CK(rsx::launch_row_fft<R>(c->ft, g.nx, 5LL * g.ny * g.nz, c->twx, s), "x-FFT kernel");
+  }
+  if (g.ny > 1) {
+    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+    RSX_CK(rsx::launch_col_fft<R>(c->ft, g.ny, g.nx, g.nx, 5LL * g.nz, c->npix, c->twy, s),
+           "y-FFT kernel");
+  }
+  PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+  const double dc = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
+  RSX_CK(rsx::launch_zbins5<R>(c->ft, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, dc,
+                               c->bins5, s),
+         "q_z bins kernel");
+  c->bins_energy = ie;
+  return RSX_OK;
+}
+
 template <typename R>
 int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t s) {
   const rsx_config& g = c->cfg;
   int rc = ensure_geo<R>(c, ie, s);
   if (rc) return rc;
+  if (g.algorithm == 3) {
+    if ((rc = ensure_bins<R>(c, ie, s))) return rc;
+    PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+    RSX_CK(rsx::launch_ewald_linear<R>(c->bins5, g.nx, g.ny, (const Geo<R>*)c->geo, alpha,
+                                       g.frame == RSX_FRAME_LITERAL, img, s),
+           "Ewald kernel");
+    return RSX_OK;
+  }
   const PolParams<R> pp = make_params<R>(c, ie, alpha, 0);
-  {
+  if (g.algorithm == 2) {
+    if ((rc = ensure_nt<R>(c, ie, s))) return rc;
+    PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
+    RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+           "N_t polarisation + x-FFT kernel");
+  } else {
     PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
     RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
            "polarisation + x-FFT kernel");
@@ -247,18 +351,6 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     dc[0] = (R)ref; dc[1] = (R)0; dc[2] = (R)0;
   } else {
     dc[0] = (R)(ref * cos(alpha)); dc[1] = (R)(ref * sin(alpha)); dc[2] = (R)0;
-  }
-  if (rsx::yz_fused_supported<R>(g.nx, g.ny, g.nz)) {
-    {
-      PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-      RSX_CK(rsx::launch_fft_y_zbins<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twy,
-                                        c->twz, c->bins, s),
-             "y-FFT + q_z kernel");
-    }
-    PhaseTimer pt(c, RSX_PHASE_EWALD, s);
-    RSX_CK(rsx::launch_ewald_bins<R>(c->bins, g.nx, g.ny, (const Geo<R>*)c->geo, dc, img, s),
-           "Ewald kernel");
-    return RSX_OK;
   }
   if (g.ny > 1) {
     PhaseTimer pt(c, RSX_PHASE_FFTY, s);
@@ -314,11 +406,14 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
   const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
   const long long npix = (long long)cfg->nx * cfg->ny;
   const size_t R = real_size(cfg->precision), Cs = complex_size(cfg->precision);
-  size_t b = (size_t)cfg->n_components * N * 4 * R;  // morphology copy (Table 1: 4c N)
+  const long long stage_vox = N < (1LL << 22) ? N : (1LL << 22);
+  size_t b = cfg->algorithm == 1
+                 ? (size_t)cfg->n_components * N * 4 * R  // morphology copy (Table 1: 4c N)
+                 : 5 * (size_t)N * Cs + 2 * (size_t)stage_vox * 4 * R;  // N_t + staging (Table 2)
+  if (cfg->algorithm == 3) b += 5 * (size_t)N * Cs + 10 * (size_t)npix * Cs;  // FFT'd N_t, bins
   b += 3 * (size_t)N * Cs;                           // p_x, p_y, p_z (Table 1: 6 N)
   b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
   b += (size_t)npix * geo_size(cfg->precision);
-  b += 6 * (size_t)npix * Cs;                        // two q_z bins x 3 components
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
   return b;
 }
@@ -356,13 +451,30 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
       {&c->img, (size_t)c->npix * R, "Ewald image"},
       {&c->acc, (size_t)c->npix * R, "Ewald average"},
       {&c->geo, (size_t)c->npix * geo_size(cfg->precision), "Ewald geometry"},
-      {&c->bins, 6 * (size_t)c->npix * Cs, "q_z bins"},
       {(void**)&c->flag, sizeof(int), "validation flag"},
   };
   for (auto& a : allocs) {
     e = cudaMalloc(a.dst, a.bytes);
     if (e != cudaSuccess) {
       rc = cuda_fail(e, a.what);
+      free_all(c);
+      delete c;
+      return rc;
+    }
+  }
+  if (cfg->algorithm >= 2) {
+    c->stage_vox = c->N < (1LL << 22) ? c->N : (1LL << 22);
+    e = cudaMalloc(&c->nt, 5 * (size_t)c->N * Cs);
+    if (e == cudaSuccess && cfg->algorithm == 3) e = cudaMalloc(&c->ft, 5 * (size_t)c->N * Cs);
+    if (e == cudaSuccess && cfg->algorithm == 3) e = cudaMalloc(&c->bins5, 10 * (size_t)c->npix * Cs);
+    for (int b = 0; b < 2 && e == cudaSuccess; ++b) {
+      e = cudaMalloc(&c->stage[b], (size_t)c->stage_vox * 4 * R);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_copied[b], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_used[b], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "Algorithm 2 buffers");
       free_all(c);
       delete c;
       return rc;
@@ -400,10 +512,21 @@ int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
   if (where == RSX_HOST) {
     if (c->cfg.validate && !host_morphology_ok(M, prec, n_entries))
       return fail(RSX_ERR_INVALID, "morphology value outside 0<=v<=1, 0<=s<=1 or non-finite angle");
+    if (c->cfg.algorithm >= 2) {
+      // Algorithm 2 keeps the morphology on the host and streams it per
+      // component for each energy (Algorithm 3): borrowed, not copied.
+      c->M_host = M;
+      c->M = M;
+      c->nt_energy = -1;
+      c->bins_energy = -1;
+      return RSX_OK;
+    }
     if (!c->M_owned) RSX_CK(cudaMalloc(&c->M_owned, bytes), "morphology copy");
     RSX_CK(cudaMemcpyAsync(c->M_owned, M, bytes, cudaMemcpyHostToDevice, s), "morphology upload");
     RSX_CK(cudaStreamSynchronize(s), "morphology upload");
     c->M = c->M_owned;
+    c->nt_energy = -1;
+    c->bins_energy = -1;
     return RSX_OK;
   }
   if (((uintptr_t)M) % (4 * real_size(prec)) != 0)
@@ -420,6 +543,9 @@ int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
     if (h) return fail(RSX_ERR_INVALID, "morphology value outside 0<=v<=1, 0<=s<=1 or non-finite angle");
   }
   c->M = M;
+  c->M_host = nullptr;
+  c->nt_energy = -1;
+  c->bins_energy = -1;
   return RSX_OK;
 }
 
@@ -434,6 +560,8 @@ int rsx_set_optical_constants(rsx_context* c, int n, const double* E, const doub
   c->energies.assign(E, E + n);
   c->constants.assign(k, k + (size_t)n * nc * 4);
   c->geo_energy = -1;
+  c->nt_energy = -1;
+  c->bins_energy = -1;
   return RSX_OK;
 }
 
@@ -445,6 +573,19 @@ int rsx_polarization(rsx_context* c, int ie, double alpha, void* p_out, void* st
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   const rsx_config& g = c->cfg;
+  if (g.algorithm >= 2) {
+    int rc2 = g.precision == 32 ? ensure_nt<float>(c, ie, s) : ensure_nt<double>(c, ie, s);
+    if (rc2) return rc2;
+    RSX_CK(g.precision == 32
+               ? rsx::launch_ntp_fftx<float>(c->nt, g.nx, g.ny, g.nz,
+                                             make_params<float>(c, ie, alpha, 1), false, p_out,
+                                             nullptr, s)
+               : rsx::launch_ntp_fftx<double>(c->nt, g.nx, g.ny, g.nz,
+                                              make_params<double>(c, ie, alpha, 1), false, p_out,
+                                              nullptr, s),
+           "N_t polarisation kernel");
+    return RSX_OK;
+  }
   if (g.precision == 32) {
     RSX_CK(rsx::launch_pol_fftx<float>(c->M, g.nx, g.ny, g.nz, make_params<float>(c, ie, alpha, 1),
                                        false, p_out, nullptr, s),
@@ -569,6 +710,26 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
   return RSX_OK;
 }
 }  // namespace
+
+int rsx_nt(rsx_context* c, int ie, void* nt_out, void* stream) {
+  int rc = check_ready(c);
+  if (rc) return rc;
+  if ((rc = check_energy(c, ie))) return rc;
+  if (!nt_out) return fail(RSX_ERR_INVALID, "nt_out is NULL");
+  if (c->cfg.algorithm < 2)
+    return fail(RSX_ERR_STATE, "N_t needs a context made with algorithm 2 or 3");
+  DeviceGuard dg(c->dev);
+  cudaStream_t s = (cudaStream_t)stream;
+  const double ref = -(double)(c->cfg.n_components - 1) / (4.0 * kPi);
+  if (c->cfg.precision == 32) {
+    if ((rc = ensure_nt<float>(c, ie, s))) return rc;
+    RSX_CK(rsx::launch_nt_restore<float>(c->nt, nt_out, c->N, ref, s), "N_t output");
+  } else {
+    if ((rc = ensure_nt<double>(c, ie, s))) return rc;
+    RSX_CK(rsx::launch_nt_restore<double>(c->nt, nt_out, c->N, ref, s), "N_t output");
+  }
+  return RSX_OK;
+}
 
 int rsx_set_timing(rsx_context* c, int enable) {
   if (!c) return fail(RSX_ERR_INVALID, "context is NULL");

@@ -120,12 +120,16 @@ __device__ __forceinline__ void load_m(const typename RT<R>::V4* M, size_t i, R&
 // 3*ROWS rows are transformed along x in shared memory and written once.
 // LOGNX >= 0 fixes nx = 2^LOGNX at compile time (the FFT's index arithmetic
 // then folds into constants); LOGNX < 0 takes lognx at run time.
-template <typename R, int T, int EC, bool DO_FFT, int LOGNX>
+// FROM_NT: the source is Algorithm 2's N_t (five complex entries per voxel,
+// nt[5][N] = xx, xy, yy, xz, yz, with the same constant removed from the
+// diagonal) instead of the morphology, and p = N_t . e.
+template <typename R, int T, int EC, bool DO_FFT, int LOGNX, bool FROM_NT>
 __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_pol_fftx(const typename RT<R>::V4* __restrict__ M,
                                                 long long N, int lognx_rt, long long nrows,
                                                 PolParams<R> pp, typename RT<R>::C* __restrict__ p,
                                                 const typename RT<R>::C* __restrict__ twx,
-                                                int tw_in_smem) {
+                                                int tw_in_smem,
+                                                const typename RT<R>::C* __restrict__ nt) {
   using C = typename RT<R>::C;
   using V4 = typename RT<R>::V4;
   constexpr int SLOTS = EC / T;
@@ -144,6 +148,42 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
   if (DO_FFT && tw_in_smem)
     for (int i = threadIdx.x; i < nx; i += T) tws[i] = twx[i];
 
+  if constexpr (FROM_NT) {
+    const R inv_ref = pp.add_ref ? R(-(pp.c - 1) / kFourPi) : R(0);
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) {
+      const int e = threadIdx.x + sl * T;
+      if (e < nel) {
+        const size_t i = vox0 + e;
+        C t[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) t[q] = nt[q * (size_t)N + i];
+        const R ce = pp.ce, se = pp.se;
+        // p = N_t . e with e = (ce, se, 0): columns x and y of N_t
+        C px = RT<R>::mk(t[0].x * ce + t[1].x * se + inv_ref * ce, t[0].y * ce + t[1].y * se);
+        C py = RT<R>::mk(t[1].x * ce + t[2].x * se + inv_ref * se, t[1].y * ce + t[2].y * se);
+        const C pz = RT<R>::mk(t[3].x * ce + t[4].x * se, t[3].y * ce + t[4].y * se);
+        C out[3];
+        if (pp.literal) {
+          out[0] = RT<R>::mk(ce * px.x + se * py.x, ce * px.y + se * py.y);
+          out[1] = RT<R>::mk(-se * px.x + ce * py.x, -se * px.y + ce * py.y);
+        } else {
+          out[0] = px;
+          out[1] = py;
+        }
+        out[2] = pz;
+        if (DO_FFT) {
+          buf[padi(e)] = out[0];
+          buf[padi(EC + e)] = out[1];
+          buf[padi(2 * EC + e)] = out[2];
+        } else {
+          p[i] = out[0];
+          p[(size_t)N + i] = out[1];
+          p[2 * (size_t)N + i] = out[2];
+        }
+      }
+    }
+  } else {
   PolAcc<R> acc[SLOTS];
 #pragma unroll
   for (int sl = 0; sl < SLOTS; ++sl) pol_zero(acc[sl]);
@@ -187,6 +227,7 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
       }
     }
   }
+  }
   if (!DO_FFT) return;
   __syncthreads();
   const C* tw = tw_in_smem ? tws : twx;
@@ -227,48 +268,64 @@ __global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p
 
 // Column FFTs: element i of column col of batch b sits at
 //   data[b * batch_stride + i * S + tile * TX + col],  i < L = 2^logL.
-// One CTA transforms TX = 2^logTX adjacent columns (coalesced rows of TX
-// complex values) of one batch.  Used for y (S = nx, W = nx, batches =
-// 3 nz) and for z (S = W = nx ny, batches = 3).  The tile arrives by
-// cp.async, NLD copies per thread in flight, without passing registers.
+// A tile is TX = 2^logTX adjacent columns (coalesced rows of TX complex
+// values) of one batch.  Used for y (S = nx, W = nx, batches = 3 nz) and for
+// z (S = W = nx ny, batches = 3).  The kernel is persistent: each CTA walks
+// tiles blockIdx.x, blockIdx.x + gridDim.x, ... and, while it transforms one
+// tile, the next one is already arriving by cp.async in the second buffer.
 template <typename R, int T, int EC, int LOGL>
-__global__ void __launch_bounds__(T, 3) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
+__global__ void __launch_bounds__(T, 2) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
                                                long long S, int logTX_rt, long long ntiles,
-                                               long long batch_stride,
+                                               long long total, long long batch_stride,
                                                const typename RT<R>::C* __restrict__ tw_g,
                                                int tw_in_smem) {
   using C = typename RT<R>::C;
   constexpr int NLD = EC / T;
+  constexpr int PB = padded(EC);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // [L][TX], padded
-  C* tws = buf + padded(EC);
+  C* buf = reinterpret_cast<C*>(smem_raw);  // two tiles [L][TX], padded
+  C* tws = buf + 2 * PB;
   // with LOGL fixed, TX = EC / L is fixed too
   const int logL = LOGL >= 0 ? LOGL : logL_rt;
   const int logTX = LOGL >= 0 ? ilog2_ct(EC >> (LOGL >= 0 ? LOGL : 0)) : logTX_rt;
   const int L = 1 << logL;
   const int TX = 1 << logTX;
-  const long long tile = (long long)blockIdx.x % ntiles;
-  const long long b = (long long)blockIdx.x / ntiles;
-  C* base = data + b * batch_stride + tile * TX;
+  const int nel = L << logTX;
+  auto base_of = [&](long long t) {
+    return data + (t / ntiles) * batch_stride + (t % ntiles) * TX;
+  };
+  auto issue = [&](long long t, C* dst) {
+    const C* base = base_of(t);
+#pragma unroll
+    for (int it = 0; it < NLD; ++it) {
+      const int e = threadIdx.x + it * T;
+      if (e < nel) cp_async_elem(dst + padi(e), base + (size_t)(e >> logTX) * S + (e & (TX - 1)));
+    }
+  };
   if (tw_in_smem)
     for (int i = threadIdx.x; i < L; i += T) tws[i] = tw_g[i];
-  const int nel = L << logTX;
-#pragma unroll
-  for (int it = 0; it < NLD; ++it) {
-    const int e = threadIdx.x + it * T;
-    if (e < nel) cp_async_elem(buf + padi(e), base + (size_t)(e >> logTX) * S + (e & (TX - 1)));
-  }
-  cp_async_wait_all();
-  __syncthreads();
   const C* tw = tw_in_smem ? tws : tw_g;
-  if constexpr (LOGL >= 0)
-    block_fft_ct<R, LOGL, (EC >> LOGL), 1, (EC >> LOGL), T, true>(buf, tw);
-  else
-    block_fft<R, EC, T, true>(buf, logL, TX, logTX, 1, TX, tw);
+  long long t = blockIdx.x;
+  if (t < total) issue(t, buf);
+  cp_async_commit();
+  for (int i = 0; t < total; t += gridDim.x, ++i) {
+    C* cur = buf + (i & 1) * PB;
+    const long long tn = t + gridDim.x;
+    if (tn < total) issue(tn, buf + ((i + 1) & 1) * PB);
+    cp_async_commit();
+    cp_async_wait<1>();  // everything but the prefetch just issued has landed
+    __syncthreads();
+    if constexpr (LOGL >= 0)
+      block_fft_ct<R, LOGL, (EC >> LOGL), 1, (EC >> LOGL), T, true>(cur, tw);
+    else
+      block_fft<R, EC, T, true>(cur, logL, TX, logTX, 1, TX, tw);
+    C* base = base_of(t);
 #pragma unroll
-  for (int it = 0; it < NLD; ++it) {
-    const int e = threadIdx.x + it * T;
-    if (e < nel) base[(size_t)(e >> logTX) * S + (e & (TX - 1))] = buf[padi(e)];
+    for (int it = 0; it < NLD; ++it) {
+      const int e = threadIdx.x + it * T;
+      if (e < nel) base[(size_t)(e >> logTX) * S + (e & (TX - 1))] = cur[padi(e)];
+    }
+    __syncthreads();  // cur is refilled by the prefetch of the iteration after next
   }
 }
 
@@ -529,108 +586,87 @@ __global__ void k_ewald_single(const typename RT<R>::C* __restrict__ p, int nz,
   img[0] = ewald_value<R>(g, a0, a1);
 }
 
-// ------------------------------------------- y-FFT fused with the pruned z
-// One CTA owns a tile of TX = EC / ny adjacent x-columns of one component
-// for every z.  For each slice it transforms the tile along y in shared
-// memory and adds its contribution to the two q_z bins each pixel needs,
-//   acc_b += P(z) exp(-2 pi i b z / nz),  b = b0, b0 + 1,
-// keeping the accumulators in registers across the slices, so the
-// y-transformed data never go back to memory.  Slices arrive by cp.async
-// NBUF - 1 ahead of the one being transformed.  Output: bins[k][2][npix]
-// (FFT order), combined into the image by k_ewald_bins.
-template <typename R, int T, int EC, int LOGL, int NBUF>
-__global__ void __launch_bounds__(T, 2) k_fft_y_zbins(const typename RT<R>::C* __restrict__ p,
-                                                      int nx, int nz,
-                                                      const Geo<R>* __restrict__ geo,
-                                                      const typename RT<R>::C* __restrict__ twy_g,
-                                                      const typename RT<R>::C* __restrict__ twz_g,
-                                                      typename RT<R>::C* __restrict__ bins) {
+// ------------------------------------------------ linearity fast path
+// p~(alpha) = cos(alpha) F(N_t x) + sin(alpha) F(N_t y): the five FFT'd
+// N_t entries are reduced once per energy to the two q_z bins each pixel
+// needs (k_zbins5); each angle then only combines them per pixel
+// (k_ewald_linear).
+template <typename R, int ZB>
+__global__ void __launch_bounds__(256) k_zbins5(const typename RT<R>::C* __restrict__ f, int nx, int ny,
+                                                int nz, const Geo<R>* __restrict__ geo,
+                                                const typename RT<R>::C* __restrict__ twz_g,
+                                                int tw_in_smem, R dc,
+                                                typename RT<R>::C* __restrict__ bins) {
   using C = typename RT<R>::C;
-  constexpr int L = 1 << LOGL;
-  constexpr int TX = EC >> LOGL;
-  constexpr int LOGTX = ilog2_ct(TX);
-  constexpr int NE = EC / T;
-  constexpr int PB = padded(EC);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // NBUF tiles [L][TX], padded
-  C* twy = buf + NBUF * PB;
-  C* twz = twy + L;
-  const int ntiles = nx / TX;
-  const int tile = blockIdx.x % ntiles;
-  const int k = blockIdx.x / ntiles;
-  const size_t npix = (size_t)nx * L;
-  const size_t N = npix * nz;
-  const C* src = p + k * N + (size_t)tile * TX;
-
-  for (int i = threadIdx.x; i < L; i += T) twy[i] = twy_g[i];
-  for (int i = threadIdx.x; i < nz; i += T) twz[i] = twz_g[i];
-
-  auto issue = [&](int z, int slot) {
-    C* dst = buf + slot * PB;
-    const C* s = src + (size_t)z * npix;
+  C* tws = reinterpret_cast<C*>(smem_raw);
+  if (tw_in_smem) {
+    for (int i = threadIdx.x; i < nz; i += blockDim.x) tws[i] = twz_g[i];
+    __syncthreads();
+  }
+  const C* twz = tw_in_smem ? tws : twz_g;
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const size_t N = (size_t)npix * nz;
+  const Geo<R> g = geo[pix];
+  const int s0 = g.b0 < 0 ? 0 : g.b0, s1 = g.b1 < 0 ? 0 : g.b1;
+  C a0[5], a1[5];
 #pragma unroll
-    for (int it = 0; it < NE; ++it) {
-      const int e = threadIdx.x + it * T;
-      cp_async_elem(dst + padi(e), s + (size_t)(e >> LOGTX) * nx + (e & (TX - 1)));
+  for (int q = 0; q < 5; ++q) a0[q] = a1[q] = RT<R>::mk(0, 0);
+  int i0 = 0, i1 = 0;
+  const C* src = f + pix;
+  int z = 0;
+  if (g.b0 >= 0) {
+    for (; z + ZB <= nz; z += ZB) {
+      C v[ZB][5];
+#pragma unroll
+      for (int u = 0; u < ZB; ++u)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) v[u][q] = __ldg(src + q * N + (size_t)(z + u) * npix);
+#pragma unroll
+      for (int u = 0; u < ZB; ++u) {
+        const C w0 = twz[i0], w1 = twz[i1];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          a0[q] = cadd(a0[q], cmul(v[u][q], w0));
+          a1[q] = cadd(a1[q], cmul(v[u][q], w1));
+        }
+        i0 += s0;
+        if (i0 >= nz) i0 -= nz;
+        i1 += s1;
+        if (i1 >= nz) i1 -= nz;
+      }
     }
-  };
-
-  // the lower bin of each owned pixel lives in shared memory, its running
-  // twiddle index and the two accumulators in registers
-  int* b0s = reinterpret_cast<int*>(twz + nz);
-  int i0[NE];
-  C a0[NE], a1[NE];
+    for (; z < nz; ++z) {
+      const C w0 = twz[i0], w1 = twz[i1];
 #pragma unroll
-  for (int it = 0; it < NE; ++it) {
-    const int e = threadIdx.x + it * T;
-    const size_t pix = (size_t)(e >> LOGTX) * nx + (size_t)tile * TX + (e & (TX - 1));
-    const int g = geo[pix].b0;
-    b0s[e] = g < 0 ? 0 : g;
-    i0[it] = 0;
-    a0[it] = a1[it] = RT<R>::mk(0, 0);
-  }
-#pragma unroll
-  for (int z = 0; z < NBUF - 1; ++z) {
-    if (z < nz) issue(z, z);
-    cp_async_commit();
-  }
-  for (int z = 0; z < nz; ++z) {
-    cp_async_wait<NBUF - 2>();
-    __syncthreads();  // slice z landed for all threads; slot (z-1) % NBUF is free
-    if (z + NBUF - 1 < nz) issue(z + NBUF - 1, (z + NBUF - 1) % NBUF);
-    cp_async_commit();
-    C* cur = buf + (z % NBUF) * PB;
-    block_fft_ct<R, LOGL, TX, 1, TX, T, true>(cur, twy);
-    const C wz = twz[z];
-#pragma unroll
-    for (int it = 0; it < NE; ++it) {
-      const int e = threadIdx.x + it * T;
-      const C v = cur[padi(e)];
-      const C w0 = twz[i0[it]];
-      const C w1 = cmul(w0, wz);  // exp(-2 pi i (b0 + 1) z / nz)
-      a0[it] = cadd(a0[it], cmul(v, w0));
-      a1[it] = cadd(a1[it], cmul(v, w1));
-      i0[it] += b0s[e];
-      if (i0[it] >= nz) i0[it] -= nz;
+      for (int q = 0; q < 5; ++q) {
+        const C v = __ldg(src + q * N + (size_t)z * npix);
+        a0[q] = cadd(a0[q], cmul(v, w0));
+        a1[q] = cadd(a1[q], cmul(v, w1));
+      }
+      i0 += s0;
+      if (i0 >= nz) i0 -= nz;
+      i1 += s1;
+      if (i1 >= nz) i1 -= nz;
+    }
+    if (pix == 0) {  // diagonal entries xx (0) and yy (2) get the constant back
+      if (g.b0 == 0) { a0[0].x += dc; a0[2].x += dc; }
+      if (g.b1 == 0) { a1[0].x += dc; a1[2].x += dc; }
     }
   }
-  C* out0 = bins + (size_t)(2 * k) * npix;
-  C* out1 = out0 + npix;
 #pragma unroll
-  for (int it = 0; it < NE; ++it) {
-    const int e = threadIdx.x + it * T;
-    const size_t pix = (size_t)(e >> LOGTX) * nx + (size_t)tile * TX + (e & (TX - 1));
-    out0[pix] = a0[it];
-    out1[pix] = a1[it];
+  for (int q = 0; q < 5; ++q) {
+    bins[(size_t)(2 * q) * npix + pix] = a0[q];
+    bins[(size_t)(2 * q + 1) * npix + pix] = a1[q];
   }
 }
 
-// Eqs. (3Dscatter) and (Ewald) from the two accumulated bins per pixel, with
-// the constant removed before the FFT added back at q = 0.
 template <typename R>
-__global__ void __launch_bounds__(256) k_ewald_bins(const typename RT<R>::C* __restrict__ bins, int nx,
-                                                    int ny, const Geo<R>* __restrict__ geo, R dc0,
-                                                    R dc1, R dc2, R* __restrict__ img) {
+__global__ void __launch_bounds__(256) k_ewald_linear(const typename RT<R>::C* __restrict__ bins, int nx,
+                                                      int ny, const Geo<R>* __restrict__ geo, R ce,
+                                                      R se, int literal, R* __restrict__ img) {
   using C = typename RT<R>::C;
   const long long npix = (long long)nx * ny;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -642,21 +678,118 @@ __global__ void __launch_bounds__(256) k_ewald_bins(const typename RT<R>::C* __r
     *dst = R(0);
     return;
   }
-  C a0[3], a1[3];
+  C pb[2][3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    a0[k] = bins[(size_t)(2 * k) * npix + pix];
-    a1[k] = bins[(size_t)(2 * k + 1) * npix + pix];
-  }
-  if (pix == 0) {
-    const R dcs[3] = {dc0, dc1, dc2};
+  for (int b = 0; b < 2; ++b) {
+    C t[5];
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (g.b0 == 0) a0[k].x += dcs[k];
-      if (g.b1 == 0) a1[k].x += dcs[k];
+    for (int q = 0; q < 5; ++q) t[q] = bins[(size_t)(2 * q + b) * npix + pix];
+    // columns x = (xx, xy, xz) and y = (xy, yy, yz) of N_t, combined with e
+    const C px = RT<R>::mk(ce * t[0].x + se * t[1].x, ce * t[0].y + se * t[1].y);
+    const C py = RT<R>::mk(ce * t[1].x + se * t[2].x, ce * t[1].y + se * t[2].y);
+    const C pz = RT<R>::mk(ce * t[3].x + se * t[4].x, ce * t[3].y + se * t[4].y);
+    if (literal) {
+      pb[b][0] = RT<R>::mk(ce * px.x + se * py.x, ce * px.y + se * py.y);
+      pb[b][1] = RT<R>::mk(-se * px.x + ce * py.x, -se * px.y + ce * py.y);
+    } else {
+      pb[b][0] = px;
+      pb[b][1] = py;
     }
+    pb[b][2] = pz;
   }
-  *dst = ewald_value<R>(g, a0, a1);
+  *dst = ewald_value<R>(g, pb[0], pb[1]);
+}
+
+// ------------------------------------------------ Algorithm 3 (NrComputation)
+// N_t = sum_j (N_rot^j N_rot^j - I) / (4 pi) with N_rot^2 - I =
+// (a^2 - 1) I + (2ab + b^2) d d^T, stored as the five entries an in-plane e
+// reads (xx, xy, yy, xz, yz; zz is never used), nt[5][N], with the
+// constant -(c - 1)/(4 pi) removed from the diagonal as in Algorithm 1.
+template <typename R> struct NtAcc {
+  R aw;          // sum_j v_j^2
+  R as[2];       // sum_j v_j^2 tau' (2 + tau')
+  R g[5][2];     // sum_j (2ab + b^2) d d^T entries xx, xy, yy, xz, yz
+};
+
+template <typename R>
+__device__ __forceinline__ void nt_add(NtAcc<R>& A, R v, R s, R phi, R theta,
+                                       const PolParams<R>& pp, int j) {
+  const R tpr = pp.tau[j][0] + s * pp.dperp[j][0];
+  const R tpi = pp.tau[j][1] + s * pp.dperp[j][1];
+  const R v2 = v * v;
+  A.aw += v2;
+  A.as[0] += v2 * (tpr * (R(2) + tpr) - tpi * tpi);
+  A.as[1] += v2 * (tpi * (R(2) + tpr) + tpr * tpi);
+  const R vs = v * s;
+  const R br = vs * pp.dpar[j][0], bi = vs * pp.dpar[j][1];
+  const R qr = R(2) * v * (R(1) + tpr) + br, qi = R(2) * v * tpi + bi;
+  const R gr = br * qr - bi * qi, gi = br * qi + bi * qr;
+  R sp, cp, st, ct;
+  sincos_r(phi, &sp, &cp);
+  sincos_r(theta, &st, &ct);
+  const R dx = cp * st, dy = sp * st, dz = ct;
+  const R dd[5] = {dx * dx, dx * dy, dy * dy, dx * dz, dy * dz};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    A.g[q][0] += gr * dd[q];
+    A.g[q][1] += gi * dd[q];
+  }
+}
+
+// All components from device-resident M: one pass, N_t written once.
+template <typename R>
+__global__ void __launch_bounds__(256) k_nt_all(const typename RT<R>::V4* __restrict__ M, long long N,
+                                                PolParams<R> pp, typename RT<R>::C* __restrict__ nt) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  NtAcc<R> A = {};
+  for (int j = 0; j < pp.c; ++j) {
+    const typename RT<R>::V4 m = M[(size_t)j * N + i];
+    nt_add(A, (R)m.x, (R)m.y, (R)m.z, (R)m.w, pp, j);
+  }
+  const R inv = R(1.0 / kFourPi);
+  const R dr = (A.aw - R(1)) + A.as[0], di = A.as[1];
+  const R diag[5] = {R(1), R(0), R(1), R(0), R(0)};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    nt[q * (size_t)N + i] = RT<R>::mk((A.g[q][0] + diag[q] * dr) * inv, (A.g[q][1] + diag[q] * di) * inv);
+}
+
+// One component j over the voxel range [off, off + n) from a staging copy
+// (Algorithm 3's per-material streaming).  FIRST writes, later components add.
+template <typename R, bool FIRST>
+__global__ void __launch_bounds__(256) k_nt_comp(const typename RT<R>::V4* __restrict__ Mj,
+                                                 long long off, long long n, long long N, int j,
+                                                 PolParams<R> pp, typename RT<R>::C* __restrict__ nt) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const size_t i = (size_t)(off + t);
+  NtAcc<R> A = {};
+  const typename RT<R>::V4 m = Mj[t];
+  nt_add(A, (R)m.x, (R)m.y, (R)m.z, (R)m.w, pp, j);
+  const R inv = R(1.0 / kFourPi);
+  // the first component carries the -1 of (sum v^2 - 1)
+  const R dr = (FIRST ? A.aw - R(1) : A.aw) + A.as[0], di = A.as[1];
+  const R diag[5] = {R(1), R(0), R(1), R(0), R(0)};
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    typename RT<R>::C v =
+        RT<R>::mk((A.g[q][0] + diag[q] * dr) * inv, (A.g[q][1] + diag[q] * di) * inv);
+    if (!FIRST) v = cadd(v, nt[q * (size_t)N + i]);
+    nt[q * (size_t)N + i] = v;
+  }
+}
+
+// N_t for output: the removed constant restored on the diagonal.
+template <typename R>
+__global__ void k_nt_restore(const typename RT<R>::C* __restrict__ nt, typename RT<R>::C* __restrict__ out,
+                             long long N, R ref) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 5 * N) return;
+  typename RT<R>::C v = nt[i];
+  const int q = (int)(i / N);
+  if (q == 0 || q == 2) v.x += ref;
+  out[i] = v;
 }
 
 // ------------------------------------------------------- detector rotation
@@ -721,9 +854,9 @@ static inline int ilog2(long long n) {
 }
 static inline unsigned grid1(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
-template <typename R, int T, int EC, bool DO_FFT, int LOGNX>
+template <typename R, int T, int EC, bool DO_FFT, int LOGNX, bool FROM_NT>
 static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
-                                 void* p, const void* twx, cudaStream_t s) {
+                                 void* p, const void* twx, const void* nt, cudaStream_t s) {
   using C = typename RT<R>::C;
   const long long N = (long long)nx * ny * nz;
   // Without the FFT the voxels are independent: treat them as N rows of one.
@@ -736,27 +869,41 @@ static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const Po
     smem += nx * sizeof(C);
     tw_in_smem = 1;
   }
-  auto kern = k_pol_fftx<R, T, EC, DO_FFT, LOGNX>;
+  auto kern = k_pol_fftx<R, T, EC, DO_FFT, LOGNX, FROM_NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid1(nrows, rows), T, smem, s>>>((const typename RT<R>::V4*)M, N, lognx, nrows, pp,
-                                           (C*)p, (const C*)twx, tw_in_smem);
+                                           (C*)p, (const C*)twx, tw_in_smem, (const C*)nt);
   return cudaGetLastError();
+}
+
+template <typename R, bool FROM_NT>
+static cudaError_t pol_fftx_dispatch(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
+                                     bool do_fft, void* p, const void* twx, const void* nt,
+                                     cudaStream_t s) {
+  if (!do_fft)
+    return pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+#define RSX_POL(L) \
+  case L: return pol_fftx_impl<R, 256, 1024, true, L, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+  switch (ilog2(nx)) {
+    RSX_POL(6) RSX_POL(7) RSX_POL(8) RSX_POL(9) RSX_POL(10)
+    case 11: return pol_fftx_impl<R, 256, 2048, true, 11, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+    case 12: return pol_fftx_impl<R, 512, 4096, true, 12, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+    default: return pol_fftx_impl<R, 256, 1024, true, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+  }
+#undef RSX_POL
 }
 
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                             bool do_fft, void* p, const void* twx, cudaStream_t s) {
-  if (!do_fft) return pol_fftx_impl<R, 256, 1024, false, -1>(M, nx, ny, nz, pp, p, twx, s);
-#define RSX_POL(L) \
-  case L: return pol_fftx_impl<R, 256, 1024, true, L>(M, nx, ny, nz, pp, p, twx, s);
-  switch (ilog2(nx)) {
-    RSX_POL(6) RSX_POL(7) RSX_POL(8) RSX_POL(9) RSX_POL(10)
-    case 11: return pol_fftx_impl<R, 256, 2048, true, 11>(M, nx, ny, nz, pp, p, twx, s);
-    case 12: return pol_fftx_impl<R, 512, 4096, true, 12>(M, nx, ny, nz, pp, p, twx, s);
-    default: return pol_fftx_impl<R, 256, 1024, true, -1>(M, nx, ny, nz, pp, p, twx, s);
-  }
-#undef RSX_POL
+  return pol_fftx_dispatch<R, false>(M, nx, ny, nz, pp, do_fft, p, twx, nullptr, s);
+}
+
+template <typename R>
+cudaError_t launch_ntp_fftx(const void* nt, int nx, int ny, int nz, const PolParams<R>& pp,
+                            bool do_fft, void* p, const void* twx, cudaStream_t s) {
+  return pol_fftx_dispatch<R, true>(nullptr, nx, ny, nz, pp, do_fft, p, twx, nt, s);
 }
 
 template <typename R, int T, int EC>
@@ -781,6 +928,17 @@ cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cu
   return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s);
 }
 
+static int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 1;
+  }
+  return n;
+}
+
 template <typename R, int T, int EC, int LOGL>
 static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long long nbatch,
                                 long long batch_stride, const void* tw, cudaStream_t s) {
@@ -792,7 +950,8 @@ static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long l
   if (LOGL >= 0 && TX != EC / L) return cudaErrorInvalidValue;
   const int logTX = ilog2(TX);
   const long long ntiles = W / TX;
-  size_t smem = (size_t)padded(EC) * sizeof(C);
+  const long long total = ntiles * nbatch;
+  size_t smem = 2 * (size_t)padded(EC) * sizeof(C);
   int tw_in_smem = 0;
   if (smem + L * sizeof(C) <= 200 * 1024) {
     smem += L * sizeof(C);
@@ -801,8 +960,14 @@ static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long l
   auto kern = k_col_fft<R, T, EC, LOGL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<(unsigned)(ntiles * nbatch), T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles,
-                                                     batch_stride, (const C*)tw, tw_in_smem);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) per_sm = 1;
+  long long grid = (long long)per_sm * sm_count();
+  if (grid > total) grid = total;
+  kern<<<(unsigned)grid, T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles, total, batch_stride,
+                                       (const C*)tw, tw_in_smem);
   return cudaGetLastError();
 }
 
@@ -868,53 +1033,52 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
   return cudaGetLastError();
 }
 
-template <typename R, int T, int EC, int LOGL, int NBUF>
-static cudaError_t yz_impl(const void* p, int nx, int nz, const Geo<R>* geo, const void* twy,
-                           const void* twz, void* bins, cudaStream_t s) {
+template <typename R>
+cudaError_t launch_zbins5(const void* f, int nx, int ny, int nz, const Geo<R>* geo, const void* twz,
+                          double dc, void* bins, cudaStream_t s) {
   using C = typename RT<R>::C;
-  constexpr int L = 1 << LOGL;
-  constexpr int TX = EC / L;
-  const size_t smem = ((size_t)NBUF * padded(EC) + L + nz) * sizeof(C) + EC * sizeof(int);
-  auto kern = k_fft_y_zbins<R, T, EC, LOGL, NBUF>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  kern<<<(unsigned)((nx / TX) * 3), T, smem, s>>>((const C*)p, nx, nz, geo, (const C*)twy,
-                                                 (const C*)twz, (C*)bins);
+  const long long npix = (long long)nx * ny;
+  const int tw_in_smem = nz <= 4096;
+  const size_t smem = tw_in_smem ? nz * sizeof(C) : 0;
+  k_zbins5<R, 4><<<grid1(npix, 256), 256, smem, s>>>((const C*)f, nx, ny, nz, geo, (const C*)twz,
+                                                      tw_in_smem, (R)dc, (C*)bins);
   return cudaGetLastError();
 }
 
 template <typename R>
-bool yz_fused_supported(int nx, int ny, int nz) {
-  constexpr int EC = 2048;
-  if (ny < 32 || ny > EC || nz > 4096) return false;
-  return nx >= EC / ny;
-}
-
-template <typename R>
-cudaError_t launch_fft_y_zbins(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
-                               const void* twy, const void* twz, void* bins, cudaStream_t s) {
-  if (!yz_fused_supported<R>(nx, ny, nz)) return cudaErrorInvalidValue;
-  constexpr int EC = 2048;
-  constexpr int NB = sizeof(R) == 4 ? 3 : 2;
-  switch (ilog2(ny)) {
-#define RSX_YZ(LL) \
-  case LL: return yz_impl<R, 256, EC, LL, NB>(p, nx, nz, geo, twy, twz, bins, s);
-    RSX_YZ(5) RSX_YZ(6) RSX_YZ(7) RSX_YZ(8) RSX_YZ(9) RSX_YZ(10) RSX_YZ(11)
-#undef RSX_YZ
-    case 12:
-      if constexpr (EC >= 4096) return yz_impl<R, 256, EC, 12, NB>(p, nx, nz, geo, twy, twz, bins, s);
-      return cudaErrorInvalidValue;
-    default:
-      return cudaErrorInvalidValue;
-  }
-}
-
-template <typename R>
-cudaError_t launch_ewald_bins(const void* bins, int nx, int ny, const Geo<R>* geo, const R dc[3],
-                              void* img, cudaStream_t s) {
+cudaError_t launch_ewald_linear(const void* bins, int nx, int ny, const Geo<R>* geo, double alpha,
+                                bool literal, void* img, cudaStream_t s) {
   using C = typename RT<R>::C;
-  k_ewald_bins<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>((const C*)bins, nx, ny, geo, dc[0],
-                                                                 dc[1], dc[2], (R*)img);
+  k_ewald_linear<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>(
+      (const C*)bins, nx, ny, geo, (R)cos(alpha), (R)sin(alpha), literal ? 1 : 0, (R*)img);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_nt_all(const void* M, long long N, const PolParams<R>& pp, void* nt,
+                          cudaStream_t s) {
+  k_nt_all<R><<<grid1(N, 256), 256, 0, s>>>((const typename RT<R>::V4*)M, N, pp,
+                                            (typename RT<R>::C*)nt);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_nt_comp(const void* Mj, long long off, long long n, long long N, int j,
+                           bool first, const PolParams<R>& pp, void* nt, cudaStream_t s) {
+  using V4 = typename RT<R>::V4;
+  using C = typename RT<R>::C;
+  if (n <= 0) return cudaSuccess;
+  if (first)
+    k_nt_comp<R, true><<<grid1(n, 256), 256, 0, s>>>((const V4*)Mj, off, n, N, j, pp, (C*)nt);
+  else
+    k_nt_comp<R, false><<<grid1(n, 256), 256, 0, s>>>((const V4*)Mj, off, n, N, j, pp, (C*)nt);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_nt_restore(const void* nt, void* out, long long N, double ref, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  k_nt_restore<R><<<grid1(5 * N, 256), 256, 0, s>>>((const C*)nt, (C*)out, N, (R)ref);
   return cudaGetLastError();
 }
 
@@ -954,11 +1118,18 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                             cudaStream_t);                                        \
   template cudaError_t launch_scale<R>(const void*, void*, long long, double, cudaStream_t);      \
   template cudaError_t launch_validate<R>(const void*, long long, int*, cudaStream_t);          \
-  template bool yz_fused_supported<R>(int, int, int);                                             \
-  template cudaError_t launch_fft_y_zbins<R>(const void*, int, int, int, const Geo<R>*,           \
-                                             const void*, const void*, void*, cudaStream_t);      \
-  template cudaError_t launch_ewald_bins<R>(const void*, int, int, const Geo<R>*, const R*, void*, \
-                                            cudaStream_t);
+  template cudaError_t launch_ntp_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \
+                                          void*, const void*, cudaStream_t);                      \
+  template cudaError_t launch_nt_all<R>(const void*, long long, const PolParams<R>&, void*,       \
+                                        cudaStream_t);                                            \
+  template cudaError_t launch_nt_comp<R>(const void*, long long, long long, long long, int, bool, \
+                                         const PolParams<R>&, void*, cudaStream_t);               \
+  template cudaError_t launch_nt_restore<R>(const void*, void*, long long, double, cudaStream_t); \
+  template cudaError_t launch_zbins5<R>(const void*, int, int, int, const Geo<R>*, const void*,    \
+                                        double, void*, cudaStream_t);                             \
+  template cudaError_t launch_ewald_linear<R>(const void*, int, int, const Geo<R>*, double, bool,  \
+                                              void*, cudaStream_t);
+
 
 RSX_INSTANTIATE(float)
 RSX_INSTANTIATE(double)

@@ -38,6 +38,29 @@ void set_last_error(const char* msg);
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                             bool do_fft, void* p, const void* twx, cudaStream_t s);
+// Algorithm 2: p = N_t . e from nt[5][N] (xx, xy, yy, xz, yz), fused with
+// the x-FFT like launch_pol_fftx.
+template <typename R>
+cudaError_t launch_ntp_fftx(const void* nt, int nx, int ny, int nz, const PolParams<R>& pp,
+                            bool do_fft, void* p, const void* twx, cudaStream_t s);
+// Algorithm 3: N_t from device-resident M (all components), or one
+// component's staged voxel range [off, off + n) added to it.
+template <typename R>
+cudaError_t launch_nt_all(const void* M, long long N, const PolParams<R>& pp, void* nt,
+                          cudaStream_t s);
+template <typename R>
+cudaError_t launch_nt_comp(const void* Mj, long long off, long long n, long long N, int j,
+                           bool first, const PolParams<R>& pp, void* nt, cudaStream_t s);
+template <typename R>
+cudaError_t launch_nt_restore(const void* nt, void* out, long long N, double ref, cudaStream_t s);
+// Linearity fast path: the two q_z bins of the five FFT'd N_t entries per
+// pixel (f[5][N] -> bins[5][2][npix]), then one angle's image from them.
+template <typename R>
+cudaError_t launch_zbins5(const void* f, int nx, int ny, int nz, const Geo<R>* geo, const void* twz,
+                          double dc, void* bins, cudaStream_t s);
+template <typename R>
+cudaError_t launch_ewald_linear(const void* bins, int nx, int ny, const Geo<R>* geo, double alpha,
+                                bool literal, void* img, cudaStream_t s);
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s);
 template <typename R>
@@ -52,15 +75,6 @@ cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm
 template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
                          const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s);
-// y-FFT fused with the pruned z transform (sizes where it is built) and the
-// image from its per-pixel bins.
-template <typename R> bool yz_fused_supported(int nx, int ny, int nz);
-template <typename R>
-cudaError_t launch_fft_y_zbins(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
-                               const void* twy, const void* twz, void* bins, cudaStream_t s);
-template <typename R>
-cudaError_t launch_ewald_bins(const void* bins, int nx, int ny, const Geo<R>* geo, const R dc[3],
-                              void* img, cudaStream_t s);
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s);

@@ -31,11 +31,11 @@ EXPORTED = (
     "rsx_create", "rsx_destroy", "rsx_last_error", "rsx_workspace_bytes", "rsx_angle_count",
     "rsx_set_morphology", "rsx_set_optical_constants", "rsx_run", "rsx_polarization",
     "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
-    "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc",
+    "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc", "rsx_nt",
 )
 NOALLOC_MAX_VOXELS = 1 << 20
 NOALLOC_MAX_PIXELS = 1 << 16
-PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other")
+PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other", "nt")
 
 
 class RsxConfig(ctypes.Structure):
@@ -80,6 +80,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "rsx_set_timing": (ci, [vp, ci]),
         "rsx_phase_times": (ci, [vp, vp, vp]),
         "rsx_scatter_angle_noalloc": (ci, [vp, ci, ci, ci, ci, cd, cd, vp, cd, ci, vp, vp]),
+        "rsx_nt": (ci, [vp, ci, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -171,7 +172,8 @@ class Context:
             self._check_shape(A.shape)
             _check(lib().rsx_set_morphology(self._h, A.ctypes.data_as(ctypes.c_void_p), RSX_HOST,
                                             _stream_handle(stream) if stream is not None else None))
-            self._keep = None
+            # Algorithm 2 streams from this host array on every energy
+            self._keep = A if self.cfg.algorithm >= 2 else None
             return
         self._check_shape(tuple(M.shape))
         if not M.is_contiguous():
@@ -239,6 +241,12 @@ class Context:
         _check(lib().rsx_polarization(self._h, int(energy_index), float(alpha_rad),
                                       ctypes.c_void_p(p_out.data_ptr()), _stream_handle(stream)))
         return p_out
+
+    def nt(self, energy_index, nt_out, stream=None):
+        """Algorithm 3's N_t (entries xx, xy, yy, xz, yz) into nt_out [5][nz][ny][nx][2]."""
+        _check(lib().rsx_nt(self._h, int(energy_index), ctypes.c_void_p(nt_out.data_ptr()),
+                            _stream_handle(stream)))
+        return nt_out
 
     def fft3d(self, p, stream=None):
         _check(lib().rsx_fft3d(self._h, ctypes.c_void_p(p.data_ptr()), _stream_handle(stream)))

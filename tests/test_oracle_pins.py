@@ -505,3 +505,49 @@ def test_hexagonal_lattice_bragg_positions():
     for rr in ratios:
         ring = np.abs(q - rr * qstar) < 1.2 * dq
         assert img[ring].max() > 1e3 * bg
+
+
+# ------------------------------------------------------ Algorithms 2 and 3
+def test_nr_computation_closed_form_and_symmetry():
+    """Algorithm 3's N_t equals sum_j [(a_j^2 - 1) I + (2 a_j b_j + b_j^2) d_j d_j^T]
+    / (4 pi) (uniaxial algebra) and is complex symmetric (Sec. 4.3)."""
+    c, shape = 3, (2, 3, 4)
+    M = synth.morphology_random(shape, c, seed=41, dtype=np.float64)
+    nts = synth.optical_constants([287.0], c, seed=42, vacuum_last=False)[0]
+    Nt = O.nr_computation(M, nts)
+    ref = np.zeros(shape + (3, 3), complex)
+    for j in range(c):
+        npar, nperp = 1 - nts[j, 0] + 1j * nts[j, 1], 1 - nts[j, 2] + 1j * nts[j, 3]
+        t = (npar + 2 * nperp) / 3
+        v, s, phi, th = (M[j, ..., k] for k in range(4))
+        a = v * (s * nperp + (1 - s) * t)
+        b = v * s * (npar - nperp)
+        d = np.stack([np.cos(phi) * np.sin(th), np.sin(phi) * np.sin(th), np.cos(th)], axis=-1)
+        ref += ((a * a - 1)[..., None, None] * np.eye(3)
+                + (2 * a * b + b * b)[..., None, None] * d[..., :, None] * d[..., None, :]) / FOUR_PI
+    np.testing.assert_allclose(Nt, ref, atol=1e-15)
+    np.testing.assert_allclose(Nt, np.swapaxes(Nt, -1, -2), atol=1e-16)
+
+
+def test_algorithm2_equals_algorithm1():
+    """Sec. 4.3: Algorithm 2 reorganises Algorithm 1 (N_t precomputed per
+    energy); the images agree up to rounding, in both frames."""
+    E = [275.0, 290.0]
+    M = synth.morphology_random((3, 8, 16), 3, seed=43, dtype=np.float64)
+    K = synth.optical_constants(E, 3, seed=44)
+    for mode in ("literal", "lab"):
+        a1 = O.run_alg1(M, K, E, 5.0, angles_deg=(0, 40, 160), uT_mode=mode)
+        a2 = O.run_alg2(M, K, E, 5.0, angles_deg=(0, 40, 160), uT_mode=mode)
+        np.testing.assert_allclose(a2, a1, rtol=1e-10, atol=1e-14 * a1.max())
+
+
+def test_linearity_restatement_equals_algorithm1():
+    """p~ is linear in e and the FFT is linear: forming FFT(N_t x) and
+    FFT(N_t y) once per energy gives Algorithm 1's images up to rounding."""
+    E = [278.0, 295.0]
+    M = synth.morphology_random((4, 8, 16), 3, seed=45, dtype=np.float64)
+    K = synth.optical_constants(E, 3, seed=46)
+    for mode in ("literal", "lab"):
+        a1 = O.run_alg1(M, K, E, 5.0, angles_deg=(0, 20, 180), uT_mode=mode)
+        al = O.run_linear(M, K, E, 5.0, angles_deg=(0, 20, 180), uT_mode=mode)
+        np.testing.assert_allclose(al, a1, rtol=1e-10, atol=1e-14 * a1.max())
