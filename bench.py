@@ -208,6 +208,12 @@ def run_ours(args):
         # the ewald phase mixes one q_z reduction per energy with light per-angle kernels
         n_l = args.steps
     achieved = (bytes_per_voxel * N * n_l) / (t_ms / 1e3) / 1e9 if bytes_per_voxel else None
+    if args.algorithm == 3:
+        # per-energy FFT work dominates; report the y-FFT of the five N_t fields
+        top = "ffty"
+        t_ms, n_l = phases[top]
+        bytes_per_voxel = per_voxel[top]
+        achieved = (bytes_per_voxel * N * n_l) / (t_ms / 1e3) / 1e9 if n_l else None
     traffic = _traffic_from_profiles(args.workload, top, prec)
 
     # end to end through the public API: host morphology in, host image out

@@ -307,7 +307,8 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
   }
   if (g.ny > 1) {
     PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-    RSX_CK(rsx::launch_col_fft<R>(c->ft, g.ny, g.nx, g.nx, 5LL * g.nz, c->npix, c->twy, s),
+    RSX_CK(rsx::launch_col_fft<R>(c->ft, g.ny, g.nx, g.nx, {5LL * g.nz, g.nz, c->N, c->npix, 0},
+                                  c->twy, s),
            "y-FFT kernel");
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
@@ -332,16 +333,23 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
            "Ewald kernel");
     return RSX_OK;
   }
+  if (g.algorithm == 2 && (rc = ensure_nt<R>(c, ie, s))) return rc;
   const PolParams<R> pp = make_params<R>(c, ie, alpha, 0);
-  if (g.algorithm == 2) {
-    if ((rc = ensure_nt<R>(c, ie, s))) return rc;
+  {
     PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
-           "N_t polarisation + x-FFT kernel");
-  } else {
-    PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
-           "polarisation + x-FFT kernel");
+    if (g.algorithm == 2) {
+      RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+             "N_t polarisation + x-FFT kernel");
+    } else {
+      RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+             "polarisation + x-FFT kernel");
+    }
+  }
+  if (g.ny > 1) {
+    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+    RSX_CK(rsx::launch_col_fft<R>(c->p, g.ny, g.nx, g.nx, {3LL * g.nz, g.nz, c->N, c->npix, 0},
+                                  c->twy, s),
+           "y-FFT kernel");
   }
   // The constant -(c-1) e' / (4 pi) left out of p before the FFT returns at
   // q = 0 as N times itself (e' = x-hat in the literal frame, e otherwise).
@@ -351,12 +359,6 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     dc[0] = (R)ref; dc[1] = (R)0; dc[2] = (R)0;
   } else {
     dc[0] = (R)(ref * cos(alpha)); dc[1] = (R)(ref * sin(alpha)); dc[2] = (R)0;
-  }
-  if (g.ny > 1) {
-    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-    RSX_CK(rsx::launch_col_fft<R>(c->p, g.ny, g.nx, g.nx, 3LL * g.nz, (long long)g.nx * g.ny,
-                                  c->twy, s),
-           "y-FFT kernel");
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
   RSX_CK(rsx::launch_ewald<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, true, dc, img,
@@ -604,11 +606,12 @@ template <typename R>
 int fft3d_impl(rsx_context* c, void* p, cudaStream_t s) {
   const rsx_config& g = c->cfg;
   RSX_CK(rsx::launch_row_fft<R>(p, g.nx, 3LL * g.ny * g.nz, c->twx, s), "x-FFT kernel");
-  RSX_CK(rsx::launch_col_fft<R>(p, g.ny, g.nx, g.nx, 3LL * g.nz, (long long)g.nx * g.ny, c->twy, s),
+  RSX_CK(rsx::launch_col_fft<R>(p, g.ny, g.nx, g.nx, {3LL * g.nz, g.nz, c->N, c->npix, 0}, c->twy, s),
          "y-FFT kernel");
   if (g.nz == 1) return RSX_OK;
   if (is_pow2(g.nz) && g.nz <= 4096) {
-    RSX_CK(rsx::launch_col_fft<R>(p, g.nz, c->npix, c->npix, 3, c->N, c->twz, s), "z-FFT kernel");
+    RSX_CK(rsx::launch_col_fft<R>(p, g.nz, c->npix, c->npix, {3, 1, c->N, 0, 0}, c->twz, s),
+           "z-FFT kernel");
   } else {
     RSX_CK(rsx::launch_dft_z<R>(p, c->p, g.nx, g.ny, g.nz, c->twz, s), "z-DFT kernel");
     RSX_CK(cudaMemcpyAsync(p, c->p, 3 * (size_t)c->N * sizeof(R) * 2, cudaMemcpyDeviceToDevice, s),

@@ -106,6 +106,14 @@ __device__ __forceinline__ void pol_final(const PolAcc<R>& acc, const PolParams<
   out[2] = RT<R>::mk(acc.b[2][0] * inv, acc.b[2][1] * inv);
 }
 
+// Loads of data read once per pass (the morphology, N_t): streaming hint, so
+// that they do not push the x-transformed slices out of L2 before the y pass
+// reads them back.
+__device__ __forceinline__ float4 ld_stream(const float4* p) { return __ldcs(p); }
+__device__ __forceinline__ double4_32a ld_stream(const double4_32a* p) { return *p; }
+__device__ __forceinline__ float2 ld_stream(const float2* p) { return __ldcs(p); }
+__device__ __forceinline__ double2 ld_stream(const double2* p) { return __ldcs(p); }
+
 template <typename R>
 __device__ __forceinline__ void load_m(const typename RT<R>::V4* M, size_t i, R& v, R& s, R& ph,
                                        R& th) {
@@ -125,8 +133,9 @@ __device__ __forceinline__ void load_m(const typename RT<R>::V4* M, size_t i, R&
 // diagonal) instead of the morphology, and p = N_t . e.
 template <typename R, int T, int EC, bool DO_FFT, int LOGNX, bool FROM_NT>
 __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_pol_fftx(const typename RT<R>::V4* __restrict__ M,
-                                                long long N, int lognx_rt, long long nrows,
-                                                PolParams<R> pp, typename RT<R>::C* __restrict__ p,
+                                                long long N, int lognx_rt, long long row_begin,
+                                                long long row_end, PolParams<R> pp,
+                                                typename RT<R>::C* __restrict__ p,
                                                 const typename RT<R>::C* __restrict__ twx,
                                                 int tw_in_smem,
                                                 const typename RT<R>::C* __restrict__ nt) {
@@ -139,8 +148,8 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
   const int lognx = LOGNX >= 0 ? LOGNX : lognx_rt;
   const int nx = 1 << lognx;
   const int ROWS = EC >> lognx;
-  const long long row0 = (long long)blockIdx.x * ROWS;
-  const long long rl = nrows - row0;
+  const long long row0 = row_begin + (long long)blockIdx.x * ROWS;
+  const long long rl = row_end - row0;
   const int rows_here = rl < ROWS ? (int)rl : ROWS;
   const int nel = rows_here << lognx;
   const size_t vox0 = (size_t)row0 << lognx;
@@ -157,7 +166,7 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
         const size_t i = vox0 + e;
         C t[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) t[q] = nt[q * (size_t)N + i];
+        for (int q = 0; q < 5; ++q) t[q] = ld_stream(nt + q * (size_t)N + i);
         const R ce = pp.ce, se = pp.se;
         // p = N_t . e with e = (ce, se, 0): columns x and y of N_t
         C px = RT<R>::mk(t[0].x * ce + t[1].x * se + inv_ref * ce, t[0].y * ce + t[1].y * se);
@@ -191,7 +200,7 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
 #pragma unroll
   for (int sl = 0; sl < SLOTS; ++sl) {
     const int e = threadIdx.x + sl * T;
-    if (e < nel) cur[sl] = M[vox0 + e];
+    if (e < nel) cur[sl] = ld_stream(M + vox0 + e);
   }
   for (int j = 0; j < pp.c; ++j) {
     if (j + 1 < pp.c) {
@@ -199,7 +208,7 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
 #pragma unroll
       for (int sl = 0; sl < SLOTS; ++sl) {
         const int e = threadIdx.x + sl * T;
-        if (e < nel) nxt[sl] = Mj[e];
+        if (e < nel) nxt[sl] = ld_stream(Mj + e);
       }
     }
 #pragma unroll
@@ -267,65 +276,51 @@ __global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p
 }
 
 // Column FFTs: element i of column col of batch b sits at
-//   data[b * batch_stride + i * S + tile * TX + col],  i < L = 2^logL.
-// A tile is TX = 2^logTX adjacent columns (coalesced rows of TX complex
-// values) of one batch.  Used for y (S = nx, W = nx, batches = 3 nz) and for
-// z (S = W = nx ny, batches = 3).  The kernel is persistent: each CTA walks
-// tiles blockIdx.x, blockIdx.x + gridDim.x, ... and, while it transforms one
-// tile, the next one is already arriving by cp.async in the second buffer.
+//   data[off(b) + i * S + tile * TX + col],  i < L = 2^logL,
+//   off(b) = base + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo
+// (batches = (component, z-slice) pairs for y, components for z).  One CTA
+// transforms TX = 2^logTX adjacent columns (coalesced rows of TX complex
+// values) of one batch; the tile arrives by cp.async, NLD copies per thread
+// in flight, without passing registers.
 template <typename R, int T, int EC, int LOGL>
-__global__ void __launch_bounds__(T, 2) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
+__global__ void __launch_bounds__(T, 3) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
                                                long long S, int logTX_rt, long long ntiles,
-                                               long long total, long long batch_stride,
+                                               long long bdiv, long long stride_hi,
+                                               long long stride_lo, long long base_off,
                                                const typename RT<R>::C* __restrict__ tw_g,
                                                int tw_in_smem) {
   using C = typename RT<R>::C;
   constexpr int NLD = EC / T;
-  constexpr int PB = padded(EC);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);  // two tiles [L][TX], padded
-  C* tws = buf + 2 * PB;
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [L][TX], padded
+  C* tws = buf + padded(EC);
   // with LOGL fixed, TX = EC / L is fixed too
   const int logL = LOGL >= 0 ? LOGL : logL_rt;
   const int logTX = LOGL >= 0 ? ilog2_ct(EC >> (LOGL >= 0 ? LOGL : 0)) : logTX_rt;
   const int L = 1 << logL;
   const int TX = 1 << logTX;
-  const int nel = L << logTX;
-  auto base_of = [&](long long t) {
-    return data + (t / ntiles) * batch_stride + (t % ntiles) * TX;
-  };
-  auto issue = [&](long long t, C* dst) {
-    const C* base = base_of(t);
-#pragma unroll
-    for (int it = 0; it < NLD; ++it) {
-      const int e = threadIdx.x + it * T;
-      if (e < nel) cp_async_elem(dst + padi(e), base + (size_t)(e >> logTX) * S + (e & (TX - 1)));
-    }
-  };
+  const long long tile = (long long)blockIdx.x % ntiles;
+  const long long b = (long long)blockIdx.x / ntiles;
+  C* base = data + base_off + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo + tile * TX;
   if (tw_in_smem)
     for (int i = threadIdx.x; i < L; i += T) tws[i] = tw_g[i];
-  const C* tw = tw_in_smem ? tws : tw_g;
-  long long t = blockIdx.x;
-  if (t < total) issue(t, buf);
-  cp_async_commit();
-  for (int i = 0; t < total; t += gridDim.x, ++i) {
-    C* cur = buf + (i & 1) * PB;
-    const long long tn = t + gridDim.x;
-    if (tn < total) issue(tn, buf + ((i + 1) & 1) * PB);
-    cp_async_commit();
-    cp_async_wait<1>();  // everything but the prefetch just issued has landed
-    __syncthreads();
-    if constexpr (LOGL >= 0)
-      block_fft_ct<R, LOGL, (EC >> LOGL), 1, (EC >> LOGL), T, true>(cur, tw);
-    else
-      block_fft<R, EC, T, true>(cur, logL, TX, logTX, 1, TX, tw);
-    C* base = base_of(t);
+  const int nel = L << logTX;
 #pragma unroll
-    for (int it = 0; it < NLD; ++it) {
-      const int e = threadIdx.x + it * T;
-      if (e < nel) base[(size_t)(e >> logTX) * S + (e & (TX - 1))] = cur[padi(e)];
-    }
-    __syncthreads();  // cur is refilled by the prefetch of the iteration after next
+  for (int it = 0; it < NLD; ++it) {
+    const int e = threadIdx.x + it * T;
+    if (e < nel) cp_async_elem(buf + padi(e), base + (size_t)(e >> logTX) * S + (e & (TX - 1)));
+  }
+  cp_async_wait_all();
+  __syncthreads();
+  const C* tw = tw_in_smem ? tws : tw_g;
+  if constexpr (LOGL >= 0)
+    block_fft_ct<R, LOGL, (EC >> LOGL), 1, (EC >> LOGL), T, true>(buf, tw);
+  else
+    block_fft<R, EC, T, true>(buf, logL, TX, logTX, 1, TX, tw);
+#pragma unroll
+  for (int it = 0; it < NLD; ++it) {
+    const int e = threadIdx.x + it * T;
+    if (e < nel) base[(size_t)(e >> logTX) * S + (e & (TX - 1))] = buf[padi(e)];
   }
 }
 
@@ -362,7 +357,7 @@ __global__ void k_geometry(Geo<R>* __restrict__ geo, int nx, int ny, int nz, dou
                            double k) {
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= (long long)nx * ny) return;
-  const int mx = (int)(pix % nx), my = (int)(pix / nx);
+  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
   const int fx = mx < (nx + 1) / 2 ? mx : mx - nx;
   const int fy = my < (ny + 1) / 2 ? my : my - ny;
   const double two_pi = 6.283185307179586476925286766559;
@@ -438,8 +433,8 @@ __global__ void __launch_bounds__(256) k_ewald_full(const typename RT<R>::C* __r
   const long long npix = (long long)nx * ny;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
-  const int mx = (int)(pix % nx), my = (int)(pix / nx);
-  R* dst = img + (size_t)((my + ny / 2) % ny) * nx + (mx + nx / 2) % nx;
+  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
+  R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
   const Geo<R> g = geo[pix];
   if (g.b0 < 0) {
     *dst = R(0);
@@ -547,8 +542,8 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const long long pix = pix0 + q;
-    const int mx = (int)(pix % nx), my = (int)(pix / nx);
-    R* dst = img + (size_t)((my + ny / 2) % ny) * nx + (mx + nx / 2) % nx;
+    const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
+    R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
     *dst = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
   }
 }
@@ -671,8 +666,8 @@ __global__ void __launch_bounds__(256) k_ewald_linear(const typename RT<R>::C* _
   const long long npix = (long long)nx * ny;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
-  const int mx = (int)(pix % nx), my = (int)(pix / nx);
-  R* dst = img + (size_t)((my + ny / 2) % ny) * nx + (mx + nx / 2) % nx;
+  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
+  R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
   const Geo<R> g = geo[pix];
   if (g.b0 < 0) {
     *dst = R(0);
@@ -804,29 +799,32 @@ __global__ void k_rotate_acc(const R* __restrict__ img, R* __restrict__ acc, int
     acc[pix] += img[pix];
     return;
   }
-  const int ix = (int)(pix % nx), iy = (int)(pix / nx);
+  // The source position and its integer part in FP64 (so the choice of the
+  // four neighbours matches an FP64 evaluation); the weights and the sum in
+  // the working precision.
+  const int ix = (int)pix & (nx - 1), iy = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
   const int cx = nx / 2, cy = ny / 2;
-  const double rxy = (double)nx / ny, ryx = (double)ny / nx;
-  const double fx = cx + ca * (ix - cx) - sa * rxy * (iy - cy);
-  const double fy = cy + sa * ryx * (ix - cx) + ca * (iy - cy);
+  const double dx = ix - cx, dy = iy - cy;
+  const double fx = cx + (ca * dx - (sa * ((double)nx / ny)) * dy);
+  const double fy = cy + ((sa * ((double)ny / nx)) * dx + ca * dy);
   const double x0f = floor(fx), y0f = floor(fy);
-  const double tx = fx - x0f, ty = fy - y0f;
-  const long long x0 = (long long)x0f, y0 = (long long)y0f;
-  double val = 0.0;
+  const R tx = (R)(fx - x0f), ty = (R)(fy - y0f);
+  const int x0 = (int)x0f, y0 = (int)y0f;
+  R val = R(0);
 #pragma unroll
-  for (int dy = 0; dy < 2; ++dy) {
-    const long long yy = y0 + dy;
+  for (int dyy = 0; dyy < 2; ++dyy) {
+    const int yy = y0 + dyy;
     if (yy < 0 || yy >= ny) continue;
-    const double wy = dy ? ty : 1.0 - ty;
+    const R wy = dyy ? ty : R(1) - ty;
 #pragma unroll
-    for (int dx = 0; dx < 2; ++dx) {
-      const long long xx = x0 + dx;
+    for (int dxx = 0; dxx < 2; ++dxx) {
+      const int xx = x0 + dxx;
       if (xx < 0 || xx >= nx) continue;
-      const double wx = dx ? tx : 1.0 - tx;
-      val += wy * wx * (double)img[yy * nx + xx];
+      const R wx = dxx ? tx : R(1) - tx;
+      val += wy * wx * img[(size_t)yy * nx + xx];
     }
   }
-  acc[pix] += (R)val;
+  acc[pix] += val;
 }
 
 template <typename R>
@@ -856,12 +854,15 @@ static inline unsigned grid1(long long n, int t) { return (unsigned)((n + t - 1)
 
 template <typename R, int T, int EC, bool DO_FFT, int LOGNX, bool FROM_NT>
 static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
-                                 void* p, const void* twx, const void* nt, cudaStream_t s) {
+                                 void* p, const void* twx, const void* nt, long long row_begin,
+                                 long long row_count, cudaStream_t s) {
   using C = typename RT<R>::C;
   const long long N = (long long)nx * ny * nz;
   // Without the FFT the voxels are independent: treat them as N rows of one.
   const int lognx = DO_FFT ? ilog2(nx) : 0;
-  const long long nrows = DO_FFT ? (long long)ny * nz : N;
+  long long nrows = DO_FFT ? (long long)ny * nz : N;
+  if (DO_FFT && row_count >= 0) nrows = row_count;
+  else row_begin = 0;
   const int rows = DO_FFT ? EC / nx : EC;
   size_t smem = DO_FFT ? padded(3 * EC) * sizeof(C) : 0;
   int tw_in_smem = 0;
@@ -872,38 +873,48 @@ static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const Po
   auto kern = k_pol_fftx<R, T, EC, DO_FFT, LOGNX, FROM_NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid1(nrows, rows), T, smem, s>>>((const typename RT<R>::V4*)M, N, lognx, nrows, pp,
-                                           (C*)p, (const C*)twx, tw_in_smem, (const C*)nt);
+  if (nrows <= 0) return cudaSuccess;
+  kern<<<grid1(nrows, rows), T, smem, s>>>((const typename RT<R>::V4*)M, N, lognx, row_begin,
+                                           row_begin + nrows, pp, (C*)p, (const C*)twx,
+                                           tw_in_smem, (const C*)nt);
   return cudaGetLastError();
 }
 
 template <typename R, bool FROM_NT>
 static cudaError_t pol_fftx_dispatch(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                                      bool do_fft, void* p, const void* twx, const void* nt,
-                                     cudaStream_t s) {
+                                     long long rb, long long rc, cudaStream_t s) {
   if (!do_fft)
-    return pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
-#define RSX_POL(L) \
-  case L: return pol_fftx_impl<R, 256, 1024, true, L, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+    return pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+#define RSX_POL(L)                                                                                \
+  case L:                                                                                         \
+    return pol_fftx_impl<R, 256, 1024, true, L, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
   switch (ilog2(nx)) {
     RSX_POL(6) RSX_POL(7) RSX_POL(8) RSX_POL(9) RSX_POL(10)
-    case 11: return pol_fftx_impl<R, 256, 2048, true, 11, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
-    case 12: return pol_fftx_impl<R, 512, 4096, true, 12, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
-    default: return pol_fftx_impl<R, 256, 1024, true, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, s);
+    case 11:
+      return pol_fftx_impl<R, 256, 2048, true, 11, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+    case 12:
+      return pol_fftx_impl<R, 512, 4096, true, 12, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+    default:
+      return pol_fftx_impl<R, 256, 1024, true, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
   }
 #undef RSX_POL
 }
 
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
-                            bool do_fft, void* p, const void* twx, cudaStream_t s) {
-  return pol_fftx_dispatch<R, false>(M, nx, ny, nz, pp, do_fft, p, twx, nullptr, s);
+                            bool do_fft, void* p, const void* twx, cudaStream_t s,
+                            long long row_begin, long long row_count) {
+  return pol_fftx_dispatch<R, false>(M, nx, ny, nz, pp, do_fft, p, twx, nullptr, row_begin,
+                                     row_count, s);
 }
 
 template <typename R>
 cudaError_t launch_ntp_fftx(const void* nt, int nx, int ny, int nz, const PolParams<R>& pp,
-                            bool do_fft, void* p, const void* twx, cudaStream_t s) {
-  return pol_fftx_dispatch<R, true>(nullptr, nx, ny, nz, pp, do_fft, p, twx, nt, s);
+                            bool do_fft, void* p, const void* twx, cudaStream_t s,
+                            long long row_begin, long long row_count) {
+  return pol_fftx_dispatch<R, true>(nullptr, nx, ny, nz, pp, do_fft, p, twx, nt, row_begin,
+                                    row_count, s);
 }
 
 template <typename R, int T, int EC>
@@ -928,20 +939,9 @@ cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cu
   return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s);
 }
 
-static int sm_count() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
-      n = 1;
-  }
-  return n;
-}
-
 template <typename R, int T, int EC, int LOGL>
-static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long long nbatch,
-                                long long batch_stride, const void* tw, cudaStream_t s) {
+static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, const ColBatches& bt,
+                                const void* tw, cudaStream_t s) {
   using C = typename RT<R>::C;
   if (L > EC) return cudaErrorInvalidValue;
   long long TX = EC / L;
@@ -950,8 +950,9 @@ static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long l
   if (LOGL >= 0 && TX != EC / L) return cudaErrorInvalidValue;
   const int logTX = ilog2(TX);
   const long long ntiles = W / TX;
-  const long long total = ntiles * nbatch;
-  size_t smem = 2 * (size_t)padded(EC) * sizeof(C);
+  const long long total = ntiles * bt.nbatch;
+  if (total <= 0) return cudaSuccess;
+  size_t smem = (size_t)padded(EC) * sizeof(C);
   int tw_in_smem = 0;
   if (smem + L * sizeof(C) <= 200 * 1024) {
     smem += L * sizeof(C);
@@ -960,39 +961,33 @@ static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, long l
   auto kern = k_col_fft<R, T, EC, LOGL>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, T, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  long long grid = (long long)per_sm * sm_count();
-  if (grid > total) grid = total;
-  kern<<<(unsigned)grid, T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles, total, batch_stride,
-                                       (const C*)tw, tw_in_smem);
+  kern<<<(unsigned)total, T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles, bt.bdiv, bt.stride_hi,
+                                        bt.stride_lo, bt.base, (const C*)tw, tw_in_smem);
   return cudaGetLastError();
 }
 
 template <typename R, int EC>
-static cudaError_t col_fft_dispatch(void* p, int L, long long S, long long W, long long nbatch,
-                                    long long batch_stride, const void* tw, cudaStream_t s) {
+static cudaError_t col_fft_dispatch(void* p, int L, long long S, long long W, const ColBatches& bt,
+                                    const void* tw, cudaStream_t s) {
   const int logL = ilog2(L);
   if (W >= EC / L) {
     switch (logL) {
 #define RSX_COL(LL) \
-  case LL: return col_fft_impl<R, 256, EC, LL>(p, L, S, W, nbatch, batch_stride, tw, s);
+  case LL: return col_fft_impl<R, 256, EC, LL>(p, L, S, W, bt, tw, s);
       RSX_COL(5) RSX_COL(6) RSX_COL(7) RSX_COL(8) RSX_COL(9) RSX_COL(10) RSX_COL(11) RSX_COL(12)
 #undef RSX_COL
       default: break;
     }
   }
-  return col_fft_impl<R, 256, EC, -1>(p, L, S, W, nbatch, batch_stride, tw, s);
+  return col_fft_impl<R, 256, EC, -1>(p, L, S, W, bt, tw, s);
 }
 
 template <typename R>
-cudaError_t launch_col_fft(void* p, int L, long long S, long long W, long long nbatch,
-                           long long batch_stride, const void* tw, cudaStream_t s) {
+cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
+                           const void* tw, cudaStream_t s) {
   if (L == 1) return cudaSuccess;
   // 4096 elements per CTA: 34 KB (FP32) or 70 KB (FP64) of padded tile
-  return col_fft_dispatch<R, 4096>(p, L, S, W, nbatch, batch_stride, tw, s);
+  return col_fft_dispatch<R, 4096>(p, L, S, W, bt, tw, s);
 }
 
 template <typename R>
@@ -1105,9 +1100,9 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
 
 #define RSX_INSTANTIATE(R)                                                                        \
   template cudaError_t launch_pol_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \
-                                          void*, const void*, cudaStream_t);                      \
+                                          void*, const void*, cudaStream_t, long long, long long);\
   template cudaError_t launch_row_fft<R>(void*, int, long long, const void*, cudaStream_t);       \
-  template cudaError_t launch_col_fft<R>(void*, int, long long, long long, long long, long long,  \
+  template cudaError_t launch_col_fft<R>(void*, int, long long, long long, const ColBatches&,     \
                                          const void*, cudaStream_t);                              \
   template cudaError_t launch_dft_z<R>(const void*, void*, int, int, int, const void*,            \
                                        cudaStream_t);                                             \
@@ -1119,7 +1114,7 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
   template cudaError_t launch_scale<R>(const void*, void*, long long, double, cudaStream_t);      \
   template cudaError_t launch_validate<R>(const void*, long long, int*, cudaStream_t);          \
   template cudaError_t launch_ntp_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \
-                                          void*, const void*, cudaStream_t);                      \
+                                          void*, const void*, cudaStream_t, long long, long long);\
   template cudaError_t launch_nt_all<R>(const void*, long long, const PolParams<R>&, void*,       \
                                         cudaStream_t);                                            \
   template cudaError_t launch_nt_comp<R>(const void*, long long, long long, long long, int, bool, \

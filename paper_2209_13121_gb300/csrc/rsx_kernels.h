@@ -35,14 +35,18 @@ template <typename R> struct __align__(16) Geo {
 // Sets the message returned by rsx_last_error() on this host thread.
 void set_last_error(const char* msg);
 
+// Rows are (z, y) pairs; row_begin / row_count restrict the launch to a
+// range of rows (a group of z-slices); row_count < 0 means all rows.
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
-                            bool do_fft, void* p, const void* twx, cudaStream_t s);
+                            bool do_fft, void* p, const void* twx, cudaStream_t s,
+                            long long row_begin = 0, long long row_count = -1);
 // Algorithm 2: p = N_t . e from nt[5][N] (xx, xy, yy, xz, yz), fused with
 // the x-FFT like launch_pol_fftx.
 template <typename R>
 cudaError_t launch_ntp_fftx(const void* nt, int nx, int ny, int nz, const PolParams<R>& pp,
-                            bool do_fft, void* p, const void* twx, cudaStream_t s);
+                            bool do_fft, void* p, const void* twx, cudaStream_t s,
+                            long long row_begin = 0, long long row_count = -1);
 // Algorithm 3: N_t from device-resident M (all components), or one
 // component's staged voxel range [off, off + n) added to it.
 template <typename R>
@@ -63,9 +67,14 @@ cudaError_t launch_ewald_linear(const void* bins, int nx, int ny, const Geo<R>* 
                                 bool literal, void* img, cudaStream_t s);
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s);
+// Batches of a column-FFT launch: batch b starts at
+// base + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo (complex elements).
+struct ColBatches {
+  long long nbatch, bdiv, stride_hi, stride_lo, base;
+};
 template <typename R>
-cudaError_t launch_col_fft(void* p, int L, long long S, long long W, long long nbatch,
-                           long long batch_stride, const void* tw, cudaStream_t s);
+cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
+                           const void* tw, cudaStream_t s);
 template <typename R>
 cudaError_t launch_dft_z(const void* in, void* out, int nx, int ny, int nz, const void* twz,
                          cudaStream_t s);

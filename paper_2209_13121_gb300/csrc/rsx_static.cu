@@ -156,7 +156,8 @@ int rsx_scatter_angle_noalloc(const void* M, int nx, int ny, int nz, int n_compo
     return fail(RSX_ERR_CUDA, "geometry kernel: %s", cudaGetErrorString(e));
   if ((e = rsx::launch_pol_fftx<float>(M, nx, ny, nz, pp, true, p, twx, s)) != cudaSuccess)
     return fail(RSX_ERR_CUDA, "polarisation + x-FFT kernel: %s", cudaGetErrorString(e));
-  if ((e = rsx::launch_col_fft<float>(p, ny, nx, nx, 3LL * nz, npix, twy, s)) != cudaSuccess)
+  if ((e = rsx::launch_col_fft<float>(p, ny, nx, nx, {3LL * nz, nz, N, npix, 0}, twy, s)) !=
+      cudaSuccess)
     return fail(RSX_ERR_CUDA, "y-FFT kernel: %s", cudaGetErrorString(e));
   if ((e = rsx::launch_ewald<float>(p, nx, ny, nz, geo, twz, true, dc, img_out, s)) != cudaSuccess)
     return fail(RSX_ERR_CUDA, "Ewald kernel: %s", cudaGetErrorString(e));
