@@ -214,7 +214,7 @@ def run_ours(args):
         t_ms, n_l = phases[top]
         bytes_per_voxel = per_voxel[top]
         achieved = (bytes_per_voxel * N * n_l) / (t_ms / 1e3) / 1e9 if n_l else None
-    traffic = _traffic_from_profiles(args.workload, top, prec)
+    traffic = _traffic_from_profiles(args.workload, top, prec) if args.algorithm == 1 else None
 
     # end to end through the public API: host morphology in, host image out
     e2e = None
@@ -283,15 +283,18 @@ def run_ours(args):
 
 
 def _traffic_from_profiles(workload, kernel, prec):
-    """DRAM bytes per launch recorded by the committed ncu summary for this
-    kernel and workload, when one exists (else None)."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of this kernel and workload recorded from an ncu
+    capture in profiles/traffic.txt (None when there is none)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         with open(path) as f:
-            d = json.load(f)
-        return d[f"{workload}/{kernel}/f{prec}"]["bytes_per_launch"]
-    except Exception:
-        return None
+            for line in f:
+                parts = line.split("#")[0].split()
+                if len(parts) == 2 and parts[0] == f"{workload}/{kernel}/f{prec}":
+                    return float(parts[1])
+    except OSError:
+        pass
+    return None
 
 
 def cpu_baseline(W, args, angles_sample=10):

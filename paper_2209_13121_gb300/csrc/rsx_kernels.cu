@@ -790,26 +790,37 @@ __global__ void k_nt_restore(const typename RT<R>::C* __restrict__ nt, typename 
 // ------------------------------------------------------- detector rotation
 // acc(Q) += img(U(alpha) Q), bilinear, zero outside; pixel coordinates in
 // fftshift order with centre (nx/2, ny/2) and the q-spacing ratio nx/ny.
+// One 16 x 16 tile of output pixels per CTA, so that the source footprint
+// of a CTA is a compact rotated square.  The source position is computed in
+// fixed point with 48 fractional bits: cos/sin (times the aspect ratio) are
+// integers scaled by 2^48 and the offsets from the centre are integers, so
+// the only error is the coefficients' rounding, 2^-49 of a pixel per pixel
+// of offset (an FP64 evaluation errs by about 2^-52 |position|); every term
+// stays below 2^60 for n <= 4096.  The floor is a shift and the fraction a
+// mask (no FP64 arithmetic).
+constexpr int kRotTile = 16;
 template <typename R>
-__global__ void k_rotate_acc(const R* __restrict__ img, R* __restrict__ acc, int nx, int ny,
-                             double ca, double sa, int rotate) {
-  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pix >= (long long)nx * ny) return;
+__global__ void __launch_bounds__(kRotTile * kRotTile) k_rotate_acc(const R* __restrict__ img,
+                                                                    R* __restrict__ acc, int nx,
+                                                                    int ny, long long cxx,
+                                                                    long long cxy, long long cyx,
+                                                                    long long cyy, int rotate) {
+  const int ix = blockIdx.x * kRotTile + threadIdx.x;
+  const int iy = blockIdx.y * kRotTile + threadIdx.y;
+  if (ix >= nx || iy >= ny) return;
+  const size_t pix = (size_t)iy * nx + ix;
   if (!rotate) {
     acc[pix] += img[pix];
     return;
   }
-  // The source position and its integer part in FP64 (so the choice of the
-  // four neighbours matches an FP64 evaluation); the weights and the sum in
-  // the working precision.
-  const int ix = (int)pix & (nx - 1), iy = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
   const int cx = nx / 2, cy = ny / 2;
-  const double dx = ix - cx, dy = iy - cy;
-  const double fx = cx + (ca * dx - (sa * ((double)nx / ny)) * dy);
-  const double fy = cy + ((sa * ((double)ny / nx)) * dx + ca * dy);
-  const double x0f = floor(fx), y0f = floor(fy);
-  const R tx = (R)(fx - x0f), ty = (R)(fy - y0f);
-  const int x0 = (int)x0f, y0 = (int)y0f;
+  const long long dx = ix - cx, dy = iy - cy;
+  const long long fx = ((long long)cx << 48) + cxx * dx - cxy * dy;
+  const long long fy = ((long long)cy << 48) + cyx * dx + cyy * dy;
+  const int x0 = (int)(fx >> 48), y0 = (int)(fy >> 48);
+  const R scale = R(1.0 / 281474976710656.0);  // 2^-48
+  const R tx = (R)(fx & ((1LL << 48) - 1)) * scale;
+  const R ty = (R)(fy & ((1LL << 48) - 1)) * scale;
   R val = R(0);
 #pragma unroll
   for (int dyy = 0; dyy < 2; ++dyy) {
@@ -821,7 +832,7 @@ __global__ void k_rotate_acc(const R* __restrict__ img, R* __restrict__ acc, int
       const int xx = x0 + dxx;
       if (xx < 0 || xx >= nx) continue;
       const R wx = dxx ? tx : R(1) - tx;
-      val += wy * wx * img[(size_t)yy * nx + xx];
+      val += wy * wx * __ldg(img + (size_t)yy * nx + xx);
     }
   }
   acc[pix] += val;
@@ -1080,8 +1091,17 @@ cudaError_t launch_nt_restore(const void* nt, void* out, long long N, double ref
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s) {
-  k_rotate_acc<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>(
-      (const R*)img, (R*)acc, nx, ny, cos(alpha), sin(alpha), rotate ? 1 : 0);
+  // fixed-point (2^-48) coefficients of the map Q -> U(alpha) Q in pixel
+  // units: fx = cx + cos a dx - sin a (nx/ny) dy, fy = cy + sin a (ny/nx) dx + cos a dy
+  const double two48 = 281474976710656.0;
+  const double ca = cos(alpha), sa = sin(alpha);
+  const long long cxx = llround(ca * two48), cyy = cxx;
+  const long long cxy = llround(sa * ((double)nx / ny) * two48);
+  const long long cyx = llround(sa * ((double)ny / nx) * two48);
+  const dim3 block(kRotTile, kRotTile);
+  const dim3 grid((nx + kRotTile - 1) / kRotTile, (ny + kRotTile - 1) / kRotTile);
+  k_rotate_acc<R><<<grid, block, 0, s>>>((const R*)img, (R*)acc, nx, ny, cxx, cxy, cyx, cyy,
+                                          rotate ? 1 : 0);
   return cudaGetLastError();
 }
 
