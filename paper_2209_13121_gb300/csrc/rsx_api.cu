@@ -124,6 +124,7 @@ struct rsx_context {
   void* twx = nullptr;
   void* twy = nullptr;
   void* twz = nullptr;
+  void* tw4 = nullptr;  // four-step twiddles [k2][n1] for 1024-point axes
   int* flag = nullptr;
   // per-phase timing: event pairs recorded around launches while enabled
   bool timing = false;
@@ -138,7 +139,8 @@ struct rsx_context {
 namespace {
 
 void free_all(rsx_context* c) {
-  void* ptrs[] = {c->M_owned, c->p, c->img, c->acc, c->geo, c->twx, c->twy, c->twz, c->flag};
+  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc, c->geo,
+                  c->twx,     c->twy, c->twz, c->tw4, c->flag};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -190,6 +192,37 @@ struct PhaseTimer {
     c->recs.push_back({phase, a, b});
   }
 };
+
+// Four-step twiddles tw4[k2 * 32 + n1] = exp(-2 pi i n1 k2 / 1024).
+int upload_tw4(rsx_context* c) {
+  const int prec = c->cfg.precision;
+  std::vector<double> tw(2 * 1024);
+  for (int k2 = 0; k2 < 32; ++k2)
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const double a = -2.0 * kPi * (double)(n1 * k2) / 1024.0;
+      tw[2 * (k2 * 32 + n1)] = cos(a);
+      tw[2 * (k2 * 32 + n1) + 1] = sin(a);
+    }
+  RSX_CK(cudaMalloc(&c->tw4, complex_size(prec) * 1024), "twiddle table");
+  if (prec == 64) {
+    RSX_CK(cudaMemcpy(c->tw4, tw.data(), 16 * 1024, cudaMemcpyHostToDevice), "twiddle upload");
+  } else {
+    std::vector<float> f(tw.begin(), tw.end());
+    RSX_CK(cudaMemcpy(c->tw4, f.data(), 8 * 1024, cudaMemcpyHostToDevice), "twiddle upload");
+  }
+  return RSX_OK;
+}
+
+// y-FFT of nbatch = k * nz (component, slice) batches: the four-step kernel
+// for ny = 1024, the Stockham column kernel otherwise.
+template <typename R>
+cudaError_t launch_y_fft(rsx_context* c, void* data, long long ncomp, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  const rsx::ColBatches bt = {ncomp * g.nz, g.nz, c->N, c->npix, 0};
+  if (g.ny == 1024 && g.nx % 8 == 0 && c->tw4)
+    return rsx::launch_col_fft4s<R>(data, g.nx, g.nx, bt, c->tw4, s);
+  return rsx::launch_col_fft<R>(data, g.ny, g.nx, g.nx, bt, c->twy, s);
+}
 
 // exp(-2 pi i t / n), t < n, in the context precision.
 int upload_twiddles(rsx_context* c, int n, void** dst) {
@@ -307,9 +340,7 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
   }
   if (g.ny > 1) {
     PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-    RSX_CK(rsx::launch_col_fft<R>(c->ft, g.ny, g.nx, g.nx, {5LL * g.nz, g.nz, c->N, c->npix, 0},
-                                  c->twy, s),
-           "y-FFT kernel");
+    RSX_CK(launch_y_fft<R>(c, c->ft, 5, s), "y-FFT kernel");
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
   const double dc = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
@@ -337,7 +368,11 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
   const PolParams<R> pp = make_params<R>(c, ie, alpha, 0);
   {
     PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    if (g.algorithm == 2) {
+    if (g.nx == 1024) {
+      RSX_CK(rsx::launch_pol_fft4s<R>(c->M, g.algorithm == 2 ? c->nt : nullptr, g.nx, g.ny, g.nz,
+                                      pp, c->p, c->tw4, s),
+             "polarisation + x-FFT kernel");
+    } else if (g.algorithm == 2) {
       RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
              "N_t polarisation + x-FFT kernel");
     } else {
@@ -347,9 +382,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
   }
   if (g.ny > 1) {
     PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-    RSX_CK(rsx::launch_col_fft<R>(c->p, g.ny, g.nx, g.nx, {3LL * g.nz, g.nz, c->N, c->npix, 0},
-                                  c->twy, s),
-           "y-FFT kernel");
+    RSX_CK(launch_y_fft<R>(c, c->p, 3, s), "y-FFT kernel");
   }
   // The constant -(c-1) e' / (4 pi) left out of p before the FFT returns at
   // q = 0 as N times itself (e' = x-hat in the literal frame, e otherwise).
@@ -481,6 +514,11 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
       delete c;
       return rc;
     }
+  }
+  if ((cfg->nx == 1024 || cfg->ny == 1024) && (rc = upload_tw4(c))) {
+    free_all(c);
+    delete c;
+    return rc;
   }
   if ((rc = upload_twiddles(c, cfg->nx, &c->twx)) || (rc = upload_twiddles(c, cfg->ny, &c->twy)) ||
       (rc = upload_twiddles(c, cfg->nz, &c->twz))) {

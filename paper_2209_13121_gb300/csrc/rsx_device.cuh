@@ -19,15 +19,15 @@ template <> struct RT<double> {
   static __host__ __device__ __forceinline__ C mk(double a, double b) { return make_double2(a, b); }
 };
 
-template <typename C> __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
-template <typename C> __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
-template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+template <typename C> __host__ __device__ __forceinline__ C cadd(C a, C b) { a.x += b.x; a.y += b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C csub(C a, C b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename C> __host__ __device__ __forceinline__ C cmul(C a, C b) {
   C r;
   r.x = a.x * b.x - a.y * b.y;
   r.y = a.x * b.y + a.y * b.x;
   return r;
 }
-template <typename C> __device__ __forceinline__ C cmul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
+template <typename C> __host__ __device__ __forceinline__ C cmul_mi(C a) { C r; r.x = a.y; r.y = -a.x; return r; }
 
 // Asynchronous global -> shared copies of one complex element (cp.async):
 // the copy goes straight to shared memory without passing through
@@ -58,7 +58,7 @@ __host__ __device__ constexpr int padded(int n) { return n + (n >> 4) + 1; }
 
 // ------------------------------------------------ in-register small DFTs
 // a * exp(-2 pi i E / 16) for a compile-time E.
-template <int E, typename C> __device__ __forceinline__ C w16(C a) {
+template <int E, typename C> __host__ __device__ __forceinline__ C w16(C a) {
   using R = decltype(a.x);
   constexpr int e = E & 15;
   constexpr double h = 0.70710678118654752440;
@@ -83,14 +83,14 @@ template <int E, typename C> __device__ __forceinline__ C w16(C a) {
   }
 }
 
-template <typename C> __device__ __forceinline__ void dft2(C& a, C& b) {
+template <typename C> __host__ __device__ __forceinline__ void dft2(C& a, C& b) {
   const C t = a;
   a = cadd(t, b);
   b = csub(t, b);
 }
 
 // 4-point forward DFT in place, outputs in natural order.
-template <typename C> __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
+template <typename C> __host__ __device__ __forceinline__ void dft4(C& v0, C& v1, C& v2, C& v3) {
   const C a0 = cadd(v0, v2), a1 = csub(v0, v2);
   const C a2 = cadd(v1, v3), a3 = cmul_mi(csub(v1, v3));
   v0 = cadd(a0, a2);
@@ -106,7 +106,7 @@ template <int RAD> __host__ __device__ constexpr int out_pos(int r) {
   return RAD == 16 ? 4 * (r & 3) + (r >> 2) : RAD == 8 ? 2 * (r & 3) + (r >> 2) : r;
 }
 
-template <int RAD, typename C> __device__ __forceinline__ void dft_reg(C* v) {
+template <int RAD, typename C> __host__ __device__ __forceinline__ void dft_reg(C* v) {
   if constexpr (RAD == 2) {
     dft2(v[0], v[1]);
   } else if constexpr (RAD == 4) {
@@ -143,6 +143,54 @@ template <int RAD, typename C> __device__ __forceinline__ void dft_reg(C* v) {
     dft4(v[8], v[9], v[10], v[11]);
     dft4(v[12], v[13], v[14], v[15]);
   }
+}
+
+// a * exp(-2 pi i E / 32) for a compile-time E in [0, 16).
+template <int E, typename C> __host__ __device__ __forceinline__ C w32(C a) {
+  using R = decltype(a.x);
+  if constexpr (E % 2 == 0) {
+    return w16<E / 2>(a);
+  } else {
+    // cos and sin of pi e / 16 for odd e
+    constexpr double cs[8] = {0.98078528040323044913, 0.83146961230254523708,
+                              0.55557023301960222474, 0.19509032201612826785,
+                              -0.19509032201612826785, -0.55557023301960222474,
+                              -0.83146961230254523708, -0.98078528040323044913};
+    constexpr double sn[8] = {0.19509032201612826785, 0.55557023301960222474,
+                              0.83146961230254523708, 0.98078528040323044913,
+                              0.98078528040323044913, 0.83146961230254523708,
+                              0.55557023301960222474, 0.19509032201612826785};
+    const R c = R(cs[E / 2]), s = R(sn[E / 2]);
+    C r;
+    r.x = a.x * c + a.y * s;
+    r.y = a.y * c - a.x * s;
+    return r;
+  }
+}
+
+template <int K, typename C>
+__host__ __device__ __forceinline__ void dft32_combine(C* v, const C* e, const C* o) {
+  if constexpr (K < 16) {
+    const C t = w32<K>(o[out_pos<16>(K)]);
+    v[K] = cadd(e[out_pos<16>(K)], t);
+    v[K + 16] = csub(e[out_pos<16>(K)], t);
+    dft32_combine<K + 1>(v, e, o);
+  }
+}
+
+// 32-point forward DFT of v[0..32) in registers, natural order in and out:
+// two 16-point DFTs of the even and odd samples, X[k] = E[k] + W32^k O[k],
+// X[k + 16] = E[k] - W32^k O[k].
+template <typename C> __host__ __device__ __forceinline__ void dft32(C* v) {
+  C e[16], o[16];
+#pragma unroll
+  for (int m = 0; m < 16; ++m) {
+    e[m] = v[2 * m];
+    o[m] = v[2 * m + 1];
+  }
+  dft_reg<16>(e);
+  dft_reg<16>(o);
+  dft32_combine<0>(v, e, o);
 }
 
 // ---------------------------------------------------------------------------

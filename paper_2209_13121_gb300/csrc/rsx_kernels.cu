@@ -249,6 +249,148 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
     for (int e = threadIdx.x; e < nel; e += T) p[(size_t)k * N + vox0 + e] = buf[padi(k * EC + e)];
 }
 
+// ------------------------------------------------- four-step 1024-point FFTs
+// N = 1024 = 32 x 32: with n = n1 + 32 n2 and k = k2 + 32 k1,
+//   X[k2 + 32 k1] = sum_n1 W32^(n1 k1) W1024^(n1 k2) sum_n2 x[n1 + 32 n2] W32^(n2 k2).
+// A thread owning n1 holds the 32 samples n2 in registers (32-point DFT),
+// multiplies by W1024^(n1 k2) (table tw4[k2 * 32 + n1]), and after one
+// transpose through shared memory a thread owning k2 does the second
+// 32-point DFT and holds X[k2 + 32 k1] for k1 = 0..31.  One shared-memory
+// round trip instead of three Stockham passes.
+
+// x pass: polarisation of one row into shared memory (as k_pol_fftx), then
+// warps 0..2 each transform one field with warp-level synchronisation only,
+// writing the spectrum straight from registers (coalesced over k2).
+template <typename R, bool FROM_NT>
+__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_pol_fft4s(const typename RT<R>::V4* __restrict__ M,
+                                                      long long N, long long nrows, PolParams<R> pp,
+                                                      typename RT<R>::C* __restrict__ p,
+                                                      const typename RT<R>::C* __restrict__ tw4_g,
+                                                      const typename RT<R>::C* __restrict__ nt) {
+  using C = typename RT<R>::C;
+  using V4 = typename RT<R>::V4;
+  constexpr int T = 256, NX = 1024, SLOTS = NX / T, FS = 32 * 33;  // field stride in smem
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* P = reinterpret_cast<C*>(smem_raw);  // [3][32 * 33]
+  C* tw4 = P + 3 * FS;                     // [32][32]
+  const long long row = blockIdx.x;
+  if (row >= nrows) return;
+  const size_t vox0 = (size_t)row * NX;
+  for (int i = threadIdx.x; i < NX; i += T) tw4[i] = tw4_g[i];
+
+  if constexpr (FROM_NT) {
+    const R inv_ref = pp.add_ref ? R(-(pp.c - 1) / kFourPi) : R(0);
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) {
+      const int e = threadIdx.x + sl * T;
+      const size_t i = vox0 + e;
+      C t[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) t[q] = ld_stream(nt + q * (size_t)N + i);
+      const R ce = pp.ce, se = pp.se;
+      const C px = RT<R>::mk(t[0].x * ce + t[1].x * se + inv_ref * ce, t[0].y * ce + t[1].y * se);
+      const C py = RT<R>::mk(t[1].x * ce + t[2].x * se + inv_ref * se, t[1].y * ce + t[2].y * se);
+      const C pz = RT<R>::mk(t[3].x * ce + t[4].x * se, t[3].y * ce + t[4].y * se);
+      if (pp.literal) {
+        P[e] = RT<R>::mk(ce * px.x + se * py.x, ce * px.y + se * py.y);
+        P[FS + e] = RT<R>::mk(-se * px.x + ce * py.x, -se * px.y + ce * py.y);
+      } else {
+        P[e] = px;
+        P[FS + e] = py;
+      }
+      P[2 * FS + e] = pz;
+    }
+  } else {
+    PolAcc<R> acc[SLOTS];
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) pol_zero(acc[sl]);
+    V4 cur[SLOTS], nxt[SLOTS];
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = ld_stream(M + vox0 + threadIdx.x + sl * T);
+    for (int j = 0; j < pp.c; ++j) {
+      if (j + 1 < pp.c) {
+        const V4* Mj = M + (size_t)(j + 1) * N + vox0;
+#pragma unroll
+        for (int sl = 0; sl < SLOTS; ++sl) nxt[sl] = ld_stream(Mj + threadIdx.x + sl * T);
+      }
+#pragma unroll
+      for (int sl = 0; sl < SLOTS; ++sl)
+        pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
+#pragma unroll
+      for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = nxt[sl];
+    }
+#pragma unroll
+    for (int sl = 0; sl < SLOTS; ++sl) {
+      const int e = threadIdx.x + sl * T;
+      C out[3];
+      pol_final(acc[sl], pp, out);
+      P[e] = out[0];
+      P[FS + e] = out[1];
+      P[2 * FS + e] = out[2];
+    }
+  }
+  __syncthreads();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (w >= 3) return;
+  C* F = P + w * FS;
+  C v[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
+  dft32(v);
+#pragma unroll
+  for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+  __syncwarp();
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
+  __syncwarp();
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+  dft32(v);
+  C* out = p + (size_t)w * N + vox0 + lane;
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+}
+
+// y pass: a tile of TX adjacent columns of one batch.  Thread (n1, col)
+// loads rows n1 + 32 n2 straight from global memory (32 independent loads),
+// transforms over n2 in registers, applies the twiddles and writes row k2 of
+// a [32][32 x TX] shared tile whose row stride 32 TX + 8 keeps both the
+// writes and the transposed reads free of bank conflicts; thread (k2, col)
+// then transforms over n1 and stores rows k2 + 32 k1.
+template <typename R, int TX>
+__global__ void __launch_bounds__(32 * TX, sizeof(R) == 4 ? 2 : 1) k_col_fft4s(typename RT<R>::C* __restrict__ data,
+                                                          long long S, long long ntiles,
+                                                          long long bdiv, long long stride_hi,
+                                                          long long stride_lo, long long base_off,
+                                                          const typename RT<R>::C* __restrict__ tw4_g) {
+  using C = typename RT<R>::C;
+  constexpr int T = 32 * TX, STR = 32 * TX + 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);  // [32][STR]
+  C* tw4 = buf + 32 * STR;                   // [32][32]
+  const long long tile = (long long)blockIdx.x % ntiles;
+  const long long b = (long long)blockIdx.x / ntiles;
+  C* base = data + base_off + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo + tile * TX;
+  const int col = threadIdx.x % TX, n1 = threadIdx.x / TX;
+  C v[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = __ldcs(base + (size_t)(n1 + 32 * n2) * S + col);
+  for (int i = threadIdx.x; i < 1024; i += T) tw4[i] = tw4_g[i];
+  dft32(v);
+  __syncthreads();  // twiddle table in place
+#pragma unroll
+  for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + n1]);
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) buf[k2 * STR + n1 * TX + col] = v[k2];
+  __syncthreads();
+  const int k2 = n1;
+#pragma unroll
+  for (int m = 0; m < 32; ++m) v[m] = buf[k2 * STR + m * TX + col];
+  dft32(v);
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) base[(size_t)(k2 + 32 * k1) * S + col] = v[k1];
+}
+
 // Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d.
 template <typename R, int T, int EC>
 __global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p, int lognx,
@@ -928,6 +1070,47 @@ cudaError_t launch_ntp_fftx(const void* nt, int nx, int ny, int nz, const PolPar
                                     row_count, s);
 }
 
+template <typename R>
+cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int nz,
+                             const PolParams<R>& pp, void* p, const void* tw4, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  if (nx != 1024) return cudaErrorInvalidValue;
+  const long long N = (long long)nx * ny * nz, nrows = (long long)ny * nz;
+  const size_t smem = (3 * 32 * 33 + 1024) * sizeof(C);
+  if (nt) {
+    auto kern = k_pol_fft4s<R, true>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nrows, 256, smem, s>>>(nullptr, N, nrows, pp, (C*)p, (const C*)tw4,
+                                            (const C*)nt);
+  } else {
+    auto kern = k_pol_fft4s<R, false>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)nrows, 256, smem, s>>>((const typename RT<R>::V4*)M, N, nrows, pp, (C*)p,
+                                            (const C*)tw4, nullptr);
+  }
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
+                             const void* tw4, cudaStream_t s) {
+  using C = typename RT<R>::C;
+  constexpr int TX = 8;
+  if (W % TX) return cudaErrorInvalidValue;
+  const long long ntiles = W / TX;
+  const long long total = ntiles * bt.nbatch;
+  if (total <= 0) return cudaSuccess;
+  const size_t smem = (32 * (32 * TX + 8) + 1024) * sizeof(C);
+  auto kern = k_col_fft4s<R, TX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)total, 32 * TX, smem, s>>>((C*)p, S, ntiles, bt.bdiv, bt.stride_hi,
+                                               bt.stride_lo, bt.base, (const C*)tw4);
+  return cudaGetLastError();
+}
+
 template <typename R, int T, int EC>
 static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* twx, cudaStream_t s) {
   using C = typename RT<R>::C;
@@ -1140,6 +1323,10 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
   template cudaError_t launch_nt_comp<R>(const void*, long long, long long, long long, int, bool, \
                                          const PolParams<R>&, void*, cudaStream_t);               \
   template cudaError_t launch_nt_restore<R>(const void*, void*, long long, double, cudaStream_t); \
+  template cudaError_t launch_pol_fft4s<R>(const void*, const void*, int, int, int,               \
+                                           const PolParams<R>&, void*, const void*, cudaStream_t); \
+  template cudaError_t launch_col_fft4s<R>(void*, long long, long long, const ColBatches&,         \
+                                           const void*, cudaStream_t);                            \
   template cudaError_t launch_zbins5<R>(const void*, int, int, int, const Geo<R>*, const void*,    \
                                         double, void*, cudaStream_t);                             \
   template cudaError_t launch_ewald_linear<R>(const void*, int, int, const Geo<R>*, double, bool,  \

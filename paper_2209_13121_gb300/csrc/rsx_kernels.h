@@ -32,6 +32,12 @@ template <typename R> struct __align__(16) Geo {
   R w, rx, ry, rz, k4;
 };
 
+// Batches of a column-FFT launch: batch b starts at
+// base + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo (complex elements).
+struct ColBatches {
+  long long nbatch, bdiv, stride_hi, stride_lo, base;
+};
+
 // Sets the message returned by rsx_last_error() on this host thread.
 void set_last_error(const char* msg);
 
@@ -65,13 +71,17 @@ cudaError_t launch_zbins5(const void* f, int nx, int ny, int nz, const Geo<R>* g
 template <typename R>
 cudaError_t launch_ewald_linear(const void* bins, int nx, int ny, const Geo<R>* geo, double alpha,
                                 bool literal, void* img, cudaStream_t s);
+// Four-step (32 x 32) transforms for 1024-point axes: the x pass fused with
+// the polarisation (from M, or from N_t when nt is given) and the y pass.
+// tw4[k2 * 32 + n1] = exp(-2 pi i n1 k2 / 1024).
+template <typename R>
+cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int nz,
+                             const PolParams<R>& pp, void* p, const void* tw4, cudaStream_t s);
+template <typename R>
+cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
+                             const void* tw4, cudaStream_t s);
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s);
-// Batches of a column-FFT launch: batch b starts at
-// base + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo (complex elements).
-struct ColBatches {
-  long long nbatch, bdiv, stride_hi, stride_lo, base;
-};
 template <typename R>
 cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
                            const void* tw, cudaStream_t s);

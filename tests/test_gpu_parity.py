@@ -86,9 +86,11 @@ CASES = [
     ((2, 1, 8), 2),       # ny = 1
     ((1, 1, 1), 1),       # single voxel
     ((7, 4, 2048), 2),    # nx at the x-FFT tile size, ragged nz
-    ((6, 32, 128), 3),    # fused y-FFT + q_z kernel, ragged nz
-    ((9, 128, 64), 2),    # fused, odd nz
-    ((3, 256, 32), 4),    # fused, tall tile
+    ((6, 32, 128), 3),    # ragged nz
+    ((9, 128, 64), 2),    # odd nz
+    ((3, 256, 32), 4),    # tall column tile
+    ((3, 8, 1024), 3),    # four-step x pass (nx = 1024)
+    ((2, 1024, 16), 2),   # four-step y pass (ny = 1024)
 ]
 IDS = ["x".join(map(str, s)) + f"c{c}" for s, c in CASES]
 
