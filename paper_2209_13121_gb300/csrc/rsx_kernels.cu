@@ -258,18 +258,19 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
 // 32-point DFT and holds X[k2 + 32 k1] for k1 = 0..31.  One shared-memory
 // round trip instead of three Stockham passes.
 
-// x pass: polarisation of one row into shared memory (as k_pol_fftx), then
-// warps 0..2 each transform one field with warp-level synchronisation only,
-// writing the spectrum straight from registers (coalesced over k2).
+// x pass: polarisation of one row into shared memory by four warps (eight
+// voxels per thread, component loads double-buffered), then warps 0..2 each
+// transform one field with warp-level synchronisation only, writing the
+// spectrum straight from registers (coalesced over k2).
 template <typename R, bool FROM_NT>
-__global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_pol_fft4s(const typename RT<R>::V4* __restrict__ M,
+__global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const typename RT<R>::V4* __restrict__ M,
                                                       long long N, long long nrows, PolParams<R> pp,
                                                       typename RT<R>::C* __restrict__ p,
                                                       const typename RT<R>::C* __restrict__ tw4_g,
                                                       const typename RT<R>::C* __restrict__ nt) {
   using C = typename RT<R>::C;
   using V4 = typename RT<R>::V4;
-  constexpr int T = 256, NX = 1024, SLOTS = NX / T, FS = 32 * 33;  // field stride in smem
+  constexpr int T = 128, NX = 1024, SLOTS = NX / T, FS = 32 * 33;  // field stride in smem
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* P = reinterpret_cast<C*>(smem_raw);  // [3][32 * 33]
   C* tw4 = P + 3 * FS;                     // [32][32]
@@ -301,23 +302,18 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_pol_fft4s(const
       P[2 * FS + e] = pz;
     }
   } else {
+    // component-outer: all eight loads of a component issued, then used
     PolAcc<R> acc[SLOTS];
 #pragma unroll
     for (int sl = 0; sl < SLOTS; ++sl) pol_zero(acc[sl]);
-    V4 cur[SLOTS], nxt[SLOTS];
-#pragma unroll
-    for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = ld_stream(M + vox0 + threadIdx.x + sl * T);
     for (int j = 0; j < pp.c; ++j) {
-      if (j + 1 < pp.c) {
-        const V4* Mj = M + (size_t)(j + 1) * N + vox0;
+      const V4* Mj = M + (size_t)j * N + vox0;
+      V4 cur[SLOTS];
 #pragma unroll
-        for (int sl = 0; sl < SLOTS; ++sl) nxt[sl] = ld_stream(Mj + threadIdx.x + sl * T);
-      }
+      for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = ld_stream(Mj + threadIdx.x + sl * T);
 #pragma unroll
       for (int sl = 0; sl < SLOTS; ++sl)
         pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
-#pragma unroll
-      for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = nxt[sl];
     }
 #pragma unroll
     for (int sl = 0; sl < SLOTS; ++sl) {
@@ -354,9 +350,10 @@ __global__ void __launch_bounds__(256, sizeof(R) == 4 ? 2 : 1) k_pol_fft4s(const
 // y pass: a tile of TX adjacent columns of one batch.  Thread (n1, col)
 // loads rows n1 + 32 n2 straight from global memory (32 independent loads),
 // transforms over n2 in registers, applies the twiddles and writes row k2 of
-// a [32][32 x TX] shared tile whose row stride 32 TX + 8 keeps both the
-// writes and the transposed reads free of bank conflicts; thread (k2, col)
-// then transforms over n1 and stores rows k2 + 32 k1.
+// a [32][32 x TX] shared tile whose row stride 33 TX keeps both the writes
+// (32 consecutive elements) and the transposed reads (the TX-wide groups of
+// a half-warp land on disjoint bank windows) free of bank conflicts; thread
+// (k2, col) then transforms over n1 and stores rows k2 + 32 k1.
 template <typename R, int TX>
 __global__ void __launch_bounds__(32 * TX, sizeof(R) == 4 ? 2 : 1) k_col_fft4s(typename RT<R>::C* __restrict__ data,
                                                           long long S, long long ntiles,
@@ -364,7 +361,7 @@ __global__ void __launch_bounds__(32 * TX, sizeof(R) == 4 ? 2 : 1) k_col_fft4s(t
                                                           long long stride_lo, long long base_off,
                                                           const typename RT<R>::C* __restrict__ tw4_g) {
   using C = typename RT<R>::C;
-  constexpr int T = 32 * TX, STR = 32 * TX + 8;
+  constexpr int T = 32 * TX, STR = 33 * TX;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);  // [32][STR]
   C* tw4 = buf + 32 * STR;                   // [32][32]
@@ -1081,13 +1078,13 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
     auto kern = k_pol_fft4s<R, true>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nrows, 256, smem, s>>>(nullptr, N, nrows, pp, (C*)p, (const C*)tw4,
+    kern<<<(unsigned)nrows, 128, smem, s>>>(nullptr, N, nrows, pp, (C*)p, (const C*)tw4,
                                             (const C*)nt);
   } else {
     auto kern = k_pol_fft4s<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)nrows, 256, smem, s>>>((const typename RT<R>::V4*)M, N, nrows, pp, (C*)p,
+    kern<<<(unsigned)nrows, 128, smem, s>>>((const typename RT<R>::V4*)M, N, nrows, pp, (C*)p,
                                             (const C*)tw4, nullptr);
   }
   return cudaGetLastError();
@@ -1102,7 +1099,7 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
   const long long ntiles = W / TX;
   const long long total = ntiles * bt.nbatch;
   if (total <= 0) return cudaSuccess;
-  const size_t smem = (32 * (32 * TX + 8) + 1024) * sizeof(C);
+  const size_t smem = (32 * 33 * TX + 1024) * sizeof(C);
   auto kern = k_col_fft4s<R, TX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
