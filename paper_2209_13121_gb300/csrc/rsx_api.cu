@@ -126,6 +126,7 @@ struct rsx_context {
   void* twz = nullptr;
   void* tw4 = nullptr;  // four-step twiddles [k2][n1] for 1024-point axes
   int* flag = nullptr;
+  int* err = nullptr;  // set by a kernel whose bounded wait timed out
   // per-phase timing: event pairs recorded around launches while enabled
   bool timing = false;
   struct Rec {
@@ -139,8 +140,8 @@ struct rsx_context {
 namespace {
 
 void free_all(rsx_context* c) {
-  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc, c->geo,
-                  c->twx,     c->twy, c->twz, c->tw4, c->flag};
+  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,
+                  c->twx,     c->twy, c->twz, c->tw4, c->flag, c->err};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -395,7 +396,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
   RSX_CK(rsx::launch_ewald<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, true, dc, img,
-                              s),
+                              s, c->err),
          "Ewald kernel");
   return RSX_OK;
 }
@@ -487,6 +488,7 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
       {&c->acc, (size_t)c->npix * R, "Ewald average"},
       {&c->geo, (size_t)c->npix * geo_size(cfg->precision), "Ewald geometry"},
       {(void**)&c->flag, sizeof(int), "validation flag"},
+      {(void**)&c->err, sizeof(int), "kernel error flag"},
   };
   for (auto& a : allocs) {
     e = cudaMalloc(a.dst, a.bytes);
@@ -514,6 +516,13 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
       delete c;
       return rc;
     }
+  }
+  e = cudaMemset(c->err, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    rc = cuda_fail(e, "kernel error flag");
+    free_all(c);
+    delete c;
+    return rc;
   }
   if ((cfg->nx == 1024 || cfg->ny == 1024) && (rc = upload_tw4(c))) {
     free_all(c);
@@ -747,7 +756,15 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
              "result download");
     }
   }
-  if (where == RSX_HOST) RSX_CK(cudaStreamSynchronize(s), "result download");
+  if (where == RSX_HOST) {
+    RSX_CK(cudaStreamSynchronize(s), "result download");
+    int h = 0;
+    RSX_CK(cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost), "kernel error flag");
+    if (h) {
+      cudaMemset(c->err, 0, sizeof(int));
+      return fail(RSX_ERR_CUDA, "a kernel pipeline wait timed out; the result is not valid");
+    }
+  }
   return RSX_OK;
 }
 }  // namespace

@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
 // a half-warp land on disjoint bank windows) free of bank conflicts; thread
 // (k2, col) then transforms over n1 and stores rows k2 + 32 k1.
 template <typename R, int TX>
-__global__ void __launch_bounds__(32 * TX, sizeof(R) == 4 ? 2 : 1) k_col_fft4s(typename RT<R>::C* __restrict__ data,
+__global__ void __launch_bounds__(32 * TX, (sizeof(R) == 4 && TX <= 8) ? 2 : 1) k_col_fft4s(typename RT<R>::C* __restrict__ data,
                                                           long long S, long long ntiles,
                                                           long long bdiv, long long stride_hi,
                                                           long long stride_lo, long long base_off,
@@ -682,6 +682,121 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
   for (int q = 0; q < 2; ++q) {
     const long long pix = pix0 + q;
     const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
+    R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
+    *dst = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
+  }
+}
+
+// Hot path, pipelined: a CTA owns PX consecutive pixels and streams their
+// x/y-transformed slices P(z) through an S-stage ring in shared memory.  For
+// each slice, thread 0 posts the byte count on the stage's mbarrier and
+// issues three 1-D bulk copies (one per component, PX complex each); all
+// threads wait on the barrier's phase, accumulate the two q_z bins of their
+// two pixels from shared memory, synchronise, and the stage is refilled with
+// slice z + S.  Every wait is bounded: on a timeout the CTA records the
+// error in *err, waits (bounded) for its copies in flight, and returns.
+template <typename R, int PX, int S>
+__global__ void __launch_bounds__(PX / 2) k_ewald_tma(const typename RT<R>::C* __restrict__ p,
+                                                      int nx, int ny, int nz,
+                                                      const Geo<R>* __restrict__ geo,
+                                                      const typename RT<R>::C* __restrict__ twz_g,
+                                                      R dc0, R dc1, R dc2, R* __restrict__ img,
+                                                      int* __restrict__ err) {
+  using C = typename RT<R>::C;
+  constexpr unsigned kPoll = 1u << 22;
+  constexpr unsigned kBytes = PX * sizeof(C);
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* stage = reinterpret_cast<C*>(smem_raw);                       // [S][3][PX]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage + S * 3 * PX);
+  C* twz = reinterpret_cast<C*>(bar + S);                           // [nz]
+  const long long npix = (long long)nx * ny;
+  const size_t N = (size_t)npix * nz;
+  const long long pix_base = (long long)blockIdx.x * PX;
+  const C* src = p + pix_base;
+  const int t = threadIdx.x;
+
+  if (t == 0) {
+    for (int st = 0; st < S; ++st) mbar_init(&bar[st], 1);
+    fence_proxy_async();
+  }
+  for (int i = t; i < nz; i += PX / 2) twz[i] = twz_g[i];
+  __syncthreads();
+  auto issue = [&](int z, int st) {
+    mbar_expect_tx(&bar[st], 3 * kBytes);
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      bulk_g2s(stage + (st * 3 + k) * PX, src + k * N + (size_t)z * npix, kBytes, &bar[st]);
+  };
+  if (t == 0)
+    for (int z = 0; z < S && z < nz; ++z) issue(z, z);
+
+  const long long pix0 = pix_base + 2 * t;
+  Geo<R> g[2];
+  g[0] = geo[pix0];
+  g[1] = geo[pix0 + 1];
+  const int s0[2] = {g[0].b0 < 0 ? 0 : g[0].b0, g[1].b0 < 0 ? 0 : g[1].b0};
+  const int s1[2] = {g[0].b1 < 0 ? 0 : g[0].b1, g[1].b1 < 0 ? 0 : g[1].b1};
+  int i0[2] = {0, 0}, i1[2] = {0, 0};
+  C a0[2][3], a1[2][3];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) a0[q][k] = a1[q][k] = RT<R>::mk(0, 0);
+
+  int failed_at = -1;
+  for (int z = 0; z < nz; ++z) {
+    const int st = z % S;
+    const bool ok = mbar_wait_bounded(&bar[st], (z / S) & 1, kPoll);
+    if (__syncthreads_or(!ok)) {
+      failed_at = z;
+      break;
+    }
+    const C* sp = stage + st * 3 * PX + 2 * t;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const C v0 = sp[k * PX], v1 = sp[k * PX + 1];
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const C v = q ? v1 : v0;
+        a0[q][k] = cadd(a0[q][k], cmul(v, twz[i0[q]]));
+        a1[q][k] = cadd(a1[q][k], cmul(v, twz[i1[q]]));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      i0[q] += s0[q];
+      if (i0[q] >= nz) i0[q] -= nz;
+      i1[q] += s1[q];
+      if (i1[q] >= nz) i1[q] -= nz;
+    }
+    __syncthreads();  // every thread is done with this stage
+    if (t == 0 && z + S < nz) {
+      fence_proxy_async();
+      issue(z + S, st);
+    }
+  }
+  if (failed_at >= 0) {
+    if (t == 0) {
+      atomicOr(err, 1);
+      // slices failed_at .. failed_at + S - 1 were issued and not consumed:
+      // let their copies land (bounded) before the CTA's shared memory goes
+      for (int z = failed_at; z < nz && z < failed_at + S; ++z)
+        mbar_wait_bounded(&bar[z % S], (z / S) & 1, kPoll);
+    }
+    return;
+  }
+  if (pix0 == 0) {
+    const R dcs[3] = {dc0, dc1, dc2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (g[0].b0 == 0) a0[0][k].x += dcs[k];
+      if (g[0].b1 == 0) a1[0][k].x += dcs[k];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const long long pix = pix0 + q;
+    const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);
     R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
     *dst = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
   }
@@ -1094,7 +1209,7 @@ template <typename R>
 cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
                              const void* tw4, cudaStream_t s) {
   using C = typename RT<R>::C;
-  constexpr int TX = 8;
+  constexpr int TX = 8;  // 75 KB (FP32) / 151 KB (FP64) of shared memory
   if (W % TX) return cudaErrorInvalidValue;
   const long long ntiles = W / TX;
   const long long total = ntiles * bt.nbatch;
@@ -1200,7 +1315,8 @@ cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm
 
 template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
-                         const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s) {
+                         const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s,
+                         int* err) {
   using C = typename RT<R>::C;
   const long long npix = (long long)nx * ny;
   if (!pruned) {
@@ -1210,6 +1326,16 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
   if (npix == 1) {
     k_ewald_single<R><<<1, 1, 0, s>>>((const C*)p, nz, geo, (const C*)twz, dc[0], dc[1], dc[2],
                                       (R*)img);
+    return cudaGetLastError();
+  }
+  constexpr int PX = 512, S = 4;
+  if (err && npix % PX == 0 && nz <= 4096) {
+    const size_t smem = (size_t)S * 3 * PX * sizeof(C) + S * 8 + (size_t)nz * sizeof(C);
+    auto kern = k_ewald_tma<R, PX, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)(npix / PX), PX / 2, smem, s>>>((const C*)p, nx, ny, nz, geo, (const C*)twz,
+                                                     dc[0], dc[1], dc[2], (R*)img, err);
     return cudaGetLastError();
   }
   const int tw_in_smem = nz <= 4096;
@@ -1308,7 +1434,7 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                        cudaStream_t);                                             \
   template cudaError_t launch_geometry<R>(Geo<R>*, int, int, int, double, double, cudaStream_t);  \
   template cudaError_t launch_ewald<R>(const void*, int, int, int, const Geo<R>*, const void*,     \
-                                       bool, const R*, void*, cudaStream_t);                      \
+                                       bool, const R*, void*, cudaStream_t, int*);                \
   template cudaError_t launch_rotate_acc<R>(const void*, void*, int, int, double, bool,           \
                                             cudaStream_t);                                        \
   template cudaError_t launch_scale<R>(const void*, void*, long long, double, cudaStream_t);      \

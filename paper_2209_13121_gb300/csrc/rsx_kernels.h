@@ -91,9 +91,13 @@ cudaError_t launch_dft_z(const void* in, void* out, int nx, int ny, int nz, cons
 template <typename R>
 cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm, double k,
                             cudaStream_t s);
+// err: device int that records a pipeline timeout (the bulk-copy pipeline
+// of the pruned path is used only when err is given and npix is a multiple
+// of 512).
 template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
-                         const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s);
+                         const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s,
+                         int* err = nullptr);
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s);
