@@ -10,6 +10,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/rsx.h"
 #include "rsx_kernels.h"
 
@@ -125,6 +128,12 @@ struct rsx_context {
   void* twy = nullptr;
   void* twz = nullptr;
   void* tw4 = nullptr;  // four-step twiddles [k2][n1] for 1024-point axes
+  // tensor maps of the p (3 fields) and, for algorithm 3, ft (5 fields)
+  // buffers for the TMA y pass (FP32, ny = 1024); valid when the flag is set
+  alignas(64) CUtensorMap tmap_p;
+  alignas(64) CUtensorMap tmap_ft;
+  bool has_tmap_p = false, has_tmap_ft = false;
+  int n_sm = 0;
   int* flag = nullptr;
   int* err = nullptr;  // set by a kernel whose bounded wait timed out
   // per-phase timing: event pairs recorded around launches while enabled
@@ -214,12 +223,43 @@ int upload_tw4(rsx_context* c) {
   return RSX_OK;
 }
 
-// y-FFT of nbatch = k * nz (component, slice) batches: the four-step kernel
-// for ny = 1024, the Stockham column kernel otherwise.
+// A tensor map over `ncomp` fields of [nz][ny][nx] complex float viewed as
+// [ncomp nz][ny][2 nx] floats with 16 x 256 x 1 boxes (TMA y pass).
+bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  const rsx_config& g = c->cfg;
+  const cuuint64_t dims[3] = {2 * (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)(ncomp * g.nz)};
+  const cuuint64_t strides[2] = {2 * (cuuint64_t)g.nx * sizeof(float),
+                                 (cuuint64_t)g.ny * 2 * g.nx * sizeof(float)};
+  const cuuint32_t box[3] = {16, 256, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// y-FFT of nbatch = k * nz (component, slice) batches: the TMA four-step
+// kernel for FP32 with ny = 1024 (when its tensor map exists), the four-step
+// kernel for ny = 1024, the Stockham column kernel otherwise.
 template <typename R>
 cudaError_t launch_y_fft(rsx_context* c, void* data, long long ncomp, cudaStream_t s) {
   const rsx_config& g = c->cfg;
   const rsx::ColBatches bt = {ncomp * g.nz, g.nz, c->N, c->npix, 0};
+  const CUtensorMap* tm = data == c->p && c->has_tmap_p     ? &c->tmap_p
+                          : data == c->ft && c->has_tmap_ft ? &c->tmap_ft
+                                                             : nullptr;
+  if (sizeof(R) == 4 && tm)
+    return rsx::launch_col_fft4s_tma(tm, data, g.nx, g.nx, bt, c->tw4, c->err, c->n_sm, s);
   if (g.ny == 1024 && g.nx % 8 == 0 && c->tw4)
     return rsx::launch_col_fft4s<R>(data, g.nx, g.nx, bt, c->tw4, s);
   return rsx::launch_col_fft<R>(data, g.ny, g.nx, g.nx, bt, c->twy, s);
@@ -528,6 +568,12 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     free_all(c);
     delete c;
     return rc;
+  }
+  if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
+    c->n_sm = 0;
+  if (cfg->precision == 32 && cfg->ny == 1024 && cfg->nx % 8 == 0 && c->n_sm > 0) {
+    c->has_tmap_p = make_tmap(c, c->p, 3, &c->tmap_p);
+    if (c->ft) c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft);
   }
   if ((rc = upload_twiddles(c, cfg->nx, &c->twx)) || (rc = upload_twiddles(c, cfg->ny, &c->twy)) ||
       (rc = upload_twiddles(c, cfg->nz, &c->twz))) {

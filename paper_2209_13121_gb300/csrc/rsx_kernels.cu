@@ -10,6 +10,7 @@
 //                fused with Eq. (3Dscatter); no 3-D X array exists.
 //   k_rotate_acc detector rotation about q = 0 and accumulation (Sec. 4).
 // All of them are HBM-bound streaming kernels; none is a dense contraction.
+#include <cuda.h>  // CUtensorMap (the type only; the library does not link libcuda)
 #include <math.h>
 
 #include "rsx_device.cuh"
@@ -386,6 +387,86 @@ __global__ void __launch_bounds__(32 * TX, (sizeof(R) == 4 && TX <= 8) ? 2 : 1) 
   dft32(v);
 #pragma unroll
   for (int k1 = 0; k1 < 32; ++k1) base[(size_t)(k2 + 32 * k1) * S + col] = v[k1];
+}
+
+// y pass with tensor-memory-access loads (FP32, ny = 1024): persistent CTAs,
+// one per SM, each walking tiles of 8 columns x 1024 rows.  Thread 0 loads
+// the next-but-one tile with four 3-D TMA boxes (8 complex x 256 rows) into
+// one of two input buffers while all threads transform the current one: the
+// loads of a tile are in flight during the FFT of the previous tile.  The
+// FFT is the four-step scheme of k_col_fft4s.  Waits are bounded; a timeout
+// records *err, drains the copies in flight (bounded) and returns.
+template <typename R>
+__global__ void __launch_bounds__(256, 1) k_col_fft4s_tma(const __grid_constant__ CUtensorMap tmap,
+                                                          typename RT<R>::C* __restrict__ data,
+                                                          long long S, long long ntiles,
+                                                          long long total, long long bdiv,
+                                                          long long stride_hi, long long stride_lo,
+                                                          const typename RT<R>::C* __restrict__ tw4_g,
+                                                          int* __restrict__ err) {
+  using C = typename RT<R>::C;
+  constexpr int TX = 8, T = 256, STR = 33 * TX, TILE = 1024 * TX;
+  constexpr unsigned kPoll = 1u << 22;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  C* in = reinterpret_cast<C*>(smem_raw);  // [2][1024][TX], dense (TMA boxes)
+  C* tr = in + 2 * TILE;                    // [32][STR]
+  C* tw4 = tr + 32 * STR;                   // [32][32]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(tw4 + 1024);
+  const int t = threadIdx.x, col = t % TX, n1 = t / TX;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  for (int i = t; i < 1024; i += T) tw4[i] = tw4_g[i];
+  __syncthreads();
+  auto issue = [&](long long tile_id, int b) {
+    const int ti = (int)(tile_id % ntiles), bb = (int)(tile_id / ntiles);
+    mbar_expect_tx(&bar[b], TILE * sizeof(C));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      tma_load_3d(in + b * TILE + q * 256 * TX, &tmap, ti * 2 * TX, q * 256, bb, &bar[b]);
+  };
+  if (t == 0) {
+    if (blockIdx.x < total) issue(blockIdx.x, 0);
+    if (blockIdx.x + gridDim.x < total) issue(blockIdx.x + gridDim.x, 1);
+  }
+  int i = 0;
+  for (long long tid = blockIdx.x; tid < total; tid += gridDim.x, ++i) {
+    const int b = i & 1;
+    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kPoll);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicOr(err, 1);
+        for (int d = 0; d < 2; ++d)
+          if (tid + d * gridDim.x < total) mbar_wait_bounded(&bar[(i + d) & 1], ((i + d) >> 1) & 1, kPoll);
+      }
+      return;
+    }
+    const C* src = in + b * TILE;
+    C v[32];
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = src[(n1 + 32 * n2) * TX + col];
+    dft32(v);
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + n1]);
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) tr[k2 * STR + n1 * TX + col] = v[k2];
+    __syncthreads();  // input buffer b consumed, transpose complete
+    if (t == 0 && tid + 2 * gridDim.x < total) {
+      fence_proxy_async();
+      issue(tid + 2 * gridDim.x, b);
+    }
+    const int k2 = n1;
+#pragma unroll
+    for (int m = 0; m < 32; ++m) v[m] = tr[k2 * STR + m * TX + col];
+    dft32(v);
+    const long long ti = tid % ntiles, bb = tid / ntiles;
+    C* base = data + (bb / bdiv) * stride_hi + (bb % bdiv) * stride_lo + ti * TX;
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) base[(size_t)(k2 + 32 * k1) * S + col] = v[k1];
+    __syncthreads();  // the transpose buffer is rewritten by the next tile
+  }
 }
 
 // Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d.
@@ -1220,6 +1301,25 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)total, 32 * TX, smem, s>>>((C*)p, S, ntiles, bt.bdiv, bt.stride_hi,
                                                bt.stride_lo, bt.base, (const C*)tw4);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long long W,
+                                 const ColBatches& bt, const void* tw4, int* err, int n_sm,
+                                 cudaStream_t s) {
+  using C = float2;
+  constexpr int TX = 8;
+  if (W % TX || bt.base != 0) return cudaErrorInvalidValue;
+  const long long ntiles = W / TX;
+  const long long total = ntiles * bt.nbatch;
+  if (total <= 0) return cudaSuccess;
+  const size_t smem = (2 * 1024 * TX + 32 * 33 * TX + 1024) * sizeof(C) + 2 * 8;
+  auto kern = k_col_fft4s_tma<float>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = total < n_sm ? total : n_sm;
+  kern<<<(unsigned)grid, 256, smem, s>>>(*(const CUtensorMap*)tmap, (C*)p, S, ntiles, total,
+                                         bt.bdiv, bt.stride_hi, bt.stride_lo, (const C*)tw4, err);
   return cudaGetLastError();
 }
 

@@ -80,6 +80,13 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
 template <typename R>
 cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
                              const void* tw4, cudaStream_t s);
+// The y pass with 2-D tensor (TMA) loads, FP32, ny = 1024, whole-volume
+// batches (bt.base = 0): tmap is a CUtensorMap over the data viewed as
+// [nbatch][ny][2 nx] floats with 16 x 256 x 1 boxes; one persistent CTA per
+// SM (n_sm).
+cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long long W,
+                                 const ColBatches& bt, const void* tw4, int* err, int n_sm,
+                                 cudaStream_t s);
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s);
 template <typename R>
