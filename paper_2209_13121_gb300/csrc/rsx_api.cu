@@ -409,7 +409,17 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
   const PolParams<R> pp = make_params<R>(c, ie, alpha, 0);
   {
     PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    if (g.nx == 1024) {
+    bool done = false;
+    if constexpr (sizeof(R) == 4) {
+      if (g.nx == 1024 && g.algorithm == 1 && c->n_sm > 0 && ((uintptr_t)c->M & 15) == 0) {
+        RSX_CK(rsx::launch_pol_fft4s_tma(c->M, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
+                                         c->n_sm, s),
+               "polarisation + x-FFT kernel");
+        done = true;
+      }
+    }
+    if (done) {
+    } else if (g.nx == 1024) {
       RSX_CK(rsx::launch_pol_fft4s<R>(c->M, g.algorithm == 2 ? c->nt : nullptr, g.nx, g.ny, g.nz,
                                       pp, c->p, c->tw4, s),
              "polarisation + x-FFT kernel");

@@ -348,6 +348,123 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
   for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
 }
 
+// x pass of Algorithm 1 (FP32, nx = 1024) as a bulk-copy pipeline: a
+// producer warp streams (row, component) slices of the morphology, 16 KB
+// each, into a ring of S shared-memory stages (full/empty mbarrier pairs),
+// running up to S slices ahead of the 256 consumer threads.  Consumers
+// accumulate four voxels each, release the stage per warp, write the row's
+// three fields to shared memory, and warps 0..2 transform them as in
+// k_pol_fft4s while the producer already fills the next row's stages.  CTAs
+// are persistent (two per SM) and walk rows with a grid stride.  Every wait
+// is bounded: a timeout sets *err, the producer waits (bounded) for its
+// copies in flight, and all threads return.
+template <int S>
+__global__ void __launch_bounds__(288, 2) k_pol_fft4s_tma(const float4* __restrict__ M, long long N,
+                                                         long long nrows, PolParams<float> pp,
+                                                         float2* __restrict__ p,
+                                                         const float2* __restrict__ tw4_g,
+                                                         int* __restrict__ err) {
+  using C = float2;
+  constexpr int NX = 1024, TC = 256, SL = NX / TC, FS = 32 * 33;
+  constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(float4);
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  float4* stage = reinterpret_cast<float4*>(smem_a128);     // [S][NX]
+  C* P = reinterpret_cast<C*>(stage + S * NX);             // [3][FS]
+  C* tw4 = P + 3 * FS;                                      // [32][32]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(tw4 + 1024);
+  unsigned long long* empty = full + S;
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (t == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], TC / 32);
+    }
+    fence_proxy_async();
+  }
+  for (int i = t; i < 1024; i += blockDim.x) tw4[i] = tw4_g[i];
+  __syncthreads();
+  const long long nmine =
+      blockIdx.x < nrows ? (nrows - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const long long G = nmine * pp.c;  // stages this CTA consumes
+
+  if (w == TC / 32) {  // producer warp, one lane
+    if (lane != 0) return;
+    long long g = 0;
+    for (; g < G; ++g) {
+      const int slot = (int)(g % S);
+      const long long k = g / S;
+      if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), kPoll)) {
+        atomicOr(err, 1);
+        break;
+      }
+      const long long rr = g / pp.c, row = blockIdx.x + rr * gridDim.x;
+      const int j = (int)(g % pp.c);
+      mbar_expect_tx(&full[slot], kStageBytes);
+      bulk_g2s(stage + slot * NX, M + (size_t)j * N + (size_t)row * NX, kStageBytes, &full[slot]);
+    }
+    // nothing may be in flight when the block exits
+    for (long long d = g - 1; d >= 0 && d >= g - S; --d)
+      mbar_wait_bounded(&full[d % S], (unsigned)((d / S) & 1), kPoll);
+    return;
+  }
+
+  bool failed = false;
+  for (long long rr = 0; rr < nmine; ++rr) {
+    const long long row = blockIdx.x + rr * gridDim.x;
+    PolAcc<float> acc[SL];
+#pragma unroll
+    for (int sl = 0; sl < SL; ++sl) pol_zero(acc[sl]);
+    for (int j = 0; j < pp.c && !failed; ++j) {
+      const long long g = rr * pp.c + j;
+      const int slot = (int)(g % S);
+      // warp-uniform: a lane that gave up makes its whole warp give up
+      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (unsigned)((g / S) & 1), kPoll))) {
+        failed = true;
+        atomicOr(err, 1);
+        break;
+      }
+      const float4* st = stage + slot * NX;
+      float4 cur[SL];
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TC];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[slot]);
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) pol_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
+    }
+    if (named_bar_or(1, TC, failed)) return;  // P of the previous row is no longer read
+#pragma unroll
+    for (int sl = 0; sl < SL; ++sl) {
+      const int e = t + sl * TC;
+      C out[3];
+      pol_final(acc[sl], pp, out);
+      P[e] = out[0];
+      P[FS + e] = out[1];
+      P[2 * FS + e] = out[2];
+    }
+    named_bar_sync(1, TC);
+    if (w < 3) {
+      C* F = P + w * FS;
+      C v[32];
+#pragma unroll
+      for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
+      dft32(v);
+#pragma unroll
+      for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+      __syncwarp();
+#pragma unroll
+      for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
+      __syncwarp();
+#pragma unroll
+      for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+      dft32(v);
+      C* out = p + (size_t)w * N + (size_t)row * NX + lane;
+#pragma unroll
+      for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+    }
+  }
+}
+
 // y pass: a tile of TX adjacent columns of one batch.  Thread (n1, col)
 // loads rows n1 + 32 n2 straight from global memory (32 independent loads),
 // transforms over n2 in registers, applies the twiddles and writes row k2 of
@@ -407,8 +524,8 @@ __global__ void __launch_bounds__(256, 1) k_col_fft4s_tma(const __grid_constant_
   using C = typename RT<R>::C;
   constexpr int TX = 8, T = 256, STR = 33 * TX, TILE = 1024 * TX;
   constexpr unsigned kPoll = 1u << 22;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* in = reinterpret_cast<C*>(smem_raw);  // [2][1024][TX], dense (TMA boxes)
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  C* in = reinterpret_cast<C*>(smem_a128);  // [2][1024][TX], dense (TMA boxes)
   C* tr = in + 2 * TILE;                    // [32][STR]
   C* tw4 = tr + 32 * STR;                   // [32][32]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(tw4 + 1024);
@@ -786,8 +903,8 @@ __global__ void __launch_bounds__(PX / 2) k_ewald_tma(const typename RT<R>::C* _
   using C = typename RT<R>::C;
   constexpr unsigned kPoll = 1u << 22;
   constexpr unsigned kBytes = PX * sizeof(C);
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  C* stage = reinterpret_cast<C*>(smem_raw);                       // [S][3][PX]
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  C* stage = reinterpret_cast<C*>(smem_a128);                       // [S][3][PX]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(stage + S * 3 * PX);
   C* twz = reinterpret_cast<C*>(bar + S);                           // [nz]
   const long long npix = (long long)nx * ny;
@@ -1283,6 +1400,26 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
     kern<<<(unsigned)nrows, 128, smem, s>>>((const typename RT<R>::V4*)M, N, nrows, pp, (C*)p,
                                             (const C*)tw4, nullptr);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
+                                 void* p, const void* tw4, int* err, int n_sm, cudaStream_t s) {
+  constexpr int S = 4;
+  if (nx != 1024 || n_sm <= 0 || ((uintptr_t)M & 15)) return cudaErrorInvalidValue;
+  const long long N = (long long)nx * ny * nz, nrows = (long long)ny * nz;
+  if (nrows <= 0) return cudaSuccess;
+  const size_t smem =
+      (size_t)S * 1024 * sizeof(float4) + (3 * 32 * 33 + 1024) * sizeof(float2) + 2 * S * 8;
+  auto kern = k_pol_fft4s_tma<S>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)  // two blocks of ~97 KB per SM
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  const long long grid = nrows < 2LL * n_sm ? nrows : 2LL * n_sm;
+  kern<<<(unsigned)grid, 288, smem, s>>>((const float4*)M, N, nrows, pp, (float2*)p,
+                                         (const float2*)tw4, err);
   return cudaGetLastError();
 }
 

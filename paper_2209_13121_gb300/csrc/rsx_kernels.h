@@ -80,6 +80,11 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
 template <typename R>
 cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
                              const void* tw4, cudaStream_t s);
+// The Algorithm-1 x pass (FP32, nx = 1024) streaming the morphology
+// through a ring of bulk-copy stages; M must be 16-byte aligned; two
+// persistent CTAs per SM (n_sm).
+cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
+                                 void* p, const void* tw4, int* err, int n_sm, cudaStream_t s);
 // The y pass with 2-D tensor (TMA) loads, FP32, ny = 1024, whole-volume
 // batches (bt.base = 0): tmap is a CUtensorMap over the data viewed as
 // [nbatch][ny][2 nx] floats with 16 x 256 x 1 boxes; one persistent CTA per
