@@ -295,12 +295,7 @@ PolParams<R> make_params(const rsx_context* c, int ie, double alpha, int add_ref
     const double epr = -k[4 * j], epi = k[4 * j + 1];
     const double eqr = -k[4 * j + 2], eqi = k[4 * j + 3];
     const double tr = (epr + 2.0 * eqr) / 3.0, ti = (epi + 2.0 * eqi) / 3.0;
-    pp.tau[j][0] = (R)tr;
-    pp.tau[j][1] = (R)ti;
-    pp.dperp[j][0] = (R)(eqr - tr);
-    pp.dperp[j][1] = (R)(eqi - ti);
-    pp.dpar[j][0] = (R)(epr - eqr);
-    pp.dpar[j][1] = (R)(epi - eqi);
+    rsx::set_component(pp, j, tr, ti, eqr - tr, eqi - ti, epr - eqr, epi - eqi);
   }
   pp.ce = (R)cos(alpha);
   pp.se = (R)sin(alpha);

@@ -56,20 +56,14 @@ __device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sinco
 template <typename R>
 __device__ __forceinline__ void pol_add(PolAcc<R>& acc, R v, R s, R phi, R theta,
                                         const PolParams<R>& pp, int j) {
-  const R tpr = pp.tau[j][0] + s * pp.dperp[j][0];
-  const R tpi = pp.tau[j][1] + s * pp.dperp[j][1];
-  const R v2 = v * v;
+  const R v2 = v * v, v2s = v2 * s, v2s2 = v2s * s;
   acc.aw += v2;
-  // tau' (2 + tau')
-  const R ur = tpr * (R(2) + tpr) - tpi * tpi;
-  const R ui = tpi * (R(2) + tpr) + tpr * tpi;
-  acc.as[0] += v2 * ur;
-  acc.as[1] += v2 * ui;
-  // b = v s dpar ; g = b (2 v (1 + tau') + b)
-  const R vs = v * s;
-  const R br = vs * pp.dpar[j][0], bi = vs * pp.dpar[j][1];
-  const R qr = R(2) * v * (R(1) + tpr) + br, qi = R(2) * v * tpi + bi;
-  const R gr = br * qr - bi * qi, gi = br * qi + bi * qr;
+  // v^2 tau' (2 + tau')
+  acc.as[0] += v2 * pp.q[j][0][0] + v2s * pp.q[j][1][0] + v2s2 * pp.q[j][2][0];
+  acc.as[1] += v2 * pp.q[j][0][1] + v2s * pp.q[j][1][1] + v2s2 * pp.q[j][2][1];
+  // g = b (2 a + b) with a = v (1 + tau'), b = v s dpar
+  const R gr = v2s * pp.q[j][3][0] + v2s2 * pp.q[j][4][0];
+  const R gi = v2s * pp.q[j][3][1] + v2s2 * pp.q[j][4][1];
   R sp, cp, st, ct;
   sincos_r(phi, &sp, &cp);
   sincos_r(theta, &st, &ct);
@@ -348,53 +342,63 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
   for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
 }
 
-// x pass of Algorithm 1 (FP32, nx = 1024) as a bulk-copy pipeline: a
-// producer warp streams (row, component) slices of the morphology, 16 KB
-// each, into a ring of S shared-memory stages (full/empty mbarrier pairs),
-// running up to S slices ahead of the 256 consumer threads.  Consumers
-// accumulate four voxels each, release the stage per warp, write the row's
-// three fields to shared memory, and warps 0..2 transform them as in
-// k_pol_fft4s while the producer already fills the next row's stages.  CTAs
-// are persistent (two per SM) and walk rows with a grid stride.  Every wait
-// is bounded: a timeout sets *err, the producer waits (bounded) for its
-// copies in flight, and all threads return.
-template <int S>
-__global__ void __launch_bounds__(288, 2) k_pol_fft4s_tma(const float4* __restrict__ M, long long N,
-                                                         long long nrows, PolParams<float> pp,
-                                                         float2* __restrict__ p,
-                                                         const float2* __restrict__ tw4_g,
-                                                         int* __restrict__ err) {
+// x pass of Algorithm 1 (FP32, nx = 1024) as a warp-specialised bulk-copy
+// pipeline.  Three roles per block:
+//  * a producer lane streams (row, component) slices of the morphology,
+//    16 KB each, into a ring of S shared-memory stages (full/empty
+//    mbarrier pairs), up to S slices ahead;
+//  * PW polarisation warps accumulate 1024 / (32 PW) voxels per thread from
+//    each stage, release it per warp, and write the row's three fields into
+//    one of NP row buffers;
+//  * FG groups of three transform warps (group g takes the rows r with
+//    r mod FG = g) run the four-step FFT of k_pol_fft4s on a filled buffer
+//    and store the spectrum.
+// Row buffers pass between the roles on named barriers (full: 1 + i, empty:
+// 1 + NP + i), so polarisation of the next rows overlaps the transforms.
+// CTAs are persistent and walk rows with a grid stride.  Every mbarrier wait
+// is bounded; a timeout sets *err and the block's abort flag, after which the
+// roles skip their work but still complete the barrier protocol (which has
+// no unbounded wait left), the producer waits (bounded) for its copies in
+// flight, and the block exits.
+template <int S, int NP, int PW, int FG>
+__global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
+    const float4* __restrict__ M, long long N, long long nrows, PolParams<float> pp,
+    float2* __restrict__ p, const float2* __restrict__ tw4_g, int* __restrict__ err) {
   using C = float2;
-  constexpr int NX = 1024, TC = 256, SL = NX / TC, FS = 32 * 33;
+  constexpr int NX = 1024, TP = 32 * PW, SL = NX / TP, FS = 32 * 33, NB = TP + 96;
+  static_assert(NX % TP == 0 && 1 + 2 * NP <= 15, "layout");
   constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(float4);
   extern __shared__ __align__(128) unsigned char smem_a128[];
-  float4* stage = reinterpret_cast<float4*>(smem_a128);     // [S][NX]
-  C* P = reinterpret_cast<C*>(stage + S * NX);             // [3][FS]
-  C* tw4 = P + 3 * FS;                                      // [32][32]
+  float4* stage = reinterpret_cast<float4*>(smem_a128);    // [S][NX]
+  C* P = reinterpret_cast<C*>(stage + S * NX);             // [NP][3][FS]
+  C* tw4 = P + NP * 3 * FS;                                 // [32][32]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(tw4 + 1024);
   unsigned long long* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   if (t == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&empty[i], TC / 32);
+      mbar_init(&empty[i], PW);
     }
+    *abort_flag = 0;
     fence_proxy_async();
   }
   for (int i = t; i < 1024; i += blockDim.x) tw4[i] = tw4_g[i];
   __syncthreads();
   const long long nmine =
       blockIdx.x < nrows ? (nrows - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const long long G = nmine * pp.c;  // stages this CTA consumes
 
-  if (w == TC / 32) {  // producer warp, one lane
+  if (w == PW + 3 * FG) {  // producer warp, one lane
     if (lane != 0) return;
+    const long long G = nmine * pp.c;
     long long g = 0;
     for (; g < G; ++g) {
       const int slot = (int)(g % S);
       const long long k = g / S;
       if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), kPoll)) {
         atomicOr(err, 1);
+        *abort_flag = 1;
         break;
       }
       const long long rr = g / pp.c, row = blockIdx.x + rr * gridDim.x;
@@ -408,43 +412,61 @@ __global__ void __launch_bounds__(288, 2) k_pol_fft4s_tma(const float4* __restri
     return;
   }
 
-  bool failed = false;
-  for (long long rr = 0; rr < nmine; ++rr) {
-    const long long row = blockIdx.x + rr * gridDim.x;
-    PolAcc<float> acc[SL];
+  if (w < PW) {  // polarisation warps
+    bool failed = false;
+    for (long long rr = 0; rr < nmine; ++rr) {
+      PolAcc<float> acc[SL];
 #pragma unroll
-    for (int sl = 0; sl < SL; ++sl) pol_zero(acc[sl]);
-    for (int j = 0; j < pp.c && !failed; ++j) {
-      const long long g = rr * pp.c + j;
-      const int slot = (int)(g % S);
-      // warp-uniform: a lane that gave up makes its whole warp give up
-      if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (unsigned)((g / S) & 1), kPoll))) {
-        failed = true;
-        atomicOr(err, 1);
-        break;
+      for (int sl = 0; sl < SL; ++sl) pol_zero(acc[sl]);
+      for (int j = 0; j < pp.c; ++j) {
+        failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
+        if (failed) break;
+        const long long g = rr * pp.c + j;
+        const int slot = (int)(g % S);
+        // warp-uniform: a lane that gave up makes its whole warp give up
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (unsigned)((g / S) & 1), kPoll))) {
+          failed = true;
+          atomicOr(err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        const float4* st = stage + slot * NX;
+        float4 cur[SL];
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl)
+          pol_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
       }
-      const float4* st = stage + slot * NX;
-      float4 cur[SL];
+      const int i = (int)(rr % NP);
+      if (rr >= NP) named_bar_sync(1 + NP + i, NB);  // transforms of row rr - NP done
+      if (!failed) {
+        C* Pi = P + i * 3 * FS;
 #pragma unroll
-      for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TC];
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[slot]);
-#pragma unroll
-      for (int sl = 0; sl < SL; ++sl) pol_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
+        for (int sl = 0; sl < SL; ++sl) {
+          const int e = t + sl * TP;
+          C out[3];
+          pol_final(acc[sl], pp, out);
+          Pi[e] = out[0];
+          Pi[FS + e] = out[1];
+          Pi[2 * FS + e] = out[2];
+        }
+      }
+      named_bar_arrive(1 + i, NB);
     }
-    if (named_bar_or(1, TC, failed)) return;  // P of the previous row is no longer read
-#pragma unroll
-    for (int sl = 0; sl < SL; ++sl) {
-      const int e = t + sl * TC;
-      C out[3];
-      pol_final(acc[sl], pp, out);
-      P[e] = out[0];
-      P[FS + e] = out[1];
-      P[2 * FS + e] = out[2];
-    }
-    named_bar_sync(1, TC);
-    if (w < 3) {
-      C* F = P + w * FS;
+    return;
+  }
+
+  // transform warps: group fg, field f
+  const int fg = (w - PW) / 3, f = (w - PW) % 3;
+  for (long long rr = fg; rr < nmine; rr += FG) {
+    const int i = (int)(rr % NP);
+    named_bar_sync(1 + i, NB);
+    if (*abort_flag == 0) {
+      const long long row = blockIdx.x + rr * gridDim.x;
+      C* F = P + i * 3 * FS + f * FS;
       C v[32];
 #pragma unroll
       for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
@@ -457,10 +479,14 @@ __global__ void __launch_bounds__(288, 2) k_pol_fft4s_tma(const float4* __restri
       __syncwarp();
 #pragma unroll
       for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+      __syncwarp();
+      if (rr + NP < nmine) named_bar_arrive(1 + NP + i, NB);
       dft32(v);
-      C* out = p + (size_t)w * N + (size_t)row * NX + lane;
+      C* out = p + (size_t)f * N + (size_t)row * NX + lane;
 #pragma unroll
       for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+    } else if (rr + NP < nmine) {
+      named_bar_arrive(1 + NP + i, NB);
     }
   }
 }
@@ -1405,21 +1431,23 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
 
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, cudaStream_t s) {
-  constexpr int S = 4;
+  // 3 stages, 2 row buffers, 4 polarisation warps, one transform group:
+  // ~106 KB of shared memory and 256 threads, two blocks per SM
+  constexpr int S = 3, NP = 2, PW = 4, FG = 1, CPS = 2;
   if (nx != 1024 || n_sm <= 0 || ((uintptr_t)M & 15)) return cudaErrorInvalidValue;
   const long long N = (long long)nx * ny * nz, nrows = (long long)ny * nz;
   if (nrows <= 0) return cudaSuccess;
-  const size_t smem =
-      (size_t)S * 1024 * sizeof(float4) + (3 * 32 * 33 + 1024) * sizeof(float2) + 2 * S * 8;
-  auto kern = k_pol_fft4s_tma<S>;
+  const size_t smem = (size_t)S * 1024 * sizeof(float4) +
+                      (NP * 3 * 32 * 33 + 1024) * sizeof(float2) + 2 * S * 8 + 16;
+  auto kern = k_pol_fft4s_tma<S, NP, PW, FG>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess)  // two blocks of ~97 KB per SM
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
-  const long long grid = nrows < 2LL * n_sm ? nrows : 2LL * n_sm;
-  kern<<<(unsigned)grid, 288, smem, s>>>((const float4*)M, N, nrows, pp, (float2*)p,
-                                         (const float2*)tw4, err);
+  const long long grid = nrows < (long long)CPS * n_sm ? nrows : (long long)CPS * n_sm;
+  kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>((const float4*)M, N, nrows, pp,
+                                                            (float2*)p, (const float2*)tw4, err);
   return cudaGetLastError();
 }
 

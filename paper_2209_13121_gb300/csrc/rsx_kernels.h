@@ -18,11 +18,39 @@ template <typename R> struct PolParams {
   R tau[RSX_MAX_COMPONENTS][2];
   R dperp[RSX_MAX_COMPONENTS][2];
   R dpar[RSX_MAX_COMPONENTS][2];
+  // Per component, complex, from the three above: tau (2 + tau),
+  // 2 dperp (1 + tau), dperp^2, 2 dpar (1 + tau), dpar (2 dperp + dpar).
+  // With tau' = tau + s dperp: tau' (2 + tau') = q0 + s q1 + s^2 q2 and
+  // (v s dpar) (2 v (1 + tau') + v s dpar) = v^2 (s q3 + s^2 q4).
+  R q[RSX_MAX_COMPONENTS][5][2];
   R ce, se;     // cos(alpha), sin(alpha): e = U(alpha) (1, 0, 0)
   int c;        // number of components
   int literal;  // 1: p <- U^T p (RSX_FRAME_LITERAL), 0: lab frame
   int add_ref;  // 1: output full p; 0: p minus the constant -(c-1) e'/(4 pi)
 };
+
+// Component j of pp from tau = (eps_par + 2 eps_perp)/3, dperp = eps_perp -
+// tau and dpar = eps_par - eps_perp (complex, eps = n - 1), in FP64.
+template <typename R>
+inline void set_component(PolParams<R>& pp, int j, double tr, double ti, double pr, double pi,
+                          double ar, double ai) {
+  pp.tau[j][0] = (R)tr;
+  pp.tau[j][1] = (R)ti;
+  pp.dperp[j][0] = (R)pr;
+  pp.dperp[j][1] = (R)pi;
+  pp.dpar[j][0] = (R)ar;
+  pp.dpar[j][1] = (R)ai;
+  const double q[5][2] = {
+      {tr * (2.0 + tr) - ti * ti, ti * (2.0 + tr) + tr * ti},
+      {2.0 * (pr * (1.0 + tr) - pi * ti), 2.0 * (pi * (1.0 + tr) + pr * ti)},
+      {pr * pr - pi * pi, 2.0 * pr * pi},
+      {2.0 * (ar * (1.0 + tr) - ai * ti), 2.0 * (ai * (1.0 + tr) + ar * ti)},
+      {ar * (2.0 * pr + ar) - ai * (2.0 * pi + ai), ai * (2.0 * pr + ar) + ar * (2.0 * pi + ai)}};
+  for (int k = 0; k < 5; ++k) {
+    pp.q[j][k][0] = (R)q[k][0];
+    pp.q[j][k][1] = (R)q[k][1];
+  }
+}
 
 // Per-pixel Ewald geometry for one energy (Eq. Ewald): the two bracketing
 // q_z bins (b0 < 0 marks a pixel with no real q_z), the interpolation
@@ -81,7 +109,8 @@ template <typename R>
 cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
                              const void* tw4, cudaStream_t s);
 // The Algorithm-1 x pass (FP32, nx = 1024) streaming the morphology
-// through a ring of bulk-copy stages; M must be 16-byte aligned; two
+// through a ring of bulk-copy stages into warp-specialised blocks
+// (polarisation, transform, producer); M must be 16-byte aligned; two
 // persistent CTAs per SM (n_sm).
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, cudaStream_t s);

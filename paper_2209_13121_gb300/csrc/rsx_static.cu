@@ -123,12 +123,7 @@ int rsx_scatter_angle_noalloc(const void* M, int nx, int ny, int nz, int n_compo
     const double* k = constants + 4 * j;
     const double epr = -k[0], epi = k[1], eqr = -k[2], eqi = k[3];
     const double tr = (epr + 2.0 * eqr) / 3.0, ti = (epi + 2.0 * eqi) / 3.0;
-    pp.tau[j][0] = (float)tr;
-    pp.tau[j][1] = (float)ti;
-    pp.dperp[j][0] = (float)(eqr - tr);
-    pp.dperp[j][1] = (float)(eqi - ti);
-    pp.dpar[j][0] = (float)(epr - eqr);
-    pp.dpar[j][1] = (float)(epi - eqi);
+    rsx::set_component(pp, j, tr, ti, eqr - tr, eqi - ti, epr - eqr, epi - eqi);
   }
   pp.ce = (float)cos(alpha_rad);
   pp.se = (float)sin(alpha_rad);

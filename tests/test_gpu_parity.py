@@ -232,6 +232,25 @@ def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
                                        rtol=1e-10 if prec == 64 else 1e-5)
 
 
+# Sizes at which the persistent FP32 passes give each block several work
+# items: x rows (nx = 1024: groups of two rows and an odd tail) and y tiles
+# (ny = 1024: both input buffers refilled more than once).
+MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2)]
+
+
+@pytest.mark.parametrize("shape,c", MULTI, ids=["x".join(map(str, s)) for s, _ in MULTI])
+def test_scatter_angle_persistent_passes(rsx, shape, c):
+    M, K = _inputs(shape, c, 32, seed=16)
+    with _ctx(rsx, shape, c, 32) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        img = torch.empty(shape[1:], dtype=torch.float32, device="cuda")
+        for ie, alpha in ((0, 0.3), (2, 2.0)):
+            ctx.scatter_angle(ie, alpha, img)
+            ref = O.scatter_one_angle(M, K[ie], ENERGIES[ie], VOXEL, alpha)
+            assert_image_close(img.cpu().numpy(), ref, 32)
+
+
 # ------------------------------------------------------- Algorithm 1 (a7)
 @pytest.mark.parametrize("prec", [32, 64])
 @pytest.mark.parametrize("shape,c", CASES[:5], ids=IDS[:5])
