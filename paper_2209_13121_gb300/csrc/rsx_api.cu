@@ -133,6 +133,9 @@ struct rsx_context {
   alignas(64) CUtensorMap tmap_p;
   alignas(64) CUtensorMap tmap_ft;
   bool has_tmap_p = false, has_tmap_ft = false;
+  // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
+  // [2 slots][3][ny][nx] float4
+  void* part = nullptr;
   int n_sm = 0;
   int* flag = nullptr;
   int* err = nullptr;  // set by a kernel whose bounded wait timed out
@@ -149,8 +152,8 @@ struct rsx_context {
 namespace {
 
 void free_all(rsx_context* c) {
-  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,
-                  c->twx,     c->twy, c->twz, c->tw4, c->flag, c->err};
+  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,  c->twx,
+                  c->twy,     c->twz, c->tw4, c->flag, c->err, c->part};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -426,10 +429,6 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
              "polarisation + x-FFT kernel");
     }
   }
-  if (g.ny > 1) {
-    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-    RSX_CK(launch_y_fft<R>(c, c->p, 3, s), "y-FFT kernel");
-  }
   // The constant -(c-1) e' / (4 pi) left out of p before the FFT returns at
   // q = 0 as N times itself (e' = x-hat in the literal frame, e otherwise).
   const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
@@ -438,6 +437,26 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     dc[0] = (R)ref; dc[1] = (R)0; dc[2] = (R)0;
   } else {
     dc[0] = (R)(ref * cos(alpha)); dc[1] = (R)(ref * sin(alpha)); dc[2] = (R)0;
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (c->part && c->has_tmap_p) {  // y-FFT and the pruned z transform in one pass
+      long long L = 0;
+      {
+        PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+        RSX_CK(rsx::launch_yz_tma(&c->tmap_p, g.nx, g.ny, g.nz, (const Geo<float>*)c->geo,
+                                  c->twz, c->tw4, c->part, c->err, c->n_sm, &L, s),
+               "y-FFT + z-bins kernel");
+      }
+      PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+      RSX_CK(rsx::launch_ewald_bins(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
+                                    dc[0], dc[1], dc[2], (float*)img, s),
+             "Ewald kernel");
+      return RSX_OK;
+    }
+  }
+  if (g.ny > 1) {
+    PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+    RSX_CK(launch_y_fft<R>(c, c->p, 3, s), "y-FFT kernel");
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
   RSX_CK(rsx::launch_ewald<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, true, dc, img,
@@ -482,6 +501,13 @@ bool host_morphology_ok(const void* M, int prec, long long n) {
 
 const char* rsx_last_error(void) { return g_err.c_str(); }
 
+// The fused y-FFT + pruned z pass serves FP32 Algorithms 1 and 2 on
+// qualifying shapes; its bins take 2 x 3 x 16 bytes per pixel.
+static bool uses_yz(const rsx_config* cfg) {
+  return cfg->precision == 32 && cfg->algorithm <= 2 && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
+}
+static size_t part_bytes(const rsx_config* cfg) { return 6 * (size_t)cfg->nx * cfg->ny * 16; }
+
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
   if (check_config(cfg) != RSX_OK) return 0;
   const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
@@ -496,6 +522,7 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
   b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
   b += (size_t)npix * geo_size(cfg->precision);
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
+  if (uses_yz(cfg)) b += part_bytes(cfg);  // bins of the fused y + z pass
   return b;
 }
 
@@ -579,6 +606,12 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
   if (cfg->precision == 32 && cfg->ny == 1024 && cfg->nx % 8 == 0 && c->n_sm > 0) {
     c->has_tmap_p = make_tmap(c, c->p, 3, &c->tmap_p);
     if (c->ft) c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft);
+  }
+  if (uses_yz(cfg) && (e = cudaMalloc(&c->part, part_bytes(cfg))) != cudaSuccess) {
+    rc = cuda_fail(e, "y + z pass bins");
+    free_all(c);
+    delete c;
+    return rc;
   }
   if ((rc = upload_twiddles(c, cfg->nx, &c->twx)) || (rc = upload_twiddles(c, cfg->ny, &c->twy)) ||
       (rc = upload_twiddles(c, cfg->nz, &c->twz))) {

@@ -269,6 +269,33 @@ template <typename C> __host__ __device__ __forceinline__ void dft32(C* v) {
   dft32_combine<0>(v, e, o);
 }
 
+// A 32-point forward DFT split over a lane pair (partner = lane ^ 16): the
+// lane with h = 0 holds the even samples x[2m] in v[m], the lane with h = 1
+// the odd samples x[2m + 1] (m = 0..15).  Each does its 16-point DFT, the
+// lane h = 1 twiddles its outputs by W32^k, and after one exchange the h = 0
+// lane holds X[k] = E[k] + W32^k O[k] and the h = 1 lane X[16 + k] =
+// E[k] - W32^k O[k] in r[k], k = 0..15.  All 32 lanes of the warp take part.
+template <int K, typename C>
+__device__ __forceinline__ void dft32_pair_step(const C* v, C* r, int h) {
+  if constexpr (K < 16) {
+    using R = decltype(v[0].x);
+    const C mine = v[out_pos<16>(K)];
+    const C tw = w32<K>(mine);
+    const C pay = h ? tw : mine;  // E[k] from h = 0, W32^k O[k] from h = 1
+    C other;
+    other.x = __shfl_xor_sync(0xffffffffu, pay.x, 16);
+    other.y = __shfl_xor_sync(0xffffffffu, pay.y, 16);
+    const R sg = h ? R(-1) : R(1);
+    r[K].x = other.x + sg * pay.x;  // h = 0: E + W O ; h = 1: E - W O
+    r[K].y = other.y + sg * pay.y;
+    dft32_pair_step<K + 1>(v, r, h);
+  }
+}
+template <typename C> __device__ __forceinline__ void dft32_pair(C* v, C* r, int h) {
+  dft_reg<16>(v);
+  dft32_pair_step<0>(v, r, h);
+}
+
 // ---------------------------------------------------------------------------
 // Shared-memory Stockham FFT (forward, unnormalised).
 //

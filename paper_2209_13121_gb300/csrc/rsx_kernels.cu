@@ -911,6 +911,178 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
   }
 }
 
+// y-FFT fused with the pruned z transform (FP32, ny = 1024, nz a power of
+// two up to 1024, nx a multiple of 8).  Work items are (field, 8-column tile); each has nz
+// steps (its z-slices).  The items' steps are laid end to end and cut into
+// one contiguous range of L >= nz steps per persistent CTA, so every CTA
+// does the same number of steps and an item is split between at most two
+// CTAs: the part that starts at z = 0 goes to slot 0 of `part`, the other
+// to slot 1, and k_ewald_bins adds them.  Per step, the slice's 8 x 1024
+// tile arrives by 2-D tensor TMA (two buffers, the next-but-one step in
+// flight); 512 threads transform it with the four-step 32 x 32 scheme, each
+// 32-point DFT split over a lane pair (dft32_pair), and every thread then
+// owns 16 pixels (row k2 + 32 k1, k1 = 16 h .. 16 h + 15) for which it
+// accumulates, across the item's z-slices, the two q_z bins b0 and b0 + 1
+// of Eq. (Ewald):
+//   A0 += Y(z) W^(b0 z),  A1 += Y(z) W^(b0 z) W^z,  W = exp(-2 pi i / nz),
+// with b0 per pixel from the energy's geometry (0 for pixels off the
+// sphere, which k_ewald_bins zeroes).  The y-transformed slices are never
+// written.  Waits are bounded as in k_col_fft4s_tma.
+__global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUtensorMap tmap, int nx,
+                                                   int nz, long long ntiles, long long L, long long T,
+                                                   const Geo<float>* __restrict__ geo,
+                                                   const float2* __restrict__ twz_g,
+                                                   const float2* __restrict__ tw4_g,
+                                                   float4* __restrict__ part, int* __restrict__ err) {
+  using C = float2;
+  constexpr int TX = 8, TILE = 1024 * TX, STR = 33 * TX;
+  constexpr unsigned kPoll = 1u << 22;
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  C* in = reinterpret_cast<C*>(smem_a128);  // [2][1024][TX], dense (TMA boxes)
+  C* tr = in + 2 * TILE;                     // [32][STR]
+  C* tw4 = tr + 32 * STR;                    // [32][32]
+  C* twz = tw4 + 1024;                       // [nz]
+  unsigned short* btab = reinterpret_cast<unsigned short*>(twz + nz);  // [1024][TX]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(btab + TILE);
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int col = lane & 7, sub = (lane >> 3) & 1, h = lane >> 4;
+  const long long s0 = (long long)blockIdx.x * L;
+  const long long s1 = s0 + L < T ? s0 + L : T;
+  if (s0 >= s1) return;
+  const long long npix = 1024LL * nx;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  for (int i = t; i < 1024; i += 512) tw4[i] = tw4_g[i];
+  for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
+  __syncthreads();
+  auto issue = [&](long long st, int b) {
+    const long long item = st / nz;
+    const int z = (int)(st % nz), f = (int)(item / ntiles), ti = (int)(item % ntiles);
+    mbar_expect_tx(&bar[b], TILE * sizeof(C));
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      tma_load_3d(in + b * TILE + q * 256 * TX, &tmap, ti * 2 * TX, q * 256, f * nz + z, &bar[b]);
+  };
+  if (t == 0) {
+    issue(s0, 0);
+    if (s0 + 1 < s1) issue(s0 + 1, 1);
+  }
+  C acc0[16], acc1[16];
+  int i = 0;
+  for (long long st = s0; st < s1; ++st, ++i) {
+    const int b = i & 1;
+    const long long item = st / nz;
+    const int z = (int)(st % nz);
+    const int ti = (int)(item % ntiles);
+    if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
+      for (int e = t; e < TILE; e += 512) {
+        const int b0 = geo[(size_t)(e >> 3) * nx + ti * TX + (e & 7)].b0;
+        btab[e] = (unsigned short)(b0 < 0 ? 0 : b0);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
+    }
+    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kPoll);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicOr(err, 1);
+        for (int d = 0; d < 2; ++d)
+          if (st + d < s1) mbar_wait_bounded(&bar[(i + d) & 1], ((i + d) >> 1) & 1, kPoll);
+      }
+      return;
+    }
+    // stage 1: 32-point DFTs over n2 (rows n1 + 32 n2), twiddle, transpose
+    {
+      const int n1 = 2 * w + sub;
+      const C* src = in + b * TILE;
+      C v[16], r[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = src[(n1 + 32 * h + 64 * m) * TX + col];
+      dft32_pair(v, r, h);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int k2 = 16 * h + k;
+        tr[k2 * STR + n1 * TX + col] = cmul(r[k], tw4[k2 * 32 + n1]);
+      }
+    }
+    __syncthreads();  // input buffer b consumed, transpose complete, bins in place
+    if (t == 0 && st + 2 < s1) {
+      fence_proxy_async();
+      issue(st + 2, b);
+    }
+    // stage 2: 32-point DFTs over n1, then the two q_z bins of 16 pixels
+    {
+      const int k2 = 2 * w + sub;
+      C v[16], r[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = tr[k2 * STR + (2 * m + h) * TX + col];
+      dft32_pair(v, r, h);
+      const C wz = twz[z];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const int row = k2 + 512 * h + 32 * k;
+        const int b0 = btab[row * TX + col];
+        const C q = cmul(r[k], twz[(b0 * z) & (nz - 1)]);
+        acc0[k] = cadd(acc0[k], q);
+        acc1[k] = cadd(acc1[k], cmul(q, wz));
+      }
+      if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
+        const int slot = st - z >= s0 ? 0 : 1;
+        const int f = (int)(item / ntiles);
+        float4* dst = part + ((size_t)slot * 3 + f) * npix + (size_t)ti * TX + col;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+          const int row = k2 + 512 * h + 32 * k;
+          dst[(size_t)row * nx] = make_float4(acc0[k].x, acc0[k].y, acc1[k].x, acc1[k].y);
+        }
+      }
+    }
+    __syncthreads();  // the transpose buffer and the bins are rewritten next step
+  }
+}
+
+// Eqs. (3Dscatter)/(Ewald) from the bins of k_yz_tma: per pixel, the two
+// q_z bins of the three fields (slot 1 added where the item was split), the
+// constant part returned at q = 0, the projection and the interpolation;
+// written in fftshift order.
+__global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, int nz,
+                             long long ntiles, long long L, const Geo<float>* __restrict__ geo,
+                             float dc0, float dc1, float dc2, float* __restrict__ img) {
+  using C = float2;
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const Geo<float> g = geo[pix];
+  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);
+  float* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
+  if (g.b0 < 0) {
+    *dst = 0.f;
+    return;
+  }
+  const long long ti = mx / 8;
+  C a0[3], a1[3];
+  const float dcs[3] = {dc0, dc1, dc2};
+#pragma unroll
+  for (int f = 0; f < 3; ++f) {
+    float4 v = part[(size_t)f * npix + pix];
+    const long long item = f * ntiles + ti;
+    if ((item * nz) / L != ((item + 1) * nz - 1) / L) {
+      const float4 u = part[(size_t)(3 + f) * npix + pix];
+      v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+    }
+    a0[f] = make_float2(v.x, v.y);
+    a1[f] = make_float2(v.z, v.w);
+    if (pix == 0) {
+      if (g.b0 == 0) a0[f].x += dcs[f];
+      if (g.b1 == 0) a1[f].x += dcs[f];
+    }
+  }
+  *dst = ewald_value<float>(g, a0, a1);
+}
+
 // Hot path, pipelined: a CTA owns PX consecutive pixels and streams their
 // x/y-transformed slices P(z) through an S-stage ring in shared memory.  For
 // each slice, thread 0 posts the byte count on the stage's mbarrier and
@@ -1448,6 +1620,37 @@ cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const Po
   const long long grid = nrows < (long long)CPS * n_sm ? nrows : (long long)CPS * n_sm;
   kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>((const float4*)M, N, nrows, pp,
                                                             (float2*)p, (const float2*)tw4, err);
+  return cudaGetLastError();
+}
+
+bool yz_fusable(int nx, int ny, int nz) {
+  return ny == 1024 && nx % 8 == 0 && nx >= 8 && nz >= 1 && nz <= 1024 && (nz & (nz - 1)) == 0;
+}
+
+cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<float>* geo,
+                          const void* twz, const void* tw4, void* part, int* err, int n_sm,
+                          long long* L_out, cudaStream_t s) {
+  if (!yz_fusable(nx, ny, nz) || n_sm <= 0) return cudaErrorInvalidValue;
+  const long long ntiles = nx / 8, items = 3 * ntiles, T = items * nz;
+  const long long grid = items < n_sm ? items : n_sm;
+  const long long L = (T + grid - 1) / grid;  // >= nz: an item meets at most two blocks
+  *L_out = L;
+  const size_t smem = (2 * 8192 + 32 * 33 * 8 + 1024 + (size_t)nz) * sizeof(float2) +
+                      8192 * sizeof(unsigned short) + 2 * 8;
+  cudaError_t e = cudaFuncSetAttribute(k_yz_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_yz_tma<<<(unsigned)grid, 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, ntiles, L, T, geo,
+                                             (const float2*)twz, (const float2*)tw4, (float4*)part,
+                                             err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ewald_bins(const void* part, int nx, int ny, int nz, long long L,
+                              const Geo<float>* geo, float dc0, float dc1, float dc2, float* img,
+                              cudaStream_t s) {
+  const long long npix = (long long)nx * ny;
+  k_ewald_bins<<<grid1(npix, 256), 256, 0, s>>>((const float4*)part, nx, ny, nz, nx / 8, L, geo,
+                                                dc0, dc1, dc2, img);
   return cudaGetLastError();
 }
 

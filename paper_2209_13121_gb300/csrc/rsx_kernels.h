@@ -114,6 +114,19 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 // persistent CTAs per SM (n_sm).
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, cudaStream_t s);
+// The y-FFT fused with the pruned z transform (FP32): yz_fusable says
+// whether the shape qualifies (ny = 1024, nx a multiple of 8, nz a power of
+// two up to 1024).
+// launch_yz_tma writes the two q_z bins of every pixel and field into part
+// ([2 slots][3][ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
+// the step count per block that launch_ewald_bins needs to add the slots.
+bool yz_fusable(int nx, int ny, int nz);
+cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<float>* geo,
+                          const void* twz, const void* tw4, void* part, int* err, int n_sm,
+                          long long* L_out, cudaStream_t s);
+cudaError_t launch_ewald_bins(const void* part, int nx, int ny, int nz, long long L,
+                              const Geo<float>* geo, float dc0, float dc1, float dc2, float* img,
+                              cudaStream_t s);
 // The y pass with 2-D tensor (TMA) loads, FP32, ny = 1024, whole-volume
 // batches (bt.base = 0): tmap is a CUtensorMap over the data viewed as
 // [nbatch][ny][2 nx] floats with 16 x 256 x 1 boxes; one persistent CTA per
