@@ -47,6 +47,7 @@ extern "C" {
 
 #define RSX_HOST 0
 #define RSX_DEVICE 1
+#define RSX_HOST_ASYNC 2 /* rsx_set_morphology only: page-locked host memory */
 
 #define RSX_MAX_COMPONENTS 32
 
@@ -109,6 +110,14 @@ int rsx_angle_count(double start_deg, double increment_deg, double end_deg, int 
  * where = RSX_DEVICE: borrowed, not copied; the pointer must stay valid and
  *   unchanged until the last run that uses it has finished, and must be
  *   aligned to 4 * sizeof(Real).
+ * where = RSX_HOST_ASYNC (Algorithm 1): like RSX_HOST, but M must be
+ *   page-locked host memory and the copy is only enqueued on `stream`: the
+ *   call returns before it lands, M must stay valid and unchanged until the
+ *   stream reaches that point, and runs of this context must be ordered after
+ *   it (the same stream, or an event).  With one context per stream a
+ *   caller can upload the next morphology while another context computes.
+ *   Memory that is not page-locked returns RSX_ERR_INVALID.  Algorithms 2
+ *   and 3 treat it as RSX_HOST (borrowed).
  * With validate set, a value outside the ranges of Sec. 3.1 returns
  * RSX_ERR_INVALID and leaves the previous morphology in place. */
 int rsx_set_morphology(rsx_context* ctx, const void* M, int where, void* stream);

@@ -634,15 +634,22 @@ int rsx_destroy(rsx_context* c) {
 int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
   if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
   if (!M) return fail(RSX_ERR_INVALID, "morphology pointer is NULL");
-  if (where != RSX_HOST && where != RSX_DEVICE)
-    return fail(RSX_ERR_INVALID, "where=%d: must be RSX_HOST or RSX_DEVICE", where);
+  if (where != RSX_HOST && where != RSX_DEVICE && where != RSX_HOST_ASYNC)
+    return fail(RSX_ERR_INVALID, "where=%d: must be RSX_HOST, RSX_DEVICE or RSX_HOST_ASYNC", where);
   DeviceGuard dg(c->dev);
   if (!dg.ok) return fail(RSX_ERR_CUDA, "cannot select the context's device");
   cudaStream_t s = (cudaStream_t)stream;
   const int prec = c->cfg.precision;
   const long long n_entries = (long long)c->cfg.n_components * c->N;
   const size_t bytes = (size_t)n_entries * 4 * real_size(prec);
-  if (where == RSX_HOST) {
+  if (where == RSX_HOST_ASYNC && c->cfg.algorithm == 1) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, M) != cudaSuccess || at.type != cudaMemoryTypeHost) {
+      cudaGetLastError();  // clear a sticky "invalid value" from an unknown pointer
+      return fail(RSX_ERR_INVALID, "RSX_HOST_ASYNC needs page-locked host memory");
+    }
+  }
+  if (where == RSX_HOST || where == RSX_HOST_ASYNC) {
     if (c->cfg.validate && !host_morphology_ok(M, prec, n_entries))
       return fail(RSX_ERR_INVALID, "morphology value outside 0<=v<=1, 0<=s<=1 or non-finite angle");
     if (c->cfg.algorithm >= 2) {
@@ -656,7 +663,7 @@ int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
     }
     if (!c->M_owned) RSX_CK(cudaMalloc(&c->M_owned, bytes), "morphology copy");
     RSX_CK(cudaMemcpyAsync(c->M_owned, M, bytes, cudaMemcpyHostToDevice, s), "morphology upload");
-    RSX_CK(cudaStreamSynchronize(s), "morphology upload");
+    if (where == RSX_HOST) RSX_CK(cudaStreamSynchronize(s), "morphology upload");
     c->M = c->M_owned;
     c->nt_energy = -1;
     c->bins_energy = -1;

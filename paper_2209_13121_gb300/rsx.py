@@ -23,6 +23,7 @@ RSX_ERR_UNSUPPORTED = -4
 RSX_ERR_STATE = -5
 RSX_HOST = 0
 RSX_DEVICE = 1
+RSX_HOST_ASYNC = 2
 RSX_FRAME_LITERAL = 0
 RSX_FRAME_LAB = 1
 RSX_MAX_COMPONENTS = 32
@@ -164,14 +165,21 @@ class Context:
         self.close()
 
     # ------------------------------------------------------------ inputs
-    def set_morphology(self, M, stream=None):
+    def set_morphology(self, M, stream=None, async_copy=False):
         """M: [c][nz][ny][nx][4] (v, s, phi, theta).  numpy -> copied from
-        host; torch CUDA tensor -> borrowed (kept alive by this object)."""
+        host; torch CUDA tensor -> borrowed (kept alive by this object).
+        async_copy (numpy in page-locked memory, e.g. a pinned torch
+        tensor's .numpy()): the copy is only enqueued on `stream`; M must
+        stay unchanged until the stream has passed it."""
         if isinstance(M, np.ndarray):
             A = np.ascontiguousarray(M, dtype=self.real)
             self._check_shape(A.shape)
-            _check(lib().rsx_set_morphology(self._h, A.ctypes.data_as(ctypes.c_void_p), RSX_HOST,
+            where = RSX_HOST_ASYNC if async_copy else RSX_HOST
+            _check(lib().rsx_set_morphology(self._h, A.ctypes.data_as(ctypes.c_void_p), where,
                                             _stream_handle(stream) if stream is not None else None))
+            if async_copy:
+                self._keep = A
+                return
             # Algorithm 2 streams from this host array on every energy
             self._keep = A if self.cfg.algorithm >= 2 else None
             return

@@ -313,6 +313,49 @@ def test_device_morphology_is_borrowed(rsx):
         np.testing.assert_array_equal(a.run((0, 60, 120)), b.run((0, 60, 120)))
 
 
+def test_async_upload_pipeline_matches_synchronous_upload(rsx):
+    """Two contexts on two streams, the next morphology uploaded
+    asynchronously from page-locked memory while the other context runs:
+    every energy's image equals the synchronous single-context result."""
+    shape, c = (4, 32, 64), 3
+    Ms = [_inputs(shape, c, 32, seed=40 + i)[0] for i in range(3)]
+    _, K = _inputs(shape, c, 32, seed=40)
+    pinned = []
+    for M in Ms:
+        t = torch.empty(M.shape, dtype=torch.float32, pin_memory=True)
+        t.copy_(torch.from_numpy(M))
+        pinned.append(t)
+    ref = []
+    with _ctx(rsx, shape, c, 32) as a:
+        a.set_optical_constants(ENERGIES, K)
+        for i, M in enumerate(Ms):
+            a.set_morphology(M)
+            ref.append(a.run((0, 30, 180), energy_indices=[i]))
+    got = []
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    with _ctx(rsx, shape, c, 32) as a, _ctx(rsx, shape, c, 32) as b:
+        cx = [a, b]
+        for x in cx:
+            x.set_optical_constants(ENERGIES, K)
+        cx[0].set_morphology(pinned[0].numpy(), stream=streams[0], async_copy=True)
+        for i in range(3):
+            if i + 1 < 3:
+                j = (i + 1) % 2
+                cx[j].set_morphology(pinned[i + 1].numpy(), stream=streams[j], async_copy=True)
+            got.append(cx[i % 2].run((0, 30, 180), energy_indices=[i], stream=streams[i % 2]))
+    for g, r in zip(got, ref):
+        np.testing.assert_array_equal(g, r)
+
+
+def test_async_upload_needs_page_locked_memory(rsx):
+    shape, c = (2, 8, 8), 2
+    M, K = _inputs(shape, c, 32, seed=41)
+    with _ctx(rsx, shape, c, 32) as a:
+        with pytest.raises(rsx.RsxError) as e:
+            a.set_morphology(M, async_copy=True)   # pageable numpy memory
+        assert e.value.code == rsx.RSX_ERR_INVALID
+
+
 # ------------------------------------------------------------- error paths
 def test_errors_are_reported_and_write_nothing(rsx):
     shape, c = (2, 8, 8), 2
