@@ -269,6 +269,15 @@ template <typename C> __host__ __device__ __forceinline__ void dft32(C* v) {
   dft32_combine<0>(v, e, o);
 }
 
+// v[out_pos<16>(K)] *= W32^K for K = 0..15: the odd half of a 32-point DFT
+// after its 16-point DFT (compile-time twiddles).
+template <int K, typename C> __device__ __forceinline__ void w32_outputs(C* v) {
+  if constexpr (K < 16) {
+    v[out_pos<16>(K)] = w32<K>(v[out_pos<16>(K)]);
+    w32_outputs<K + 1>(v);
+  }
+}
+
 // A 32-point forward DFT split over a lane pair (partner = lane ^ 16): the
 // lane with h = 0 holds the even samples x[2m] in v[m], the lane with h = 1
 // the odd samples x[2m + 1] (m = 0..15).  Each does its 16-point DFT, the

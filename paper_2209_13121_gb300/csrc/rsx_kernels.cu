@@ -912,22 +912,31 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 }
 
 // y-FFT fused with the pruned z transform (FP32, ny = 1024, nz a power of
-// two up to 1024, nx a multiple of 8).  Work items are (field, 8-column tile); each has nz
-// steps (its z-slices).  The items' steps are laid end to end and cut into
-// one contiguous range of L >= nz steps per persistent CTA, so every CTA
-// does the same number of steps and an item is split between at most two
-// CTAs: the part that starts at z = 0 goes to slot 0 of `part`, the other
-// to slot 1, and k_ewald_bins adds them.  Per step, the slice's 8 x 1024
-// tile arrives by 2-D tensor TMA (two buffers, the next-but-one step in
-// flight); 512 threads transform it with the four-step 32 x 32 scheme, each
-// 32-point DFT split over a lane pair (dft32_pair), and every thread then
-// owns 16 pixels (row k2 + 32 k1, k1 = 16 h .. 16 h + 15) for which it
-// accumulates, across the item's z-slices, the two q_z bins b0 and b0 + 1
-// of Eq. (Ewald):
+// two up to 1024, nx a multiple of 8).  Work items are (field, 8-column
+// tile); each has nz steps (its z-slices).  The items' steps are laid end to
+// end and cut into one contiguous range of L >= nz steps per persistent CTA,
+// so every CTA does the same number of steps and an item is split between
+// at most two CTAs: the part that starts at z = 0 goes to slot 0 of `part`,
+// the other to slot 1, and k_ewald_bins adds them.
+//
+// Per step the slice's 8 x 1024 tile arrives by 2-D tensor TMA (two
+// buffers).  The four-step 32 x 32 FFT is split between the two halves of
+// the block (hw = warp / 8, uniform per warp, so every twiddle below is a
+// compile-time constant and no lane selects between two roles):
+//  stage 1: half hw takes the samples n2 = 2m + hw of row n1 and stores
+//           its 16-point DFT, the odd half times W32^k, to `tr`;
+//  stage 2: thread (k2, hw) forms the stage-1 outputs X1[n1][k2] = E +- O'
+//           for n1 = 2m + hw, applies W1024^(n1 k2), does its 16-point DFT
+//           (odd half times W32^k) and swaps halves with its partner through
+//           the input buffer it has just consumed;
+// after which each thread holds 16 pixels (row k2 + 32 k1, k1 = 16 hw ..
+// 16 hw + 15) and accumulates, across the item's z-slices, the two q_z bins
+// b0 and b0 + 1 of Eq. (Ewald):
 //   A0 += Y(z) W^(b0 z),  A1 += Y(z) W^(b0 z) W^z,  W = exp(-2 pi i / nz),
 // with b0 per pixel from the energy's geometry (0 for pixels off the
 // sphere, which k_ewald_bins zeroes).  The y-transformed slices are never
-// written.  Waits are bounded as in k_col_fft4s_tma.
+// written.  The input buffer is refilled (step + 2) once the swap has been
+// read.  Waits are bounded as in k_col_fft4s_tma.
 __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUtensorMap tmap, int nx,
                                                    int nz, long long ntiles, long long L, long long T,
                                                    const Geo<float>* __restrict__ geo,
@@ -940,12 +949,13 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   extern __shared__ __align__(128) unsigned char smem_a128[];
   C* in = reinterpret_cast<C*>(smem_a128);  // [2][1024][TX], dense (TMA boxes)
   C* tr = in + 2 * TILE;                     // [32][STR]
-  C* tw4 = tr + 32 * STR;                    // [32][32]
+  C* tw4 = tr + 32 * STR;                    // [32][32], symmetric
   C* twz = tw4 + 1024;                       // [nz]
   unsigned short* btab = reinterpret_cast<unsigned short*>(twz + nz);  // [1024][TX]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(btab + TILE);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  const int col = lane & 7, sub = (lane >> 3) & 1, h = lane >> 4;
+  const int col = lane & 7, hw = w >> 3;
+  const int q = (w & 7) * 4 + (lane >> 3);  // n1 in stage 1, k2 in stage 2
   const long long s0 = (long long)blockIdx.x * L;
   const long long s1 = s0 + L < T ? s0 + L : T;
   if (s0 >= s1) return;
@@ -963,8 +973,8 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     const int z = (int)(st % nz), f = (int)(item / ntiles), ti = (int)(item % ntiles);
     mbar_expect_tx(&bar[b], TILE * sizeof(C));
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      tma_load_3d(in + b * TILE + q * 256 * TX, &tmap, ti * 2 * TX, q * 256, f * nz + z, &bar[b]);
+    for (int k = 0; k < 4; ++k)
+      tma_load_3d(in + b * TILE + k * 256 * TX, &tmap, ti * 2 * TX, k * 256, f * nz + z, &bar[b]);
   };
   if (t == 0) {
     issue(s0, 0);
@@ -994,40 +1004,48 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
       }
       return;
     }
-    // stage 1: 32-point DFTs over n2 (rows n1 + 32 n2), twiddle, transpose
+    C* const xb = in + b * TILE;
+    // stage 1: 16-point DFT of the samples n2 = 2m + hw of row n1 = q
     {
-      const int n1 = 2 * w + sub;
-      const C* src = in + b * TILE;
-      C v[16], r[16];
+      C v[16];
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = src[(n1 + 32 * h + 64 * m) * TX + col];
-      dft32_pair(v, r, h);
+      for (int m = 0; m < 16; ++m) v[m] = xb[(q + 32 * hw + 64 * m) * TX + col];
+      dft_reg<16>(v);
+      if (hw) w32_outputs<0>(v);
 #pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const int k2 = 16 * h + k;
-        tr[k2 * STR + n1 * TX + col] = cmul(r[k], tw4[k2 * 32 + n1]);
+      for (int k = 0; k < 16; ++k) tr[(16 * hw + k) * STR + q * TX + col] = v[out_pos<16>(k)];
+    }
+    __syncthreads();  // stage-1 halves in tr, bins in place; xb consumed
+    // stage 2: X1[n1][k2] = E +- O' (minus for k2 >= 16), times W1024^(n1 k2)
+    C v[16];
+    {
+      const int k = q & 15;
+      const bool upper = q >= 16;  // warp-uniform
+#pragma unroll
+      for (int m = 0; m < 16; ++m) {
+        const int n1 = 2 * m + hw;
+        const C e = tr[k * STR + n1 * TX + col];
+        const C o = tr[(16 + k) * STR + n1 * TX + col];
+        v[m] = cmul(upper ? csub(e, o) : cadd(e, o), tw4[n1 * 32 + q]);
       }
-    }
-    __syncthreads();  // input buffer b consumed, transpose complete, bins in place
-    if (t == 0 && st + 2 < s1) {
-      fence_proxy_async();
-      issue(st + 2, b);
-    }
-    // stage 2: 32-point DFTs over n1, then the two q_z bins of 16 pixels
-    {
-      const int k2 = 2 * w + sub;
-      C v[16], r[16];
+      dft_reg<16>(v);
+      if (hw) w32_outputs<0>(v);
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = tr[k2 * STR + (2 * m + h) * TX + col];
-      dft32_pair(v, r, h);
+      for (int k2 = 0; k2 < 16; ++k2) xb[(16 * hw + k2) * 256 + q * TX + col] = v[out_pos<16>(k2)];
+    }
+    __syncthreads();  // halves swapped; every stage-2 read of tr is done
+    {
       const C wz = twz[z];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        const int row = k2 + 512 * h + 32 * k;
+        const C mine = v[out_pos<16>(k)];
+        const C other = xb[(16 * (1 - hw) + k) * 256 + q * TX + col];
+        const C y = hw ? csub(other, mine) : cadd(mine, other);  // X[k2 + 32 (16 hw + k)]
+        const int row = q + 512 * hw + 32 * k;
         const int b0 = btab[row * TX + col];
-        const C q = cmul(r[k], twz[(b0 * z) & (nz - 1)]);
-        acc0[k] = cadd(acc0[k], q);
-        acc1[k] = cadd(acc1[k], cmul(q, wz));
+        const C qq = cmul(y, twz[(b0 * z) & (nz - 1)]);
+        acc0[k] = cadd(acc0[k], qq);
+        acc1[k] = cadd(acc1[k], cmul(qq, wz));
       }
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
         const int slot = st - z >= s0 ? 0 : 1;
@@ -1035,12 +1053,16 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         float4* dst = part + ((size_t)slot * 3 + f) * npix + (size_t)ti * TX + col;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
-          const int row = k2 + 512 * h + 32 * k;
+          const int row = q + 512 * hw + 32 * k;
           dst[(size_t)row * nx] = make_float4(acc0[k].x, acc0[k].y, acc1[k].x, acc1[k].y);
         }
       }
     }
-    __syncthreads();  // the transpose buffer and the bins are rewritten next step
+    __syncthreads();  // the swap is read: xb may be refilled, tr and bins rewritten
+    if (t == 0 && st + 2 < s1) {
+      fence_proxy_async();
+      issue(st + 2, b);
+    }
   }
 }
 
