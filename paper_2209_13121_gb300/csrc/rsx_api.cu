@@ -132,6 +132,7 @@ struct rsx_context {
   // buffers for the TMA y pass (FP32, ny = 1024); valid when the flag is set
   alignas(64) CUtensorMap tmap_p;
   alignas(64) CUtensorMap tmap_ft;
+  alignas(64) CUtensorMap tmap_pz;  // p for the fused y+z pass
   bool has_tmap_p = false, has_tmap_ft = false;
   // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
   // [2 slots][3][ny][nx] float4
@@ -228,7 +229,8 @@ int upload_tw4(rsx_context* c) {
 
 // A tensor map over `ncomp` fields of [nz][ny][nx] complex float viewed as
 // [ncomp nz][ny][2 nx] floats with 16 x 256 x 1 boxes (TMA y pass).
-bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m) {
+bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m,
+               CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -246,8 +248,8 @@ bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m) {
   const cuuint32_t box[3] = {16, 256, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
@@ -443,7 +445,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
       long long L = 0;
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-        RSX_CK(rsx::launch_yz_tma(&c->tmap_p, g.nx, g.ny, g.nz, (const Geo<float>*)c->geo,
+        RSX_CK(rsx::launch_yz_tma(&c->tmap_pz, g.nx, g.ny, g.nz, (const Geo<float>*)c->geo,
                                   c->twz, c->tw4, c->part, c->err, c->n_sm, &L, s),
                "y-FFT + z-bins kernel");
       }
@@ -605,6 +607,10 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     c->n_sm = 0;
   if (cfg->precision == 32 && cfg->ny == 1024 && cfg->nx % 8 == 0 && c->n_sm > 0) {
     c->has_tmap_p = make_tmap(c, c->p, 3, &c->tmap_p);
+    // the fused y+z pass reads 64-byte halves of 128-byte lines from two
+    // blocks at once: promote to 128 bytes, not 256
+    c->has_tmap_p = c->has_tmap_p &&
+                    make_tmap(c, c->p, 3, &c->tmap_pz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
     if (c->ft) c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft);
   }
   if (uses_yz(cfg) && (e = cudaMalloc(&c->part, part_bytes(cfg))) != cudaSuccess) {

@@ -912,12 +912,15 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 }
 
 // y-FFT fused with the pruned z transform (FP32, ny = 1024, nz a power of
-// two up to 1024, nx a multiple of 8).  Work items are (field, 8-column
-// tile); each has nz steps (its z-slices).  The items' steps are laid end to
-// end and cut into one contiguous range of L >= nz steps per persistent CTA,
-// so every CTA does the same number of steps and an item is split between
-// at most two CTAs: the part that starts at z = 0 goes to slot 0 of `part`,
-// the other to slot 1, and k_ewald_bins adds them.
+// two up to 1024, nx a multiple of 16).  Work items are (field, pair of
+// adjacent 8-column tiles); each has nz steps (its z-slices).  The items'
+// steps are laid end to end and cut into one contiguous range of L >= nz
+// steps per pair of persistent CTAs (blocks 2j and 2j + 1 take the even and
+// the odd tile of the same steps, so the two 64-byte halves of every
+// 128-byte row segment are read at about the same time: DRAM fetches whole
+// lines).  Every CTA does the same number of steps and an item is split
+// between at most two CTA pairs: the part that starts at z = 0 goes to slot
+// 0 of `part`, the other to slot 1, and k_ewald_bins adds them.
 //
 // Per step the slice's 8 x 1024 tile arrives by 2-D tensor TMA (two
 // buffers).  The four-step 32 x 32 FFT is split between the two halves of
@@ -956,10 +959,11 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int col = lane & 7, hw = w >> 3;
   const int q = (w & 7) * 4 + (lane >> 3);  // n1 in stage 1, k2 in stage 2
-  const long long s0 = (long long)blockIdx.x * L;
+  const long long s0 = (long long)(blockIdx.x >> 1) * L;
   const long long s1 = s0 + L < T ? s0 + L : T;
   if (s0 >= s1) return;
-  const long long npix = 1024LL * nx;
+  const long long npix = 1024LL * nx, half = ntiles >> 1;
+  const int mem = blockIdx.x & 1;
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -970,7 +974,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   __syncthreads();
   auto issue = [&](long long st, int b) {
     const long long item = st / nz;
-    const int z = (int)(st % nz), f = (int)(item / ntiles), ti = (int)(item % ntiles);
+    const int z = (int)(st % nz), f = (int)(item / half), ti = (int)(2 * (item % half) + mem);
     mbar_expect_tx(&bar[b], TILE * sizeof(C));
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -986,7 +990,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     const int b = i & 1;
     const long long item = st / nz;
     const int z = (int)(st % nz);
-    const int ti = (int)(item % ntiles);
+    const int ti = (int)(2 * (item % half) + mem);
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
       for (int e = t; e < TILE; e += 512) {
         const int b0 = geo[(size_t)(e >> 3) * nx + ti * TX + (e & 7)].b0;
@@ -1049,7 +1053,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
       }
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
         const int slot = st - z >= s0 ? 0 : 1;
-        const int f = (int)(item / ntiles);
+        const int f = (int)(item / half);
         float4* dst = part + ((size_t)slot * 3 + f) * npix + (size_t)ti * TX + col;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -1090,7 +1094,7 @@ __global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, in
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     float4 v = part[(size_t)f * npix + pix];
-    const long long item = f * ntiles + ti;
+    const long long item = f * (ntiles >> 1) + (ti >> 1);  // the tile pair's work item
     if ((item * nz) / L != ((item + 1) * nz - 1) / L) {
       const float4 u = part[(size_t)(3 + f) * npix + pix];
       v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
@@ -1646,22 +1650,23 @@ cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const Po
 }
 
 bool yz_fusable(int nx, int ny, int nz) {
-  return ny == 1024 && nx % 8 == 0 && nx >= 8 && nz >= 1 && nz <= 1024 && (nz & (nz - 1)) == 0;
+  return ny == 1024 && nx % 16 == 0 && nz >= 1 && nz <= 1024 && (nz & (nz - 1)) == 0;
 }
 
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<float>* geo,
                           const void* twz, const void* tw4, void* part, int* err, int n_sm,
                           long long* L_out, cudaStream_t s) {
   if (!yz_fusable(nx, ny, nz) || n_sm <= 0) return cudaErrorInvalidValue;
-  const long long ntiles = nx / 8, items = 3 * ntiles, T = items * nz;
-  const long long grid = items < n_sm ? items : n_sm;
-  const long long L = (T + grid - 1) / grid;  // >= nz: an item meets at most two blocks
+  const long long ntiles = nx / 8, items = 3 * (ntiles / 2), T = items * nz;
+  const long long pairs = items < n_sm / 2 ? items : n_sm / 2;
+  if (pairs < 1) return cudaErrorInvalidValue;
+  const long long L = (T + pairs - 1) / pairs;  // >= nz: an item meets at most two pairs
   *L_out = L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 1024 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;
   cudaError_t e = cudaFuncSetAttribute(k_yz_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_yz_tma<<<(unsigned)grid, 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, ntiles, L, T, geo,
+  k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, ntiles, L, T, geo,
                                              (const float2*)twz, (const float2*)tw4, (float4*)part,
                                              err);
   return cudaGetLastError();

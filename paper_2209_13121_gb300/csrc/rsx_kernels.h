@@ -115,8 +115,8 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, cudaStream_t s);
 // The y-FFT fused with the pruned z transform (FP32): yz_fusable says
-// whether the shape qualifies (ny = 1024, nx a multiple of 8, nz a power of
-// two up to 1024).
+// whether the shape qualifies (ny = 1024, nx a multiple of 16, nz a power
+// of two up to 1024).
 // launch_yz_tma writes the two q_z bins of every pixel and field into part
 // ([2 slots][3][ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
 // the step count per block that launch_ewald_bins needs to add the slots.
