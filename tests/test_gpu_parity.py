@@ -234,8 +234,11 @@ def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
 
 # Sizes at which the persistent FP32 passes give each block several work
 # items: x rows (nx = 1024: groups of two rows and an odd tail) and y tiles
-# (ny = 1024: both input buffers refilled more than once).
-MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2)]
+# (ny = 1024: both input buffers refilled more than once); the fused y+z
+# pass at its edges: nz = 1 (both q_z bins are plane 0), the narrowest
+# width (one tile pair), a field split between two block pairs.
+MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2), ((1, 1024, 64), 3), ((4, 1024, 16), 2),
+         ((2, 1024, 512), 2)]
 
 
 @pytest.mark.parametrize("shape,c", MULTI, ids=["x".join(map(str, s)) for s, _ in MULTI])
@@ -249,6 +252,26 @@ def test_scatter_angle_persistent_passes(rsx, shape, c):
             ctx.scatter_angle(ie, alpha, img)
             ref = O.scatter_one_angle(M, K[ie], ENERGIES[ie], VOXEL, alpha)
             assert_image_close(img.cpu().numpy(), ref, 32)
+
+
+@pytest.mark.parametrize("frame", [0, 1])
+def test_fused_yz_pass_off_sphere_pixels_and_frames(rsx, frame):
+    """ny = 1024 with 2 nm voxels at 270 eV: the detector corners lie
+    outside the Ewald sphere (zero in both paths), in either frame."""
+    shape, c, vox = (4, 1024, 32), 2, 2.0
+    M, K = _inputs(shape, c, 32, seed=18)
+    nz, ny, nx = shape
+    with rsx.Context(nx, ny, nz, c, vox, precision=32, frame=frame) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        img = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        ctx.scatter_angle(0, 0.6, img)
+        got = img.cpu().numpy()
+    ref = O.scatter_one_angle(M, K[0], ENERGIES[0], vox, 0.6,
+                              uT_mode="literal" if frame == 0 else "lab")
+    assert (ref == 0).sum() > 100
+    assert np.array_equal(got == 0, ref == 0)
+    assert_image_close(got, ref, 32)
 
 
 # ------------------------------------------------------- Algorithm 1 (a7)
