@@ -391,56 +391,58 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
 
   if (w == PW + 3 * FG) {  // producer warp, one lane
     if (lane != 0) return;
-    const long long G = nmine * pp.c;
-    long long g = 0;
+    // stage g = rr * c + j goes to slot g mod S; its k-th reuse (k = g / S)
+    // waits for the k-1-th release.  32-bit counters (g < 2^31).
+    const int G = (int)nmine * pp.c;
+    int g = 0, slot = 0, k = 0, j = 0;
+    long long row = blockIdx.x;
     for (; g < G; ++g) {
-      const int slot = (int)(g % S);
-      const long long k = g / S;
       if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), kPoll)) {
         atomicOr(err, 1);
         *abort_flag = 1;
         break;
       }
-      const long long rr = g / pp.c, row = blockIdx.x + rr * gridDim.x;
-      const int j = (int)(g % pp.c);
       mbar_expect_tx(&full[slot], kStageBytes);
       bulk_g2s(stage + slot * NX, M + (size_t)j * N + (size_t)row * NX, kStageBytes, &full[slot]);
+      if (++slot == S) slot = 0, ++k;
+      if (++j == pp.c) j = 0, row += gridDim.x;
     }
     // nothing may be in flight when the block exits
-    for (long long d = g - 1; d >= 0 && d >= g - S; --d)
+    for (int d = g - 1; d >= 0 && d >= g - S; --d)
       mbar_wait_bounded(&full[d % S], (unsigned)((d / S) & 1), kPoll);
     return;
   }
 
   if (w < PW) {  // polarisation warps
     bool failed = false;
-    for (long long rr = 0; rr < nmine; ++rr) {
+    int slot = 0, ph = 0;  // stage rr * c + j: its slot and the parity of its use
+    for (int rr = 0; rr < (int)nmine; ++rr) {
       PolAcc<float> acc[SL];
 #pragma unroll
       for (int sl = 0; sl < SL; ++sl) pol_zero(acc[sl]);
       for (int j = 0; j < pp.c; ++j) {
+        const int cs = slot, cph = ph;
+        if (++slot == S) slot = 0, ph ^= 1;
         failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
         if (failed) break;
-        const long long g = rr * pp.c + j;
-        const int slot = (int)(g % S);
         // warp-uniform: a lane that gave up makes its whole warp give up
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[slot], (unsigned)((g / S) & 1), kPoll))) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, kPoll))) {
           failed = true;
           atomicOr(err, 1);
           *abort_flag = 1;
           break;
         }
-        const float4* st = stage + slot * NX;
+        const float4* st = stage + cs * NX;
         float4 cur[SL];
 #pragma unroll
         for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (lane == 0) mbar_arrive(&empty[cs]);
 #pragma unroll
         for (int sl = 0; sl < SL; ++sl)
           pol_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
       }
-      const int i = (int)(rr % NP);
+      const int i = rr % NP;
       if (rr >= NP) named_bar_sync(1 + NP + i, NB);  // transforms of row rr - NP done
       if (!failed) {
         C* Pi = P + i * 3 * FS;
@@ -461,8 +463,8 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
 
   // transform warps: group fg, field f
   const int fg = (w - PW) / 3, f = (w - PW) % 3;
-  for (long long rr = fg; rr < nmine; rr += FG) {
-    const int i = (int)(rr % NP);
+  for (int rr = fg; rr < (int)nmine; rr += FG) {
+    const int i = rr % NP;
     named_bar_sync(1 + i, NB);
     if (*abort_flag == 0) {
       const long long row = blockIdx.x + rr * gridDim.x;
@@ -941,7 +943,7 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 // written.  The input buffer is refilled (step + 2) once the swap has been
 // read.  Waits are bounded as in k_col_fft4s_tma.
 __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUtensorMap tmap, int nx,
-                                                   int nz, long long ntiles, long long L, long long T,
+                                                   int nz, int ntiles, int L, int T,
                                                    const Geo<float>* __restrict__ geo,
                                                    const float2* __restrict__ twz_g,
                                                    const float2* __restrict__ tw4_g,
@@ -959,10 +961,12 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int col = lane & 7, hw = w >> 3;
   const int q = (w & 7) * 4 + (lane >> 3);  // n1 in stage 1, k2 in stage 2
-  const long long s0 = (long long)(blockIdx.x >> 1) * L;
-  const long long s1 = s0 + L < T ? s0 + L : T;
+  // 32-bit step arithmetic (T < 2^31); nz and ntiles / 2 are powers of two
+  const int s0 = (int)(blockIdx.x >> 1) * L;
+  const int s1 = s0 + L < T ? s0 + L : T;
   if (s0 >= s1) return;
-  const long long npix = 1024LL * nx, half = ntiles >> 1;
+  const long long npix = 1024LL * nx;
+  const int half = ntiles >> 1, lognz = __ffs(nz) - 1, loghalf = __ffs(half) - 1;
   const int mem = blockIdx.x & 1;
   if (t == 0) {
     mbar_init(&bar[0], 1);
@@ -972,9 +976,9 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   for (int i = t; i < 1024; i += 512) tw4[i] = tw4_g[i];
   for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
   __syncthreads();
-  auto issue = [&](long long st, int b) {
-    const long long item = st / nz;
-    const int z = (int)(st % nz), f = (int)(item / half), ti = (int)(2 * (item % half) + mem);
+  auto issue = [&](int st, int b) {
+    const int item = st >> lognz;
+    const int z = st & (nz - 1), f = item >> loghalf, ti = 2 * (item & (half - 1)) + mem;
     mbar_expect_tx(&bar[b], TILE * sizeof(C));
 #pragma unroll
     for (int k = 0; k < 4; ++k)
@@ -986,11 +990,11 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   }
   C acc0[16], acc1[16];
   int i = 0;
-  for (long long st = s0; st < s1; ++st, ++i) {
+  for (int st = s0; st < s1; ++st, ++i) {
     const int b = i & 1;
-    const long long item = st / nz;
-    const int z = (int)(st % nz);
-    const int ti = (int)(2 * (item % half) + mem);
+    const int item = st >> lognz;
+    const int z = st & (nz - 1);
+    const int ti = 2 * (item & (half - 1)) + mem;
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
       for (int e = t; e < TILE; e += 512) {
         const int b0 = geo[(size_t)(e >> 3) * nx + ti * TX + (e & 7)].b0;
@@ -1053,7 +1057,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
       }
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
         const int slot = st - z >= s0 ? 0 : 1;
-        const int f = (int)(item / half);
+        const int f = item >> loghalf;
         float4* dst = part + ((size_t)slot * 3 + f) * npix + (size_t)ti * TX + col;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
@@ -1075,7 +1079,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
 // constant part returned at q = 0, the projection and the interpolation;
 // written in fftshift order.
 __global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, int nz,
-                             long long ntiles, long long L, const Geo<float>* __restrict__ geo,
+                             int ntiles, int L, const Geo<float>* __restrict__ geo,
                              float dc0, float dc1, float dc2, float* __restrict__ img) {
   using C = float2;
   const long long npix = (long long)nx * ny;
@@ -1088,13 +1092,13 @@ __global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, in
     *dst = 0.f;
     return;
   }
-  const long long ti = mx / 8;
+  const int ti = mx >> 3;
   C a0[3], a1[3];
   const float dcs[3] = {dc0, dc1, dc2};
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     float4 v = part[(size_t)f * npix + pix];
-    const long long item = f * (ntiles >> 1) + (ti >> 1);  // the tile pair's work item
+    const int item = f * (ntiles >> 1) + (ti >> 1);  // the tile pair's work item
     if ((item * nz) / L != ((item + 1) * nz - 1) / L) {
       const float4 u = part[(size_t)(3 + f) * npix + pix];
       v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
@@ -1666,7 +1670,8 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<fl
                       8192 * sizeof(unsigned short) + 2 * 8;
   cudaError_t e = cudaFuncSetAttribute(k_yz_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, ntiles, L, T, geo,
+  k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, (int)ntiles,
+                                                     (int)L, (int)T, geo,
                                              (const float2*)twz, (const float2*)tw4, (float4*)part,
                                              err);
   return cudaGetLastError();
@@ -1676,7 +1681,7 @@ cudaError_t launch_ewald_bins(const void* part, int nx, int ny, int nz, long lon
                               const Geo<float>* geo, float dc0, float dc1, float dc2, float* img,
                               cudaStream_t s) {
   const long long npix = (long long)nx * ny;
-  k_ewald_bins<<<grid1(npix, 256), 256, 0, s>>>((const float4*)part, nx, ny, nz, nx / 8, L, geo,
+  k_ewald_bins<<<grid1(npix, 256), 256, 0, s>>>((const float4*)part, nx, ny, nz, nx / 8, (int)L, geo,
                                                 dc0, dc1, dc2, img);
   return cudaGetLastError();
 }
