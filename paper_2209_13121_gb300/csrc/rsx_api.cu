@@ -416,6 +416,11 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
                                          c->n_sm, s),
                "polarisation + x-FFT kernel");
         done = true;
+      } else if (g.nx == 1024 && g.algorithm == 2 && c->n_sm > 0) {
+        RSX_CK(rsx::launch_ntp_fft4s_tma(c->nt, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
+                                         c->n_sm, s),
+               "N_t polarisation + x-FFT kernel");
+        done = true;
       }
     }
     if (done) {

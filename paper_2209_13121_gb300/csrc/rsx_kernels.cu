@@ -13,6 +13,8 @@
 #include <cuda.h>  // CUtensorMap (the type only; the library does not link libcuda)
 #include <math.h>
 
+#include <type_traits>
+
 #include "rsx_device.cuh"
 #include "rsx_kernels.h"
 
@@ -342,14 +344,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
   for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
 }
 
-// x pass of Algorithm 1 (FP32, nx = 1024) as a warp-specialised bulk-copy
-// pipeline.  Three roles per block:
-//  * a producer lane streams (row, component) slices of the morphology,
-//    16 KB each, into a ring of S shared-memory stages (full/empty
-//    mbarrier pairs), up to S slices ahead;
+// x pass (FP32, nx = 1024) as a warp-specialised bulk-copy pipeline, for
+// Algorithm 1 (NT = false: the morphology, c slices of 16 KB per row) or
+// Algorithm 2 (NT = true: the five stored entries of N_t, 8 KB each).
+// Three roles per block:
+//  * a producer lane streams (row, component or entry) slices into a ring
+//    of S shared-memory stages (full/empty mbarrier pairs), up to S slices
+//    ahead;
 //  * PW polarisation warps accumulate 1024 / (32 PW) voxels per thread from
-//    each stage, release it per warp, and write the row's three fields into
-//    one of NP row buffers;
+//    each stage (Algorithm 1: pol_add per component; Algorithm 2: p = N_t e
+//    entry by entry), release it per warp, and write the row's three fields
+//    into one of NP row buffers;
 //  * FG groups of three transform warps (group g takes the rows r with
 //    r mod FG = g) run the four-step FFT of k_pol_fft4s on a filled buffer
 //    and store the spectrum.
@@ -360,16 +365,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
 // roles skip their work but still complete the barrier protocol (which has
 // no unbounded wait left), the producer waits (bounded) for its copies in
 // flight, and the block exits.
-template <int S, int NP, int PW, int FG>
+template <int S, int NP, int PW, int FG, bool NT>
 __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
-    const float4* __restrict__ M, long long N, long long nrows, PolParams<float> pp,
+    const void* __restrict__ src, long long N, long long nrows, PolParams<float> pp,
     float2* __restrict__ p, const float2* __restrict__ tw4_g, int* __restrict__ err) {
   using C = float2;
+  using SrcT = typename std::conditional<NT, float2, float4>::type;
   constexpr int NX = 1024, TP = 32 * PW, SL = NX / TP, FS = 32 * 33, NB = TP + 96;
   static_assert(NX % TP == 0 && 1 + 2 * NP <= 15, "layout");
-  constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(float4);
+  constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(SrcT);
   extern __shared__ __align__(128) unsigned char smem_a128[];
-  float4* stage = reinterpret_cast<float4*>(smem_a128);    // [S][NX]
+  SrcT* stage = reinterpret_cast<SrcT*>(smem_a128);        // [S][NX]
   C* P = reinterpret_cast<C*>(stage + S * NX);             // [NP][3][FS]
   C* tw4 = P + NP * 3 * FS;                                 // [32][32]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(tw4 + 1024);
@@ -393,7 +399,9 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
     if (lane != 0) return;
     // stage g = rr * c + j goes to slot g mod S; its k-th reuse (k = g / S)
     // waits for the k-1-th release.  32-bit counters (g < 2^31).
-    const int G = (int)nmine * pp.c;
+    const int per_row = NT ? 5 : pp.c;
+    const int G = (int)nmine * per_row;
+    const SrcT* M = reinterpret_cast<const SrcT*>(src);
     int g = 0, slot = 0, k = 0, j = 0;
     long long row = blockIdx.x;
     for (; g < G; ++g) {
@@ -405,7 +413,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
       mbar_expect_tx(&full[slot], kStageBytes);
       bulk_g2s(stage + slot * NX, M + (size_t)j * N + (size_t)row * NX, kStageBytes, &full[slot]);
       if (++slot == S) slot = 0, ++k;
-      if (++j == pp.c) j = 0, row += gridDim.x;
+      if (++j == per_row) j = 0, row += gridDim.x;
     }
     // nothing may be in flight when the block exits
     for (int d = g - 1; d >= 0 && d >= g - S; --d)
@@ -415,12 +423,20 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
 
   if (w < PW) {  // polarisation warps
     bool failed = false;
-    int slot = 0, ph = 0;  // stage rr * c + j: its slot and the parity of its use
+    const int per_row = NT ? 5 : pp.c;
+    int slot = 0, ph = 0;  // stage rr * per_row + j: its slot and the parity of its use
     for (int rr = 0; rr < (int)nmine; ++rr) {
-      PolAcc<float> acc[SL];
+      PolAcc<float> acc[SL];  // Algorithm 1
+      C pe[SL][3];            // Algorithm 2: p = N_t e, before the frame rotation
 #pragma unroll
-      for (int sl = 0; sl < SL; ++sl) pol_zero(acc[sl]);
-      for (int j = 0; j < pp.c; ++j) {
+      for (int sl = 0; sl < SL; ++sl) {
+        if constexpr (NT) {
+          pe[sl][0] = pe[sl][1] = pe[sl][2] = make_float2(0.f, 0.f);
+        } else {
+          pol_zero(acc[sl]);
+        }
+      }
+      for (int j = 0; j < per_row; ++j) {
         const int cs = slot, cph = ph;
         if (++slot == S) slot = 0, ph ^= 1;
         failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
@@ -432,15 +448,39 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
           *abort_flag = 1;
           break;
         }
-        const float4* st = stage + cs * NX;
-        float4 cur[SL];
+        const SrcT* st = stage + cs * NX;
+        SrcT cur[SL];
 #pragma unroll
         for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[cs]);
+        if constexpr (NT) {
+          // entries xx, xy, yy, xz, yz of the symmetric N_t times e = (ce, se, 0):
+          // px = xx ce + xy se, py = xy ce + yy se, pz = xz ce + yz se
+          auto madd = [&](int f, float w) {
 #pragma unroll
-        for (int sl = 0; sl < SL; ++sl)
-          pol_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
+            for (int sl = 0; sl < SL; ++sl) {
+              pe[sl][f].x += cur[sl].x * w;
+              pe[sl][f].y += cur[sl].y * w;
+            }
+          };
+          if (j == 0) {
+            madd(0, pp.ce);
+          } else if (j == 1) {
+            madd(0, pp.se);
+            madd(1, pp.ce);
+          } else if (j == 2) {
+            madd(1, pp.se);
+          } else if (j == 3) {
+            madd(2, pp.ce);
+          } else {
+            madd(2, pp.se);
+          }
+        } else {
+#pragma unroll
+          for (int sl = 0; sl < SL; ++sl)
+            pol_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
+        }
       }
       const int i = rr % NP;
       if (rr >= NP) named_bar_sync(1 + NP + i, NB);  // transforms of row rr - NP done
@@ -450,7 +490,22 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
         for (int sl = 0; sl < SL; ++sl) {
           const int e = t + sl * TP;
           C out[3];
-          pol_final(acc[sl], pp, out);
+          if constexpr (NT) {
+            // the reference constant returns as -(c-1)/(4 pi) e when add_ref
+            const float inv_ref = pp.add_ref ? -(pp.c - 1) / (float)kFourPi : 0.f;
+            const C px = make_float2(pe[sl][0].x + inv_ref * pp.ce, pe[sl][0].y);
+            const C py = make_float2(pe[sl][1].x + inv_ref * pp.se, pe[sl][1].y);
+            if (pp.literal) {
+              out[0] = make_float2(pp.ce * px.x + pp.se * py.x, pp.ce * px.y + pp.se * py.y);
+              out[1] = make_float2(-pp.se * px.x + pp.ce * py.x, -pp.se * px.y + pp.ce * py.y);
+            } else {
+              out[0] = px;
+              out[1] = py;
+            }
+            out[2] = pe[sl][2];
+          } else {
+            pol_final(acc[sl], pp, out);
+          }
           Pi[e] = out[0];
           Pi[FS + e] = out[1];
           Pi[2 * FS + e] = out[2];
@@ -1631,26 +1686,41 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
-                                 void* p, const void* tw4, int* err, int n_sm, cudaStream_t s) {
-  // 3 stages, 2 row buffers, 4 polarisation warps, one transform group:
-  // ~106 KB of shared memory and 256 threads, two blocks per SM
-  constexpr int S = 3, NP = 2, PW = 4, FG = 1, CPS = 2;
-  if (nx != 1024 || n_sm <= 0 || ((uintptr_t)M & 15)) return cudaErrorInvalidValue;
+template <bool NT>
+static cudaError_t pol_fft4s_tma_impl(const void* src, int nx, int ny, int nz,
+                                      const PolParams<float>& pp, void* p, const void* tw4, int* err,
+                                      int n_sm, cudaStream_t s) {
+  // 2 row buffers, 4 polarisation warps, one transform group, 48 KB of
+  // stages (3 x 16 KB of morphology or 6 x 8 KB of N_t): ~106 KB of shared
+  // memory and 256 threads, two blocks per SM
+  constexpr int S = NT ? 6 : 3, NP = 2, PW = 4, FG = 1, CPS = 2;
+  constexpr size_t elem = NT ? sizeof(float2) : sizeof(float4);
+  if (nx != 1024 || n_sm <= 0 || ((uintptr_t)src & 15)) return cudaErrorInvalidValue;
   const long long N = (long long)nx * ny * nz, nrows = (long long)ny * nz;
   if (nrows <= 0) return cudaSuccess;
-  const size_t smem = (size_t)S * 1024 * sizeof(float4) +
-                      (NP * 3 * 32 * 33 + 1024) * sizeof(float2) + 2 * S * 8 + 16;
-  auto kern = k_pol_fft4s_tma<S, NP, PW, FG>;
+  const size_t smem = (size_t)S * 1024 * elem + (NP * 3 * 32 * 33 + 1024) * sizeof(float2) +
+                      2 * S * 8 + 16;
+  auto kern = k_pol_fft4s_tma<S, NP, PW, FG, NT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
   if (e != cudaSuccess) return e;
   const long long grid = nrows < (long long)CPS * n_sm ? nrows : (long long)CPS * n_sm;
-  kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>((const float4*)M, N, nrows, pp,
-                                                            (float2*)p, (const float2*)tw4, err);
+  kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>(src, N, nrows, pp, (float2*)p,
+                                                            (const float2*)tw4, err);
   return cudaGetLastError();
+}
+
+cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
+                                 void* p, const void* tw4, int* err, int n_sm, cudaStream_t s) {
+  return pol_fft4s_tma_impl<false>(M, nx, ny, nz, pp, p, tw4, err, n_sm, s);
+}
+
+cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
+                                 const PolParams<float>& pp, void* p, const void* tw4, int* err,
+                                 int n_sm, cudaStream_t s) {
+  return pol_fft4s_tma_impl<true>(nt, nx, ny, nz, pp, p, tw4, err, n_sm, s);
 }
 
 bool yz_fusable(int nx, int ny, int nz) {

@@ -114,6 +114,12 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 // persistent CTAs per SM (n_sm).
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, cudaStream_t s);
+// The same pipeline for Algorithm 2: p = N_t e from the five stored entries
+// of N_t ([5][N] complex float, 16-byte aligned; the reference constant
+// left out as k_nt_all stores it).
+cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
+                                 const PolParams<float>& pp, void* p, const void* tw4, int* err,
+                                 int n_sm, cudaStream_t s);
 // The y-FFT fused with the pruned z transform (FP32): yz_fusable says
 // whether the shape qualifies (ny = 1024, nx a multiple of 16, nz a power
 // of two up to 1024).
