@@ -247,6 +247,17 @@ def run_ours(args):
 
         e2e_steps(0, args.warmup)
         torch.cuda.synchronize()
+        # host-to-device bandwidth of this machine for the same pinned buffer
+        # (outside the timed region; the end-to-end number depends on it)
+        dbuf = torch.empty(Mh.shape, dtype=Mh.dtype, device="cuda")
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        dbuf.copy_(Mh, non_blocking=True)
+        e1.record()
+        e1.synchronize()
+        h2d_gbs = Mh_np.nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
+        del dbuf
+        torch.cuda.empty_cache()
         if ws > 1:
             dist.barrier()
         t0 = time.perf_counter()
@@ -258,7 +269,8 @@ def run_ours(args):
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_s = float(t.item())
         e2e = {"value": units / e2e_s / 1e9, "unit": UNIT,
-               "h2d_bytes_per_step": int(Mh_np.nbytes), "d2h_bytes_per_step": int(host_out.nbytes)}
+               "h2d_bytes_per_step": int(Mh_np.nbytes), "d2h_bytes_per_step": int(host_out.nbytes),
+               "h2d_gbs": round(h2d_gbs, 1)}
         for cx in ctxs:
             cx.close()
     else:
