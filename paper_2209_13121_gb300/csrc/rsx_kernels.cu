@@ -1041,7 +1041,6 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   };
   if (t == 0) {
     issue(s0, 0);
-    if (s0 + 1 < s1) issue(s0 + 1, 1);
   }
   C acc0[16], acc1[16];
   int i = 0;
@@ -1051,6 +1050,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     const int z = st & (nz - 1);
     const int ti = 2 * (item & (half - 1)) + mem;
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
+      __syncthreads();  // the previous step's reads of the bins are done
       for (int e = t; e < TILE; e += 512) {
         const int b0 = geo[(size_t)(e >> 3) * nx + ti * TX + (e & 7)].b0;
         btab[e] = (unsigned short)(b0 < 0 ? 0 : b0);
@@ -1062,8 +1062,8 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicOr(err, 1);
-        for (int d = 0; d < 2; ++d)
-          if (st + d < s1) mbar_wait_bounded(&bar[(i + d) & 1], ((i + d) >> 1) & 1, kPoll);
+        // only this step's load is in flight (the next one is issued later)
+        mbar_wait_bounded(&bar[b], (i >> 1) & 1, kPoll);
       }
       return;
     }
@@ -1079,6 +1079,12 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
       for (int k = 0; k < 16; ++k) tr[(16 * hw + k) * STR + q * TX + col] = v[out_pos<16>(k)];
     }
     __syncthreads();  // stage-1 halves in tr, bins in place; xb consumed
+    // the other buffer held the previous step, whose reads all came before
+    // this barrier: load the next step into it
+    if (t == 0 && st + 1 < s1) {
+      fence_proxy_async();
+      issue(st + 1, b ^ 1);
+    }
     // stage 2: X1[n1][k2] = E +- O' (minus for k2 >= 16), times W1024^(n1 k2)
     C v[16];
     {
@@ -1120,11 +1126,6 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
           dst[(size_t)row * nx] = make_float4(acc0[k].x, acc0[k].y, acc1[k].x, acc1[k].y);
         }
       }
-    }
-    __syncthreads();  // the swap is read: xb may be refilled, tr and bins rewritten
-    if (t == 0 && st + 2 < s1) {
-      fence_proxy_async();
-      issue(st + 2, b);
     }
   }
 }
