@@ -132,7 +132,9 @@ struct rsx_context {
   // buffers for the TMA y pass (FP32, ny = 1024); valid when the flag is set
   alignas(64) CUtensorMap tmap_p;
   alignas(64) CUtensorMap tmap_ft;
-  alignas(64) CUtensorMap tmap_pz;  // p for the fused y+z pass
+  alignas(64) CUtensorMap tmap_pz;   // p for the fused y+z pass
+  alignas(64) CUtensorMap tmap_ftz;  // ft (five N_t entries) for the fused y+z pass
+  bool has_tmap_ftz = false;
   bool has_tmap_p = false, has_tmap_ft = false;
   // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
   // [2 slots][3][ny][nx] float4
@@ -373,18 +375,34 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
   int rc = ensure_geo<R>(c, ie, s);
   if (rc) return rc;
   if ((rc = ensure_nt<R>(c, ie, s))) return rc;
-  const size_t bytes = 5 * (size_t)c->N * 2 * sizeof(R);
   {
     PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    RSX_CK(cudaMemcpyAsync(c->ft, c->nt, bytes, cudaMemcpyDeviceToDevice, s), "N_t copy");
-    RSX_CK(rsx::launch_row_fft<R>(c->ft, g.nx, 5LL * g.ny * g.nz, c->twx, s), "x-FFT kernel");
+    RSX_CK(rsx::launch_row_fft<R>(c->ft, g.nx, 5LL * g.ny * g.nz, c->twx, s, c->nt),
+           "x-FFT kernel");
+  }
+  const double dc = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
+  if constexpr (sizeof(R) == 4) {
+    if (c->part && c->has_tmap_ftz) {  // y-FFT and the q_z bins in one pass
+      long long L = 0;
+      {
+        PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+        RSX_CK(rsx::launch_yz_tma(&c->tmap_ftz, g.nx, g.ny, g.nz, 5, (const Geo<float>*)c->geo,
+                                  c->twz, c->tw4, c->part, c->err, c->n_sm, &L, s),
+               "y-FFT + z-bins kernel");
+      }
+      PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+      RSX_CK(rsx::launch_bins5_from_part(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
+                                         (float)dc, c->bins5, s),
+             "q_z bins kernel");
+      c->bins_energy = ie;
+      return RSX_OK;
+    }
   }
   if (g.ny > 1) {
     PhaseTimer pt(c, RSX_PHASE_FFTY, s);
     RSX_CK(launch_y_fft<R>(c, c->ft, 5, s), "y-FFT kernel");
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
-  const double dc = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
   RSX_CK(rsx::launch_zbins5<R>(c->ft, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, dc,
                                c->bins5, s),
          "q_z bins kernel");
@@ -450,7 +468,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
       long long L = 0;
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-        RSX_CK(rsx::launch_yz_tma(&c->tmap_pz, g.nx, g.ny, g.nz, (const Geo<float>*)c->geo,
+        RSX_CK(rsx::launch_yz_tma(&c->tmap_pz, g.nx, g.ny, g.nz, 3, (const Geo<float>*)c->geo,
                                   c->twz, c->tw4, c->part, c->err, c->n_sm, &L, s),
                "y-FFT + z-bins kernel");
       }
@@ -511,9 +529,12 @@ const char* rsx_last_error(void) { return g_err.c_str(); }
 // The fused y-FFT + pruned z pass serves FP32 Algorithms 1 and 2 on
 // qualifying shapes; its bins take 2 x 3 x 16 bytes per pixel.
 static bool uses_yz(const rsx_config* cfg) {
-  return cfg->precision == 32 && cfg->algorithm <= 2 && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
+  return cfg->precision == 32 && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
 }
-static size_t part_bytes(const rsx_config* cfg) { return 6 * (size_t)cfg->nx * cfg->ny * 16; }
+// two slots of (3 fields of p, or the linearity path's 5 N_t entries) x 2 bins
+static size_t part_bytes(const rsx_config* cfg) {
+  return 2 * (size_t)(cfg->algorithm == 3 ? 5 : 3) * cfg->nx * cfg->ny * 16;
+}
 
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
   if (check_config(cfg) != RSX_OK) return 0;
@@ -617,6 +638,8 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     c->has_tmap_p = c->has_tmap_p &&
                     make_tmap(c, c->p, 3, &c->tmap_pz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
     if (c->ft) c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft);
+    if (c->ft)
+      c->has_tmap_ftz = make_tmap(c, c->ft, 5, &c->tmap_ftz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
   }
   if (uses_yz(cfg) && (e = cudaMalloc(&c->part, part_bytes(cfg))) != cudaSuccess) {
     rc = cuda_fail(e, "y + z pass bins");

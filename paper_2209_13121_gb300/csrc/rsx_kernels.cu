@@ -669,10 +669,12 @@ __global__ void __launch_bounds__(256, 1) k_col_fft4s_tma(const __grid_constant_
   }
 }
 
-// Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d.
+// Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d and of
+// the linearity path; rows are read from src and written to p (src = p for
+// in place).
 template <typename R, int T, int EC>
-__global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p, int lognx,
-                                               long long nrows,
+__global__ void __launch_bounds__(T) k_row_fft(const typename RT<R>::C* src,
+                                               typename RT<R>::C* p, int lognx, long long nrows,
                                                const typename RT<R>::C* __restrict__ twx,
                                                int tw_in_smem) {
   using C = typename RT<R>::C;
@@ -686,9 +688,10 @@ __global__ void __launch_bounds__(T) k_row_fft(typename RT<R>::C* __restrict__ p
   const int rows_here = rl < ROWS ? (int)rl : ROWS;
   const int nel = rows_here << lognx;
   C* base = p + ((size_t)row0 << lognx);
+  const C* sbase = src + ((size_t)row0 << lognx);
   if (tw_in_smem)
     for (int i = threadIdx.x; i < nx; i += T) tws[i] = twx[i];
-  for (int e = threadIdx.x; e < nel; e += T) buf[padi(e)] = base[e];
+  for (int e = threadIdx.x; e < nel; e += T) buf[padi(e)] = sbase[e];
   __syncthreads();
   const C* tw = tw_in_smem ? tws : twx;
   block_fft<R, EC, T, false>(buf, lognx, ROWS, -1, nx, 1, tw);
@@ -998,7 +1001,7 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 // written.  The input buffer is refilled (step + 2) once the swap has been
 // read.  Waits are bounded as in k_col_fft4s_tma.
 __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUtensorMap tmap, int nx,
-                                                   int nz, int ntiles, int L, int T,
+                                                   int nz, int nf, int ntiles, int L, int T,
                                                    const Geo<float>* __restrict__ geo,
                                                    const float2* __restrict__ twz_g,
                                                    const float2* __restrict__ tw4_g,
@@ -1119,7 +1122,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
         const int slot = st - z >= s0 ? 0 : 1;
         const int f = item >> loghalf;
-        float4* dst = part + ((size_t)slot * 3 + f) * npix + (size_t)ti * TX + col;
+        float4* dst = part + ((size_t)slot * nf + f) * npix + (size_t)ti * TX + col;
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int row = q + 512 * hw + 32 * k;
@@ -1391,6 +1394,40 @@ __global__ void __launch_bounds__(256) k_zbins5(const typename RT<R>::C* __restr
   for (int q = 0; q < 5; ++q) {
     bins[(size_t)(2 * q) * npix + pix] = a0[q];
     bins[(size_t)(2 * q + 1) * npix + pix] = a1[q];
+  }
+}
+
+// The linearity path's per-energy bins from the fused y+z pass over the
+// five FFT'd N_t entries (k_yz_tma with five fields): slots added, the
+// constant returned to xx and yy at q = 0, and the k_zbins5 layout written
+// (bins[2q] = bin b0, bins[2q + 1] = bin b0 + 1 of entry q; zero off the
+// sphere).
+__global__ void __launch_bounds__(256) k_bins5_from_part(const float4* __restrict__ part, int nx,
+                                                         int ny, int nz, int ntiles, int L,
+                                                         const Geo<float>* __restrict__ geo,
+                                                         float dc, float2* __restrict__ bins) {
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const Geo<float> g = geo[pix];
+  const int ti = ((int)pix & (nx - 1)) >> 3;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (g.b0 >= 0) {
+      v = part[(size_t)q * npix + pix];
+      const int item = q * (ntiles >> 1) + (ti >> 1);
+      if ((item * nz) / L != ((item + 1) * nz - 1) / L) {
+        const float4 u = part[(size_t)(5 + q) * npix + pix];
+        v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
+      }
+      if (pix == 0 && (q == 0 || q == 2)) {
+        if (g.b0 == 0) v.x += dc;
+        if (g.b1 == 0) v.z += dc;
+      }
+    }
+    bins[(size_t)(2 * q) * npix + pix] = make_float2(v.x, v.y);
+    bins[(size_t)(2 * q + 1) * npix + pix] = make_float2(v.z, v.w);
   }
 }
 
@@ -1728,11 +1765,12 @@ bool yz_fusable(int nx, int ny, int nz) {
   return ny == 1024 && nx % 16 == 0 && nz >= 1 && nz <= 1024 && (nz & (nz - 1)) == 0;
 }
 
-cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<float>* geo,
+cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, void* part, int* err, int n_sm,
                           long long* L_out, cudaStream_t s) {
   if (!yz_fusable(nx, ny, nz) || n_sm <= 0) return cudaErrorInvalidValue;
-  const long long ntiles = nx / 8, items = 3 * (ntiles / 2), T = items * nz;
+  if (nf != 3 && nf != 5) return cudaErrorInvalidValue;
+  const long long ntiles = nx / 8, items = nf * (ntiles / 2), T = items * nz;
   const long long pairs = items < n_sm / 2 ? items : n_sm / 2;
   if (pairs < 1) return cudaErrorInvalidValue;
   const long long L = (T + pairs - 1) / pairs;  // >= nz: an item meets at most two pairs
@@ -1741,10 +1779,18 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<fl
                       8192 * sizeof(unsigned short) + 2 * 8;
   cudaError_t e = cudaFuncSetAttribute(k_yz_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, (int)ntiles,
+  k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles,
                                                      (int)L, (int)T, geo,
                                              (const float2*)twz, (const float2*)tw4, (float4*)part,
                                              err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bins5_from_part(const void* part, int nx, int ny, int nz, long long L,
+                                  const Geo<float>* geo, float dc, void* bins, cudaStream_t s) {
+  const long long npix = (long long)nx * ny;
+  k_bins5_from_part<<<grid1(npix, 256), 256, 0, s>>>((const float4*)part, nx, ny, nz, nx / 8,
+                                                     (int)L, geo, dc, (float2*)bins);
   return cudaGetLastError();
 }
 
@@ -1795,7 +1841,8 @@ cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long lo
 }
 
 template <typename R, int T, int EC>
-static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* twx, cudaStream_t s) {
+static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
+                                const void* src) {
   using C = typename RT<R>::C;
   size_t smem = padded(EC) * sizeof(C);
   int tw_in_smem = 0;
@@ -1806,14 +1853,16 @@ static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* tw
   auto kern = k_row_fft<R, T, EC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid1(nrows, EC / nx), T, smem, s>>>((C*)p, ilog2(nx), nrows, (const C*)twx, tw_in_smem);
+  kern<<<grid1(nrows, EC / nx), T, smem, s>>>((const C*)(src ? src : p), (C*)p, ilog2(nx), nrows,
+                                               (const C*)twx, tw_in_smem);
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s) {
-  if (nx <= 2048) return row_fft_impl<R, 256, 2048>(p, nx, nrows, twx, s);
-  return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s);
+cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
+                           const void* src) {
+  if (nx <= 2048) return row_fft_impl<R, 256, 2048>(p, nx, nrows, twx, s, src);
+  return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s, src);
 }
 
 template <typename R, int T, int EC, int LOGL>
@@ -1998,7 +2047,8 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
 #define RSX_INSTANTIATE(R)                                                                        \
   template cudaError_t launch_pol_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \
                                           void*, const void*, cudaStream_t, long long, long long);\
-  template cudaError_t launch_row_fft<R>(void*, int, long long, const void*, cudaStream_t);       \
+  template cudaError_t launch_row_fft<R>(void*, int, long long, const void*, cudaStream_t,         \
+                                         const void*);                                           \
   template cudaError_t launch_col_fft<R>(void*, int, long long, long long, const ColBatches&,     \
                                          const void*, cudaStream_t);                              \
   template cudaError_t launch_dft_z<R>(const void*, void*, int, int, int, const void*,            \

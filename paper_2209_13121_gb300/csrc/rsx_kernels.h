@@ -123,13 +123,18 @@ cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
 // The y-FFT fused with the pruned z transform (FP32): yz_fusable says
 // whether the shape qualifies (ny = 1024, nx a multiple of 16, nz a power
 // of two up to 1024).
-// launch_yz_tma writes the two q_z bins of every pixel and field into part
-// ([2 slots][3][ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
+// launch_yz_tma writes the two q_z bins of every pixel and of each of the nf
+// fields (3: p; 5: the linearity path's N_t entries) into part ([2 slots][nf]
+// [ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
 // the step count per block that launch_ewald_bins needs to add the slots.
 bool yz_fusable(int nx, int ny, int nz);
-cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, const Geo<float>* geo,
+cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, void* part, int* err, int n_sm,
                           long long* L_out, cudaStream_t s);
+// The linearity path's per-energy bins (k_zbins5 layout) from launch_yz_tma
+// run over the five FFT'd N_t entries (nf = 5); dc = -(c-1)/(4 pi) N.
+cudaError_t launch_bins5_from_part(const void* part, int nx, int ny, int nz, long long L,
+                                  const Geo<float>* geo, float dc, void* bins, cudaStream_t s);
 cudaError_t launch_ewald_bins(const void* part, int nx, int ny, int nz, long long L,
                               const Geo<float>* geo, float dc0, float dc1, float dc2, float* img,
                               cudaStream_t s);
@@ -141,7 +146,8 @@ cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long lo
                                  const ColBatches& bt, const void* tw4, int* err, int n_sm,
                                  cudaStream_t s);
 template <typename R>
-cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s);
+cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
+                           const void* src = nullptr);
 template <typename R>
 cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
                            const void* tw, cudaStream_t s);
