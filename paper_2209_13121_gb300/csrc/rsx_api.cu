@@ -377,7 +377,9 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
   if ((rc = ensure_nt<R>(c, ie, s))) return rc;
   {
     PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    RSX_CK(rsx::launch_row_fft<R>(c->ft, g.nx, 5LL * g.ny * g.nz, c->twx, s, c->nt),
+    RSX_CK(g.nx == 1024 && c->tw4
+               ? rsx::launch_row_fft4s<R>(c->ft, 5LL * g.ny * g.nz, c->tw4, s, c->nt)
+               : rsx::launch_row_fft<R>(c->ft, g.nx, 5LL * g.ny * g.nz, c->twx, s, c->nt),
            "x-FFT kernel");
   }
   const double dc = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
@@ -777,7 +779,9 @@ namespace {
 template <typename R>
 int fft3d_impl(rsx_context* c, void* p, cudaStream_t s) {
   const rsx_config& g = c->cfg;
-  RSX_CK(rsx::launch_row_fft<R>(p, g.nx, 3LL * g.ny * g.nz, c->twx, s), "x-FFT kernel");
+  RSX_CK(g.nx == 1024 && c->tw4 ? rsx::launch_row_fft4s<R>(p, 3LL * g.ny * g.nz, c->tw4, s)
+                                : rsx::launch_row_fft<R>(p, g.nx, 3LL * g.ny * g.nz, c->twx, s),
+         "x-FFT kernel");
   RSX_CK(rsx::launch_col_fft<R>(p, g.ny, g.nx, g.nx, {3LL * g.nz, g.nz, c->N, c->npix, 0}, c->twy, s),
          "y-FFT kernel");
   if (g.nz == 1) return RSX_OK;

@@ -669,6 +669,42 @@ __global__ void __launch_bounds__(256, 1) k_col_fft4s_tma(const __grid_constant_
   }
 }
 
+// Plain 1024-point row FFTs, one warp per row (four-step 32 x 32): lane n1
+// loads the samples n1 + 32 n2 straight from global memory (32 coalesced
+// loads in flight per lane), transforms over n2 in registers, twiddles,
+// transposes through a padded 32 x 33 shared tile, transforms over n1 and
+// stores X[k2 + 32 k1] (coalesced over k2).  src -> dst, may be in place.
+template <typename R, int W>
+__global__ void __launch_bounds__(32 * W) k_row_fft4s(const typename RT<R>::C* src,
+                                                      typename RT<R>::C* dst, long long nrows,
+                                                      const typename RT<R>::C* __restrict__ tw4_g) {
+  using C = typename RT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw4 = reinterpret_cast<C*>(smem_raw);  // [32][32]
+  C* F = tw4 + 1024 + (threadIdx.x >> 5) * (32 * 33);
+  for (int i = threadIdx.x; i < 1024; i += 32 * W) tw4[i] = tw4_g[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long row = (long long)blockIdx.x * W + (threadIdx.x >> 5);
+  if (row >= nrows) return;
+  const C* in = src + (size_t)row * 1024 + lane;
+  C v[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = in[32 * n2];
+  dft32(v);
+#pragma unroll
+  for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
+  __syncwarp();
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+  dft32(v);
+  C* out = dst + (size_t)row * 1024 + lane;
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+}
+
 // Plain row FFTs along x (no polarisation): the x pass of rsx_fft3d and of
 // the linearity path; rows are read from src and written to p (src = p for
 // in place).
@@ -1859,6 +1895,21 @@ static cudaError_t row_fft_impl(void* p, int nx, long long nrows, const void* tw
 }
 
 template <typename R>
+cudaError_t launch_row_fft4s(void* p, long long nrows, const void* tw4, cudaStream_t s,
+                             const void* src) {
+  using C = typename RT<R>::C;
+  constexpr int W = 8;
+  if (nrows <= 0) return cudaSuccess;
+  const size_t smem = (1024 + W * 32 * 33) * sizeof(C);
+  auto kern = k_row_fft4s<R, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid1(nrows, W), 32 * W, smem, s>>>((const C*)(src ? src : p), (C*)p, nrows,
+                                              (const C*)tw4);
+  return cudaGetLastError();
+}
+
+template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
                            const void* src) {
   if (nx <= 2048) return row_fft_impl<R, 256, 2048>(p, nx, nrows, twx, s, src);
@@ -2049,6 +2100,8 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                           void*, const void*, cudaStream_t, long long, long long);\
   template cudaError_t launch_row_fft<R>(void*, int, long long, const void*, cudaStream_t,         \
                                          const void*);                                           \
+  template cudaError_t launch_row_fft4s<R>(void*, long long, const void*, cudaStream_t,           \
+                                           const void*);                                         \
   template cudaError_t launch_col_fft<R>(void*, int, long long, long long, const ColBatches&,     \
                                          const void*, cudaStream_t);                              \
   template cudaError_t launch_dft_z<R>(const void*, void*, int, int, int, const void*,            \

@@ -148,6 +148,11 @@ cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long lo
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
                            const void* src = nullptr);
+// 1024-point row FFTs (four-step, one warp per row) from src (or p) to p;
+// tw4 the four-step twiddle table.
+template <typename R>
+cudaError_t launch_row_fft4s(void* p, long long nrows, const void* tw4, cudaStream_t s,
+                             const void* src = nullptr);
 template <typename R>
 cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
                            const void* tw, cudaStream_t s);

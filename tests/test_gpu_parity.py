@@ -145,7 +145,7 @@ def test_polarization_lab_frame(rsx, prec):
 
 # ------------------------------------------------------------------ row a4
 FFT_SHAPES = [(4, 8, 8), (5, 16, 32), (1, 64, 64), (3, 128, 16), (2, 1, 8), (1, 1, 1),
-              (7, 4, 2048), (16, 32, 32), (6, 2, 4)]
+              (7, 4, 2048), (16, 32, 32), (6, 2, 4), (3, 4, 1024), (2, 1024, 8)]
 
 
 @pytest.mark.parametrize("prec", [32, 64])
