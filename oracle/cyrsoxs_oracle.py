@@ -206,6 +206,78 @@ def ewald(pt: np.ndarray, E_eV: float, voxel_nm: float) -> np.ndarray:
     return np.where(valid, X, 0.0)
 
 
+def dft_sparse(vals: np.ndarray, iz, iy, ix, shape, kz, ky, kx) -> np.ndarray:
+    """The forward DFT (R9) by its definition, for a field that is zero
+    except at the voxels (iz, iy, ix):
+        p~(k) = sum_v p_v exp(-2 pi i (kz z_v / Nz + ky y_v / Ny + kx x_v / Nx)),
+    at the frequency indices (kz[m], ky[m], kx[m]).  vals: [3][K] complex.
+    Returns [3][P].  The integer products are reduced modulo N before the
+    division, so the phases stay exact for large grids."""
+    Nz, Ny, Nx = shape
+    kz, ky, kx = (np.asarray(a, dtype=np.int64) for a in (kz, ky, kx))
+    ph = (np.mod(np.outer(kz, iz), Nz) / Nz + np.mod(np.outer(ky, iy), Ny) / Ny
+          + np.mod(np.outer(kx, ix), Nx) / Nx)
+    return vals @ np.exp(-2j * math.pi * ph).T
+
+
+def ewald_pixels(bins_fn, E_eV: float, voxel_nm: float, shape, iy, ix) -> np.ndarray:
+    """Eqs. (3Dscatter) and (Ewald) at selected detector pixels (FFT-order
+    indices iy, ix): the geometry and interpolation of ewald(), with p~ at
+    the two q_z bins supplied by bins_fn(b, iy, ix) -> [3][P] complex."""
+    Nz, Ny, Nx = shape
+    iy, ix = np.asarray(iy), np.asarray(ix)
+    k = wavenumber(E_eV)
+    qx = q_axis(Nx, voxel_nm)[ix]
+    qy = q_axis(Ny, voxel_nm)[iy]
+    dqz = 2.0 * math.pi / (Nz * voxel_nm)
+    rad = k * k - qx * qx - qy * qy
+    valid = rad >= 0.0
+    qz = np.where(valid, -k + np.sqrt(np.where(valid, rad, 0.0)), 0.0)
+    t = qz / dqz
+    z0 = np.floor(t)
+    w = t - z0
+    b0 = np.mod(z0.astype(np.int64), Nz)
+    b1 = np.mod(z0.astype(np.int64) + 1, Nz)
+    kout = np.stack([qx, qy, k + qz])
+    kmag = np.sqrt((kout ** 2).sum(axis=0))
+    r = kout / kmag
+    X = np.zeros(iy.shape)
+    for b, wt in ((b0, 1.0 - w), (b1, w)):
+        v = bins_fn(b, iy, ix)                     # (3, P) complex
+        rv = (r * v).sum(axis=0)
+        Y = (kmag ** 2) * (v - r * rv)
+        X += wt * (np.abs(Y) ** 2).sum(axis=0)
+    return np.where(valid, X, 0.0)
+
+
+def scatter_sparse_pixels(sparse, shape, nt, E_eV, voxel_nm, alpha, iy, ix,
+                          uT_mode="literal") -> np.ndarray:
+    """scatter_one_angle at selected pixels (FFT-order iy, ix) for a
+    morphology that is vacuum (last component) except at sparse voxels
+    (synth.sparse_voxels): p is the vacuum value p_vac everywhere else, so by
+    linearity of the DFT p~(k) = DFT(p - p_vac)(k) + N p_vac [k = 0], and
+    the first term is a sum over the sparse voxels (dft_sparse)."""
+    iz_v, iy_v, ix_v, vals = sparse
+    c = vals.shape[0]
+    e = e_field(alpha)
+    p = polarization(vals[:, None, None, :, :], nt, e)[:, 0, 0, :]    # (3, K)
+    vac = np.zeros((c, 1, 1, 1, 4))
+    vac[-1, ..., 0] = 1.0
+    p_vac = polarization(vac, nt, e)[:, 0, 0, 0]                       # (3,)
+    if uT_mode == "literal":
+        p = rotate_back(p, alpha)
+        p_vac = rotate_back(p_vac, alpha)
+    dp = p - p_vac[:, None]
+    N = int(np.prod(shape))
+
+    def bins_fn(b, qy_i, qx_i):
+        out = dft_sparse(dp, iz_v, iy_v, ix_v, shape, b, qy_i, qx_i)
+        at0 = (np.asarray(b) == 0) & (np.asarray(qy_i) == 0) & (np.asarray(qx_i) == 0)
+        return out + np.outer(p_vac * N, at0)
+
+    return ewald_pixels(bins_fn, E_eV, voxel_nm, shape, iy, ix)
+
+
 def fftshift2(img: np.ndarray) -> np.ndarray:
     """Detector image in fftshift order: q = 0 at index (Ny//2, Nx//2)."""
     return np.fft.fftshift(img, axes=(0, 1))

@@ -212,3 +212,47 @@ def morphology_random_torch(shape, n_components: int, seed: int = 0, device="cud
     M[..., 2] = torch.rand((c, Nz, Ny, Nx), generator=g, device=device) * (2.0 * np.pi)
     M[..., 3] = torch.rand((c, Nz, Ny, Nx), generator=g, device=device) * np.pi
     return M
+
+
+def sparse_voxels(shape, n_components: int, n_voxels: int, seed: int = 0):
+    """A morphology that is vacuum (the last component, v = 1) everywhere
+    except at about n_voxels distinct random voxels, which hold a random mix
+    of all components (v a random partition of unity, s ~ U[0,1],
+    phi ~ U[0, 2 pi), theta ~ U[0, pi]).  Returns (iz, iy, ix, vals) with
+    vals [c][K][4] float64; dense forms: morphology_sparse(_torch)."""
+    g = rng(seed)
+    Nz, Ny, Nx = shape
+    flat = np.unique(g.integers(0, Nz * Ny * Nx, size=n_voxels))
+    iz, rem = np.divmod(flat, Ny * Nx)
+    iy, ix = np.divmod(rem, Nx)
+    K, c = flat.size, n_components
+    v = g.random((c, K)) ** 2
+    v /= v.sum(axis=0, keepdims=True)
+    vals = np.empty((c, K, 4))
+    vals[..., 0] = v
+    vals[..., 1] = g.random((c, K))
+    vals[..., 2] = g.random((c, K)) * (2.0 * np.pi)
+    vals[..., 3] = g.random((c, K)) * np.pi
+    return iz, iy, ix, vals
+
+
+def morphology_sparse(shape, n_components: int, sparse, dtype=np.float64) -> np.ndarray:
+    """Dense [c][Nz][Ny][Nx][4] form of sparse_voxels' output."""
+    iz, iy, ix, vals = sparse
+    M = np.zeros((n_components,) + tuple(shape) + (4,), dtype=dtype)
+    M[-1, ..., 0] = 1.0
+    M[:, iz, iy, ix, :] = vals
+    return M
+
+
+def morphology_sparse_torch(shape, n_components: int, sparse, device="cuda", dtype=None):
+    """Device-side dense form of sparse_voxels' output (for full-size grids)."""
+    import torch
+
+    dtype = dtype or torch.float32
+    iz, iy, ix, vals = sparse
+    M = torch.zeros((n_components,) + tuple(shape) + (4,), device=device, dtype=dtype)
+    M[-1, ..., 0] = 1.0
+    idx = [torch.as_tensor(a, device=device) for a in (iz, iy, ix)]
+    M[:, idx[0], idx[1], idx[2], :] = torch.as_tensor(vals, device=device, dtype=dtype)
+    return M

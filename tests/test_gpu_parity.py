@@ -431,6 +431,46 @@ def test_unvalidated_context_accepts_out_of_range_v_sum(rsx):
     assert_image_close(got, ref, 64, mask=_center_mask(8, 8, 2.5))
 
 
+# ------------------------------- full benchmark size (sampled pixels, exact)
+@pytest.mark.parametrize("algorithm", [1, 2])
+def test_full_size_sampled_pixels_match_oracle(rsx, algorithm):
+    """At the benchmark's size and launch configuration (1024 x 1024 x 128,
+    c = 4, FP32: the bulk-copy x pass and the fused y+z pass), a morphology
+    that is vacuum except at ~20000 random voxels: detector pixels of two
+    angles, sampled, against the oracle's sampled path (exact by linearity
+    of the DFT, pinned against the full path)."""
+    if torch.cuda.get_device_properties(0).total_memory < 40e9:
+        pytest.skip("needs ~20 GB of device memory")
+    shape, c, E = (128, 1024, 1024), 4, 285.0
+    nz, ny, nx = shape
+    sp = synth.sparse_voxels(shape, c, 20000, seed=19)
+    K = synth.optical_constants([E], c, seed=20)
+    dev = synth.morphology_sparse_torch(shape, c, sp)
+    g = np.random.default_rng(21)
+    iy = np.concatenate([[0, 0, 1, 5, ny - 1, 300], g.integers(0, ny, 120)])
+    ix = np.concatenate([[0, 1, 0, 7, 3, nx - 2], g.integers(0, nx, 120)])
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=32, algorithm=algorithm) as ctx:
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants([E], K)
+        img = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        for alpha in (0.0, 1.1):
+            ctx.scatter_angle(0, alpha, img)
+            full = img.cpu().numpy().astype(np.float64)
+            got = full[(iy + ny // 2) % ny, (ix + nx // 2) % nx]
+            ref = O.scatter_sparse_pixels(sp, shape, K[0], E, VOXEL, alpha, iy, ix)
+            center = (iy == 0) & (ix == 0)
+            np.testing.assert_allclose(got[center], ref[center], rtol=1e-5)
+            rest = ~center
+            scale = ref[rest].max()
+            rel = np.linalg.norm(got[rest] - ref[rest]) / np.linalg.norm(ref[rest])
+            assert rel < 1e-4, rel
+            big = rest & (ref > 1e-4 * scale)
+            assert big.sum() > 100
+            assert (np.abs(got - ref)[big] / ref[big]).max() < 2e-3
+    del dev
+    torch.cuda.empty_cache()
+
+
 # ------------------------------------------ full benchmark size (property)
 def test_full_size_z_uniform_reduces_to_film(rsx):
     """At 1024 x 1024 x 128, c = 4, FP32 (the benchmark's launch shape), a

@@ -551,3 +551,44 @@ def test_linearity_restatement_equals_algorithm1():
         a1 = O.run_alg1(M, K, E, 5.0, angles_deg=(0, 20, 180), uT_mode=mode)
         al = O.run_linear(M, K, E, 5.0, angles_deg=(0, 20, 180), uT_mode=mode)
         np.testing.assert_allclose(al, a1, rtol=1e-10, atol=1e-14 * a1.max())
+
+
+# ------------------------------------- sampled pixels of sparse morphologies
+def test_dft_sparse_is_the_dft():
+    g = np.random.default_rng(31)
+    shape = (5, 6, 8)
+    iz, iy, ix = (g.integers(0, n, 7) for n in shape)
+    vals = g.normal(size=(3, 7)) + 1j * g.normal(size=(3, 7))
+    dense = np.zeros((3,) + shape, complex)
+    np.add.at(dense, (slice(None), iz, iy, ix), vals)
+    ref = np.fft.fftn(dense, axes=(1, 2, 3))
+    kz, ky, kx = (g.integers(0, n, 11) for n in shape)
+    np.testing.assert_allclose(O.dft_sparse(vals, iz, iy, ix, shape, kz, ky, kx),
+                               ref[:, kz, ky, kx], rtol=0, atol=1e-12)
+
+
+def test_ewald_pixels_equals_ewald():
+    g = np.random.default_rng(32)
+    shape = (4, 8, 16)
+    pt = g.normal(size=(3,) + shape) + 1j * g.normal(size=(3,) + shape)
+    for E, dv in ((285.0, 5.0), (270.0, 2.0)):   # 2 nm: corners off the sphere
+        full = O.ewald(pt, E, dv)
+        iy, ix = np.meshgrid(np.arange(8), np.arange(16), indexing="ij")
+        got = O.ewald_pixels(lambda b, y, x: pt[:, b, y, x], E, dv, shape, iy.ravel(), ix.ravel())
+        np.testing.assert_allclose(got.reshape(8, 16), full, rtol=1e-13, atol=0)
+
+
+def test_sparse_pixels_equal_the_full_path():
+    """Linearity of the DFT: the sampled path for a vacuum-plus-sparse
+    morphology equals Algorithm 1's full image (both frames)."""
+    from paper_2209_13121_gb300 import synth
+    shape, c = (6, 16, 32), 3
+    sp = synth.sparse_voxels(shape, c, 40, seed=33)
+    M = synth.morphology_sparse(shape, c, sp)
+    K = synth.optical_constants([285.0], c, seed=34)
+    iy, ix = np.meshgrid(np.arange(16), np.arange(32), indexing="ij")
+    for mode in ("literal", "lab"):
+        full = O.scatter_one_angle(M, K[0], 285.0, 5.0, 0.7, uT_mode=mode)
+        got = O.scatter_sparse_pixels(sp, shape, K[0], 285.0, 5.0, 0.7, iy.ravel(), ix.ravel(),
+                                      uT_mode=mode).reshape(16, 32)
+        np.testing.assert_allclose(O.fftshift2(got), full, rtol=0, atol=1e-13 * full.max())
