@@ -78,10 +78,13 @@ typedef struct rsx_config {
 typedef struct rsx_context rsx_context;
 
 /* Create a context for one grid and material count.  Allocates the device
- * workspace: 3 N complex for p, two nx*ny Real images, FFT twiddle tables
- * and, for Algorithm 2, 6 N complex for N_t (Table 2).  *out receives the
- * handle.  Errors: RSX_ERR_INVALID (sizes, precision, algorithm),
- * RSX_ERR_OOM. */
+ * workspace: 3 N complex for p, two nx*ny Real images, per-pixel Ewald
+ * geometry, FFT twiddle tables, for Algorithms 2 and 3 the stored N_t entries
+ * (Table 2) and, for FP32 grids with ny = 1024, nx a multiple of 16 and nz a
+ * power of two up to 1024, the two q_z bins per pixel of the fused y-FFT +
+ * z pass (2 x 3 x 16 bytes per pixel; 2 x 5 x 16 for Algorithm 3).  *out
+ * receives the handle.  Errors: RSX_ERR_INVALID (sizes, precision,
+ * algorithm), RSX_ERR_OOM. */
 int rsx_create(const rsx_config* cfg, rsx_context** out);
 
 /* Free the context and all device memory it owns.  NULL is a no-op.  The
@@ -93,7 +96,8 @@ int rsx_destroy(rsx_context* ctx);
 const char* rsx_last_error(void);
 
 /* Device bytes rsx_create would allocate for cfg, morphology copy included
- * (Tables 1 and 2).  Returns 0 for an invalid cfg. */
+ * (Tables 1 and 2, plus the buffers listed under rsx_create).  Returns 0 for
+ * an invalid cfg. */
 size_t rsx_workspace_bytes(const rsx_config* cfg);
 
 /* Number of e-field angles in the inclusive list start:increment:end

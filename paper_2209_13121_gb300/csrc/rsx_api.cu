@@ -412,6 +412,42 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
   return RSX_OK;
 }
 
+// The x pass (polarisation fused with the x-FFT) into c->p: the bulk-copy
+// pipelines for FP32 with nx = 1024 (morphology or N_t), the four-step
+// kernel with plain loads for other nx = 1024 cases, the Stockham kernels
+// for other sizes.
+template <typename R>
+int x_pass(rsx_context* c, const PolParams<R>& pp, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
+  if constexpr (sizeof(R) == 4) {
+    if (g.nx == 1024 && c->n_sm > 0 && g.algorithm == 1 && ((uintptr_t)c->M & 15) == 0) {
+      RSX_CK(rsx::launch_pol_fft4s_tma(c->M, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err, c->n_sm,
+                                       s),
+             "polarisation + x-FFT kernel");
+      return RSX_OK;
+    }
+    if (g.nx == 1024 && c->n_sm > 0 && g.algorithm == 2) {
+      RSX_CK(rsx::launch_ntp_fft4s_tma(c->nt, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
+                                       c->n_sm, s),
+             "N_t polarisation + x-FFT kernel");
+      return RSX_OK;
+    }
+  }
+  if (g.nx == 1024) {
+    RSX_CK(rsx::launch_pol_fft4s<R>(c->M, g.algorithm == 2 ? c->nt : nullptr, g.nx, g.ny, g.nz, pp,
+                                    c->p, c->tw4, s),
+           "polarisation + x-FFT kernel");
+  } else if (g.algorithm == 2) {
+    RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+           "N_t polarisation + x-FFT kernel");
+  } else {
+    RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+           "polarisation + x-FFT kernel");
+  }
+  return RSX_OK;
+}
+
 template <typename R>
 int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t s) {
   const rsx_config& g = c->cfg;
@@ -426,36 +462,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     return RSX_OK;
   }
   if (g.algorithm == 2 && (rc = ensure_nt<R>(c, ie, s))) return rc;
-  const PolParams<R> pp = make_params<R>(c, ie, alpha, 0);
-  {
-    PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
-    bool done = false;
-    if constexpr (sizeof(R) == 4) {
-      if (g.nx == 1024 && g.algorithm == 1 && c->n_sm > 0 && ((uintptr_t)c->M & 15) == 0) {
-        RSX_CK(rsx::launch_pol_fft4s_tma(c->M, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
-                                         c->n_sm, s),
-               "polarisation + x-FFT kernel");
-        done = true;
-      } else if (g.nx == 1024 && g.algorithm == 2 && c->n_sm > 0) {
-        RSX_CK(rsx::launch_ntp_fft4s_tma(c->nt, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
-                                         c->n_sm, s),
-               "N_t polarisation + x-FFT kernel");
-        done = true;
-      }
-    }
-    if (done) {
-    } else if (g.nx == 1024) {
-      RSX_CK(rsx::launch_pol_fft4s<R>(c->M, g.algorithm == 2 ? c->nt : nullptr, g.nx, g.ny, g.nz,
-                                      pp, c->p, c->tw4, s),
-             "polarisation + x-FFT kernel");
-    } else if (g.algorithm == 2) {
-      RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
-             "N_t polarisation + x-FFT kernel");
-    } else {
-      RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
-             "polarisation + x-FFT kernel");
-    }
-  }
+  if ((rc = x_pass<R>(c, make_params<R>(c, ie, alpha, 0), s))) return rc;
   // The constant -(c-1) e' / (4 pi) left out of p before the FFT returns at
   // q = 0 as N times itself (e' = x-hat in the literal frame, e otherwise).
   const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
