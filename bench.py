@@ -44,6 +44,9 @@ METRIC = "P-RSoXS voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s
 UNIT = "Gvoxel-angle/s"
 
 
+FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64, nominal (no measured FP64 peak is available)
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -223,6 +226,24 @@ def run_ours(args):
         bytes_per_voxel = per_voxel[top]
         achieved = (bytes_per_voxel * N * n_l) / (t_ms / 1e3) / 1e9 if n_l else None
     traffic = _traffic_from_profiles(args.workload, top, prec) if args.algorithm == 1 else None
+    roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
+                "peak_kind": peak_kind, "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                "alg_bytes_per_voxel": bytes_per_voxel,
+                "launch_ms": t_ms / n_l if n_l else None}
+    if prec == 64 and args.algorithm == 1:
+        # FP64 runs on the FP64 units (a small fraction of the FP32 rate on
+        # GB300): the x pass is bound by FP64 arithmetic, reported against
+        # the nominal FP64 rate.  Algorithmic flops per voxel: 41 per
+        # component (Eq. (polarization) in the closed form, sincos not
+        # counted), 22 for p, 100 for the x-FFT of three fields.
+        t_ms, n_l = phases["pol_fftx"]
+        flops = 41 * c + 22 + 100
+        ach = flops * N * n_l / (t_ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "kernel": "pol_fftx", "achieved": ach,
+                    "peak": FP64_NOMINAL_TFLOPS, "peak_kind": "nominal FP64",
+                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "alg_flops_per_voxel": flops, "launch_ms": t_ms / n_l}
 
     # end to end through the public API: host morphology in, host image out.
     # Two contexts on two streams: the next energy's morphology upload
@@ -296,12 +317,7 @@ def run_ours(args):
                        "voxels": N, "components": c, "angles_per_energy": n_ang,
                        "precision": prec, "parallelism": f"energy-sharded x{ws}",
                        "l2": f"inputs larger than L2 (morphology {N * c * 4 * real / 1e9:.1f} GB)"},
-            "roofline": {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
-                         "peak_kind": peak_kind, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None,
-                         "traffic": traffic,
-                         "alg_bytes_per_voxel": bytes_per_voxel,
-                         "launch_ms": t_ms / n_l if n_l else None},
+            "roofline": roofline,
             "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
             "gpu_launches": int(sum(v[1] for v in phases.values())),
             "clocks": clk,
