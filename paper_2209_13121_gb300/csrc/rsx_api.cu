@@ -139,6 +139,8 @@ struct rsx_context {
   // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
   // [2 slots][3][ny][nx] float4
   void* part = nullptr;
+  // linearity path: the images of a batch of angles ([kMaxAngleBatch][ny][nx])
+  void* imgs = nullptr;
   int n_sm = 0;
   int* flag = nullptr;
   int* err = nullptr;  // set by a kernel whose bounded wait timed out
@@ -156,7 +158,7 @@ namespace {
 
 void free_all(rsx_context* c) {
   void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,  c->twx,
-                  c->twy,     c->twz, c->tw4, c->flag, c->err, c->part};
+                  c->twy,     c->twz, c->tw4, c->flag, c->err, c->part, c->imgs};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -560,6 +562,7 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
   b += (size_t)npix * geo_size(cfg->precision);
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
   if (uses_yz(cfg)) b += part_bytes(cfg);  // bins of the fused y + z pass
+  if (cfg->algorithm == 3) b += (size_t)rsx::kMaxAngleBatch * npix * R;  // a batch of images
   return b;
 }
 
@@ -649,6 +652,13 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     if (c->ft) c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft);
     if (c->ft)
       c->has_tmap_ftz = make_tmap(c, c->ft, 5, &c->tmap_ftz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+  }
+  if (cfg->algorithm == 3 &&
+      (e = cudaMalloc(&c->imgs, (size_t)rsx::kMaxAngleBatch * c->npix * R)) != cudaSuccess) {
+    rc = cuda_fail(e, "linearity path images");
+    free_all(c);
+    delete c;
+    return rc;
   }
   if (uses_yz(cfg) && (e = cudaMalloc(&c->part, part_bytes(cfg))) != cudaSuccess) {
     rc = cuda_fail(e, "y + z pass bins");
@@ -864,6 +874,51 @@ int rsx_scatter_angle(rsx_context* c, int ie, double alpha, void* img, void* str
 }
 
 namespace {
+// All angles of one energy, one after the other: the image of each angle
+// (scatter_angle), rotated into the average.
+template <typename R>
+int run_energy_angles(rsx_context* c, int ie, double start, double inc, int nang, int rotation,
+                      cudaStream_t s) {
+  for (int a = 0; a < nang; ++a) {
+    const double alpha = rotation ? (start + inc * a) * (kPi / 180.0) : 0.0;
+    int rc = scatter_angle<R>(c, ie, alpha, c->img, s);
+    if (rc) return rc;
+    PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
+    RSX_CK(rsx::launch_rotate_acc<R>(c->img, c->acc, c->cfg.nx, c->cfg.ny, alpha, rotation != 0, s),
+           "rotation kernel");
+  }
+  return RSX_OK;
+}
+
+// All angles of one energy on the linearity path, kMaxAngleBatch at a time:
+// the images of a batch in one launch, then one rotate-and-accumulate
+// launch over the batch (the same sums in the same order as one launch per
+// angle).
+template <typename R>
+int run_energy_linear(rsx_context* c, int ie, double start, double inc, int nang, int rotation,
+                      cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  int rc = ensure_geo<R>(c, ie, s);
+  if (rc) return rc;
+  if ((rc = ensure_bins<R>(c, ie, s))) return rc;
+  for (int a0 = 0; a0 < nang; a0 += rsx::kMaxAngleBatch) {
+    rsx::AngleBatch<R> ab;
+    memset(&ab, 0, sizeof(ab));
+    for (int a = a0; a < nang && a < a0 + rsx::kMaxAngleBatch; ++a)
+      rsx::add_angle(ab, rotation ? (start + inc * a) * (kPi / 180.0) : 0.0, g.nx, g.ny);
+    {
+      PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+      RSX_CK(rsx::launch_ewald_linear_many<R>(c->bins5, g.nx, g.ny, (const Geo<R>*)c->geo, ab,
+                                              g.frame == RSX_FRAME_LITERAL, c->imgs, s),
+             "Ewald kernel");
+    }
+    PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
+    RSX_CK(rsx::launch_rotate_acc_many<R>(c->imgs, c->acc, g.nx, g.ny, ab, rotation != 0, s),
+           "rotation kernel");
+  }
+  return RSX_OK;
+}
+
 template <typename R>
 int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
              const std::vector<int>& sel, void* out, int where, cudaStream_t s) {
@@ -871,15 +926,10 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
   for (size_t o = 0; o < sel.size(); ++o) {
     const int ie = sel[o];
     RSX_CK(cudaMemsetAsync(c->acc, 0, img_bytes, s), "clear average");
-    for (int a = 0; a < nang; ++a) {
-      const double alpha = rotation ? (start + inc * a) * (kPi / 180.0) : 0.0;
-      int rc = scatter_angle<R>(c, ie, alpha, c->img, s);
-      if (rc) return rc;
-      PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
-      RSX_CK(rsx::launch_rotate_acc<R>(c->img, c->acc, c->cfg.nx, c->cfg.ny, alpha, rotation != 0,
-                                       s),
-             "rotation kernel");
-    }
+    const int rc = c->cfg.algorithm == 3 && c->imgs
+                       ? run_energy_linear<R>(c, ie, start, inc, nang, rotation, s)
+                       : run_energy_angles<R>(c, ie, start, inc, nang, rotation, s);
+    if (rc) return rc;
     const double inv = 1.0 / nang;  // Ewald_Avg[i] / numRotation (Algorithm 1)
     PhaseTimer pt(c, RSX_PHASE_OTHER, s);
     if (where == RSX_DEVICE) {

@@ -1467,21 +1467,14 @@ __global__ void __launch_bounds__(256) k_bins5_from_part(const float4* __restric
   }
 }
 
+// Detector value of one pixel for e = (ce, se, 0) from the linearity
+// bins (Eq. (Ewald) with p~ = N_t~ e per bin; zero off the sphere).
 template <typename R>
-__global__ void __launch_bounds__(256) k_ewald_linear(const typename RT<R>::C* __restrict__ bins, int nx,
-                                                      int ny, const Geo<R>* __restrict__ geo, R ce,
-                                                      R se, int literal, R* __restrict__ img) {
+__device__ __forceinline__ R linear_pixel(const typename RT<R>::C* __restrict__ bins, long long npix,
+                                          long long pix, const Geo<R>& g, R ce, R se,
+                                          int literal) {
   using C = typename RT<R>::C;
-  const long long npix = (long long)nx * ny;
-  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pix >= npix) return;
-  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
-  R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
-  const Geo<R> g = geo[pix];
-  if (g.b0 < 0) {
-    *dst = R(0);
-    return;
-  }
+  if (g.b0 < 0) return R(0);
   C pb[2][3];
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
@@ -1501,7 +1494,35 @@ __global__ void __launch_bounds__(256) k_ewald_linear(const typename RT<R>::C* _
     }
     pb[b][2] = pz;
   }
-  *dst = ewald_value<R>(g, pb[0], pb[1]);
+  return ewald_value<R>(g, pb[0], pb[1]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_ewald_linear(const typename RT<R>::C* __restrict__ bins, int nx,
+                                                      int ny, const Geo<R>* __restrict__ geo, R ce,
+                                                      R se, int literal, R* __restrict__ img) {
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
+  img[(size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1))] =
+      linear_pixel<R>(bins, npix, pix, geo[pix], ce, se, literal);
+}
+
+// The same for a batch of angles: imgs[a] for a = blockIdx.y.
+template <typename R>
+__global__ void __launch_bounds__(256) k_ewald_linear_many(const typename RT<R>::C* __restrict__ bins,
+                                                           int nx, int ny,
+                                                           const Geo<R>* __restrict__ geo,
+                                                           AngleBatch<R> ab, int literal,
+                                                           R* __restrict__ imgs) {
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const int a = blockIdx.y;
+  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);
+  imgs[(size_t)a * npix + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1))] =
+      linear_pixel<R>(bins, npix, pix, geo[pix], ab.ce[a], ab.se[a], literal);
 }
 
 // ------------------------------------------------ Algorithm 3 (NrComputation)
@@ -1608,20 +1629,13 @@ __global__ void k_nt_restore(const typename RT<R>::C* __restrict__ nt, typename 
 // stays below 2^60 for n <= 4096.  The floor is a shift and the fraction a
 // mask (no FP64 arithmetic).
 constexpr int kRotTile = 16;
+// Bilinear sample of img (fftshift order) at U(alpha) Q for the output
+// pixel (ix, iy); the coefficients are cos/sin (with the aspect ratios) in
+// 2^-48 fixed point, so the source position is exact to 2^-49 pixel.
 template <typename R>
-__global__ void __launch_bounds__(kRotTile * kRotTile) k_rotate_acc(const R* __restrict__ img,
-                                                                    R* __restrict__ acc, int nx,
-                                                                    int ny, long long cxx,
-                                                                    long long cxy, long long cyx,
-                                                                    long long cyy, int rotate) {
-  const int ix = blockIdx.x * kRotTile + threadIdx.x;
-  const int iy = blockIdx.y * kRotTile + threadIdx.y;
-  if (ix >= nx || iy >= ny) return;
-  const size_t pix = (size_t)iy * nx + ix;
-  if (!rotate) {
-    acc[pix] += img[pix];
-    return;
-  }
+__device__ __forceinline__ R rotated_sample(const R* __restrict__ img, int nx, int ny, int ix,
+                                            int iy, long long cxx, long long cxy, long long cyx,
+                                            long long cyy) {
   const int cx = nx / 2, cy = ny / 2;
   const long long dx = ix - cx, dy = iy - cy;
   const long long fx = ((long long)cx << 48) + cxx * dx - cxy * dy;
@@ -1644,7 +1658,42 @@ __global__ void __launch_bounds__(kRotTile * kRotTile) k_rotate_acc(const R* __r
       val += wy * wx * __ldg(img + (size_t)yy * nx + xx);
     }
   }
-  acc[pix] += val;
+  return val;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRotTile * kRotTile) k_rotate_acc(const R* __restrict__ img,
+                                                                    R* __restrict__ acc, int nx,
+                                                                    int ny, long long cxx,
+                                                                    long long cxy, long long cyx,
+                                                                    long long cyy, int rotate) {
+  const int ix = blockIdx.x * kRotTile + threadIdx.x;
+  const int iy = blockIdx.y * kRotTile + threadIdx.y;
+  if (ix >= nx || iy >= ny) return;
+  const size_t pix = (size_t)iy * nx + ix;
+  acc[pix] += rotate ? rotated_sample<R>(img, nx, ny, ix, iy, cxx, cxy, cyx, cyy) : img[pix];
+}
+
+// A batch of angles at once: acc += sample of imgs[0], then imgs[1], ...,
+// in that order (the same sums as one k_rotate_acc launch per angle).
+template <typename R>
+__global__ void __launch_bounds__(kRotTile * kRotTile) k_rotate_acc_many(const R* __restrict__ imgs,
+                                                                         R* __restrict__ acc,
+                                                                         int nx, int ny,
+                                                                         AngleBatch<R> ab,
+                                                                         int rotate) {
+  const int ix = blockIdx.x * kRotTile + threadIdx.x;
+  const int iy = blockIdx.y * kRotTile + threadIdx.y;
+  if (ix >= nx || iy >= ny) return;
+  const size_t npix = (size_t)nx * ny, pix = (size_t)iy * nx + ix;
+  R sum = acc[pix];
+  for (int a = 0; a < ab.n; ++a) {
+    const R* img = imgs + (size_t)a * npix;
+    sum += rotate ? rotated_sample<R>(img, nx, ny, ix, iy, ab.cxx[a], ab.cxy[a], ab.cyx[a],
+                                      ab.cyy[a])
+                  : img[pix];
+  }
+  acc[pix] = sum;
 }
 
 template <typename R>
@@ -2068,17 +2117,37 @@ cudaError_t launch_nt_restore(const void* nt, void* out, long long N, double ref
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s) {
-  // fixed-point (2^-48) coefficients of the map Q -> U(alpha) Q in pixel
-  // units: fx = cx + cos a dx - sin a (nx/ny) dy, fy = cy + sin a (ny/nx) dx + cos a dy
-  const double two48 = 281474976710656.0;
-  const double ca = cos(alpha), sa = sin(alpha);
-  const long long cxx = llround(ca * two48), cyy = cxx;
-  const long long cxy = llround(sa * ((double)nx / ny) * two48);
-  const long long cyx = llround(sa * ((double)ny / nx) * two48);
+  long long c[4];
+  rotation_coeffs(alpha, nx, ny, c);
   const dim3 block(kRotTile, kRotTile);
   const dim3 grid((nx + kRotTile - 1) / kRotTile, (ny + kRotTile - 1) / kRotTile);
-  k_rotate_acc<R><<<grid, block, 0, s>>>((const R*)img, (R*)acc, nx, ny, cxx, cxy, cyx, cyy,
+  k_rotate_acc<R><<<grid, block, 0, s>>>((const R*)img, (R*)acc, nx, ny, c[0], c[1], c[2], c[3],
                                           rotate ? 1 : 0);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_ewald_linear_many(const void* bins, int nx, int ny, const Geo<R>* geo,
+                                     const AngleBatch<R>& ab, bool literal, void* imgs,
+                                     cudaStream_t s) {
+  if (ab.n <= 0) return cudaSuccess;
+  if (ab.n > kMaxAngleBatch) return cudaErrorInvalidValue;
+  const long long npix = (long long)nx * ny;
+  const dim3 grid(grid1(npix, 256), ab.n);
+  k_ewald_linear_many<R><<<grid, 256, 0, s>>>((const typename RT<R>::C*)bins, nx, ny, geo, ab,
+                                              literal ? 1 : 0, (R*)imgs);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_rotate_acc_many(const void* imgs, void* acc, int nx, int ny,
+                                   const AngleBatch<R>& ab, bool rotate, cudaStream_t s) {
+  if (ab.n <= 0) return cudaSuccess;
+  if (ab.n > kMaxAngleBatch) return cudaErrorInvalidValue;
+  const dim3 block(kRotTile, kRotTile);
+  const dim3 grid((nx + kRotTile - 1) / kRotTile, (ny + kRotTile - 1) / kRotTile);
+  k_rotate_acc_many<R><<<grid, block, 0, s>>>((const R*)imgs, (R*)acc, nx, ny, ab,
+                                               rotate ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -2111,6 +2180,11 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                        bool, const R*, void*, cudaStream_t, int*);                \
   template cudaError_t launch_rotate_acc<R>(const void*, void*, int, int, double, bool,           \
                                             cudaStream_t);                                        \
+  template cudaError_t launch_ewald_linear_many<R>(const void*, int, int, const Geo<R>*,          \
+                                                   const AngleBatch<R>&, bool, void*,            \
+                                                   cudaStream_t);                                 \
+  template cudaError_t launch_rotate_acc_many<R>(const void*, void*, int, int,                    \
+                                                 const AngleBatch<R>&, bool, cudaStream_t);      \
   template cudaError_t launch_scale<R>(const void*, void*, long long, double, cudaStream_t);      \
   template cudaError_t launch_validate<R>(const void*, long long, int*, cudaStream_t);          \
   template cudaError_t launch_ntp_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \

@@ -1,6 +1,8 @@
 // Internal (C++) interface between the C ABI layer and the CUDA kernels.
 #pragma once
 
+#include <math.h>
+
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -28,6 +30,39 @@ template <typename R> struct PolParams {
   int literal;  // 1: p <- U^T p (RSX_FRAME_LITERAL), 0: lab frame
   int add_ref;  // 1: output full p; 0: p minus the constant -(c-1) e'/(4 pi)
 };
+
+// A batch of e-field angles for the linearity path's per-angle passes:
+// cos, sin of alpha and the detector rotation's fixed-point coefficients
+// (2^-48) of Q -> U(alpha) Q in pixel units.
+constexpr int kMaxAngleBatch = 64;
+template <typename R> struct AngleBatch {
+  int n;
+  R ce[kMaxAngleBatch], se[kMaxAngleBatch];
+  long long cxx[kMaxAngleBatch], cxy[kMaxAngleBatch], cyx[kMaxAngleBatch], cyy[kMaxAngleBatch];
+};
+
+// fx = cx + cos a dx - sin a (nx/ny) dy, fy = cy + sin a (ny/nx) dx + cos a dy
+inline void rotation_coeffs(double alpha, int nx, int ny, long long c[4]) {
+  const double two48 = 281474976710656.0;
+  const double ca = cos(alpha), sa = sin(alpha);
+  c[0] = llround(ca * two48);
+  c[1] = llround(sa * ((double)nx / ny) * two48);
+  c[2] = llround(sa * ((double)ny / nx) * two48);
+  c[3] = c[0];
+}
+
+template <typename R>
+inline void add_angle(AngleBatch<R>& ab, double alpha, int nx, int ny) {
+  long long c[4];
+  rotation_coeffs(alpha, nx, ny, c);
+  const int a = ab.n++;
+  ab.ce[a] = (R)cos(alpha);
+  ab.se[a] = (R)sin(alpha);
+  ab.cxx[a] = c[0];
+  ab.cxy[a] = c[1];
+  ab.cyx[a] = c[2];
+  ab.cyy[a] = c[3];
+}
 
 // Component j of pp from tau = (eps_par + 2 eps_perp)/3, dperp = eps_perp -
 // tau and dpar = eps_par - eps_perp (complex, eps = n - 1), in FP64.
@@ -169,6 +204,17 @@ template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
                          const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s,
                          int* err = nullptr);
+// The linearity path's per-angle passes for a batch of angles: images of
+// every angle into imgs ([ab.n][ny][nx], fftshift order), then one
+// rotate-and-accumulate pass over all of them (same sums, same order as one
+// launch per angle).
+template <typename R>
+cudaError_t launch_ewald_linear_many(const void* bins, int nx, int ny, const Geo<R>* geo,
+                                     const AngleBatch<R>& ab, bool literal, void* imgs,
+                                     cudaStream_t s);
+template <typename R>
+cudaError_t launch_rotate_acc_many(const void* imgs, void* acc, int nx, int ny,
+                                   const AngleBatch<R>& ab, bool rotate, cudaStream_t s);
 template <typename R>
 cudaError_t launch_rotate_acc(const void* img, void* acc, int nx, int ny, double alpha,
                               bool rotate, cudaStream_t s);

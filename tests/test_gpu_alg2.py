@@ -200,3 +200,30 @@ def test_linear_path_host_streamed_and_energy_subsets(rsx):
     np.testing.assert_array_equal(part, full[[4, 1]])
     ref = O.run_linear(M, K, E, VOXEL, angles_deg=(0, 10, 180), energy_indices=[0, 3])
     _close_img(full[[0, 3]], ref, 32)
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+def test_linear_path_batched_angles_equal_angle_by_angle(rsx, prec):
+    """The linearity path's run computes its angles in batches (images of a
+    batch, then one rotate-and-accumulate pass); the step entry points one
+    angle at a time must give the same average bit for bit, across more
+    angles than one batch holds."""
+    shape, c = (3, 32, 64), 3
+    nz, ny, nx = shape
+    M = synth.morphology_random(shape, c, seed=65, dtype=_real(prec))
+    K = synth.optical_constants(ENERGIES, c, seed=66)
+    start, inc, end = 0.0, 2.0, 180.0   # 91 angles
+    n = rsx.angle_count(start, inc, end)
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=prec, algorithm=3) as ctx:
+        ctx.set_morphology(torch.from_numpy(M).cuda())
+        ctx.set_optical_constants(ENERGIES, K)
+        got = ctx.run((start, inc, end), energy_indices=[1])
+        img = torch.empty((ny, nx), dtype=_tdt(prec), device="cuda")
+        acc = torch.zeros((ny, nx), dtype=_tdt(prec), device="cuda")
+        for a in range(n):
+            alpha = np.deg2rad(start + inc * a)
+            ctx.scatter_angle(1, alpha, img)
+            ctx.rotate_accumulate(img, alpha, acc)
+        ref = (acc * (1.0 / n)).cpu().numpy()
+    np.testing.assert_array_equal(got[0], ref)
+
