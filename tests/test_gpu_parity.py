@@ -236,9 +236,10 @@ def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
 # items: x rows (nx = 1024: groups of two rows and an odd tail) and y tiles
 # (ny = 1024: both input buffers refilled more than once); the fused y+z
 # pass at its edges: nz = 1 (both q_z bins are plane 0), the narrowest
-# width (one tile pair), a field split between two block pairs.
+# width (one tile pair), a field split between two block pairs, a 2048-wide
+# grid (Stockham x pass feeding the fused y+z pass).
 MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2), ((1, 1024, 64), 3), ((4, 1024, 16), 2),
-         ((2, 1024, 512), 2)]
+         ((2, 1024, 512), 2), ((1, 1024, 2048), 2)]
 
 
 @pytest.mark.parametrize("shape,c", MULTI, ids=["x".join(map(str, s)) for s, _ in MULTI])
