@@ -158,6 +158,17 @@ int rsx_run(rsx_context* ctx, double start_deg, double increment_deg, double end
  * two CUDA events on its stream (a few microseconds each); 0 stops that. */
 int rsx_set_timing(rsx_context* ctx, int enable);
 
+/* Failure-path hook (no counterpart in the paper).  The pipelined kernels
+ * wait for their bulk copies on mbarriers with a bounded number of polls;
+ * when a wait runs out the kernel records the fact, lets the copies it has
+ * in flight land (always with the default bound), and returns, and the next
+ * rsx_run with host output fails with RSX_ERR_CUDA ("a kernel pipeline wait
+ * timed out").  This sets the bound of those waits for the context's later
+ * launches: polls < 0 restores the default (2^22); 0 makes every such wait
+ * run out at once, so the failure path can be exercised without any fault.
+ * Values above 2^32 - 1 are clamped.  The context stays usable afterwards. */
+int rsx_set_wait_limit(rsx_context* ctx, long long polls);
+
 /* Waits for the recorded events, writes the summed device time of each
  * phase in ms to ms[RSX_N_PHASES] and the number of kernel launches to
  * launches[RSX_N_PHASES] (either may be NULL), then clears the record. */

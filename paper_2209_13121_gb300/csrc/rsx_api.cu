@@ -142,6 +142,7 @@ struct rsx_context {
   // linearity path: the images of a batch of angles ([kMaxAngleBatch][ny][nx])
   void* imgs = nullptr;
   int n_sm = 0;
+  unsigned wait_polls = rsx::kWaitPolls;  // bound of the pipelined kernels' waits
   int* flag = nullptr;
   int* err = nullptr;  // set by a kernel whose bounded wait timed out
   // per-phase timing: event pairs recorded around launches while enabled
@@ -268,7 +269,8 @@ cudaError_t launch_y_fft(rsx_context* c, void* data, long long ncomp, cudaStream
                           : data == c->ft && c->has_tmap_ft ? &c->tmap_ft
                                                              : nullptr;
   if (sizeof(R) == 4 && tm)
-    return rsx::launch_col_fft4s_tma(tm, data, g.nx, g.nx, bt, c->tw4, c->err, c->n_sm, s);
+    return rsx::launch_col_fft4s_tma(tm, data, g.nx, g.nx, bt, c->tw4, c->err, c->n_sm,
+                                     c->wait_polls, s);
   if (g.ny == 1024 && g.nx % 8 == 0 && c->tw4)
     return rsx::launch_col_fft4s<R>(data, g.nx, g.nx, bt, c->tw4, s);
   return rsx::launch_col_fft<R>(data, g.ny, g.nx, g.nx, bt, c->twy, s);
@@ -391,7 +393,7 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
         RSX_CK(rsx::launch_yz_tma(&c->tmap_ftz, g.nx, g.ny, g.nz, 5, (const Geo<float>*)c->geo,
-                                  c->twz, c->tw4, c->part, c->err, c->n_sm, &L, s),
+                                  c->twz, c->tw4, c->part, c->err, c->n_sm, c->wait_polls, &L, s),
                "y-FFT + z-bins kernel");
       }
       PhaseTimer pt(c, RSX_PHASE_EWALD, s);
@@ -425,13 +427,13 @@ int x_pass(rsx_context* c, const PolParams<R>& pp, cudaStream_t s) {
   if constexpr (sizeof(R) == 4) {
     if (g.nx == 1024 && c->n_sm > 0 && g.algorithm == 1 && ((uintptr_t)c->M & 15) == 0) {
       RSX_CK(rsx::launch_pol_fft4s_tma(c->M, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err, c->n_sm,
-                                       s),
+                                       c->wait_polls, s),
              "polarisation + x-FFT kernel");
       return RSX_OK;
     }
     if (g.nx == 1024 && c->n_sm > 0 && g.algorithm == 2) {
       RSX_CK(rsx::launch_ntp_fft4s_tma(c->nt, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
-                                       c->n_sm, s),
+                                       c->n_sm, c->wait_polls, s),
              "N_t polarisation + x-FFT kernel");
       return RSX_OK;
     }
@@ -480,7 +482,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
         RSX_CK(rsx::launch_yz_tma(&c->tmap_pz, g.nx, g.ny, g.nz, 3, (const Geo<float>*)c->geo,
-                                  c->twz, c->tw4, c->part, c->err, c->n_sm, &L, s),
+                                  c->twz, c->tw4, c->part, c->err, c->n_sm, c->wait_polls, &L, s),
                "y-FFT + z-bins kernel");
       }
       PhaseTimer pt(c, RSX_PHASE_EWALD, s);
@@ -496,7 +498,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
   }
   PhaseTimer pt(c, RSX_PHASE_EWALD, s);
   RSX_CK(rsx::launch_ewald<R>(c->p, g.nx, g.ny, g.nz, (const Geo<R>*)c->geo, c->twz, true, dc, img,
-                              s, c->err),
+                              s, c->err, c->wait_polls),
          "Ewald kernel");
   return RSX_OK;
 }
@@ -948,6 +950,8 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
     RSX_CK(cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost), "kernel error flag");
     if (h) {
       cudaMemset(c->err, 0, sizeof(int));
+      c->nt_energy = -1;  // per-energy data computed by an aborted kernel is not kept
+      c->bins_energy = -1;
       return fail(RSX_ERR_CUDA, "a kernel pipeline wait timed out; the result is not valid");
     }
   }
@@ -978,6 +982,13 @@ int rsx_nt(rsx_context* c, int ie, void* nt_out, void* stream) {
 int rsx_set_timing(rsx_context* c, int enable) {
   if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
   c->timing = enable != 0;
+  return RSX_OK;
+}
+
+int rsx_set_wait_limit(rsx_context* c, long long polls) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  c->wait_polls = polls < 0 ? rsx::kWaitPolls
+                            : polls > 0xffffffffLL ? 0xffffffffu : (unsigned)polls;
   return RSX_OK;
 }
 

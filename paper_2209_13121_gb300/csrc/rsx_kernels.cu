@@ -368,7 +368,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
 template <int S, int NP, int PW, int FG, bool NT>
 __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
     const void* __restrict__ src, long long N, long long nrows, PolParams<float> pp,
-    float2* __restrict__ p, const float2* __restrict__ tw4_g, int* __restrict__ err) {
+    float2* __restrict__ p, const float2* __restrict__ tw4_g, int* __restrict__ err,
+    unsigned poll) {
   using C = float2;
   using SrcT = typename std::conditional<NT, float2, float4>::type;
   constexpr int NX = 1024, TP = 32 * PW, SL = NX / TP, FS = 32 * 33, NB = TP + 96;
@@ -405,7 +406,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
     int g = 0, slot = 0, k = 0, j = 0;
     long long row = blockIdx.x;
     for (; g < G; ++g) {
-      if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), kPoll)) {
+      if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), poll)) {
         atomicOr(err, 1);
         *abort_flag = 1;
         break;
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
         failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
         if (failed) break;
         // warp-uniform: a lane that gave up makes its whole warp give up
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, kPoll))) {
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, poll))) {
           failed = true;
           atomicOr(err, 1);
           *abort_flag = 1;
@@ -603,7 +604,7 @@ __global__ void __launch_bounds__(256, 1) k_col_fft4s_tma(const __grid_constant_
                                                           long long total, long long bdiv,
                                                           long long stride_hi, long long stride_lo,
                                                           const typename RT<R>::C* __restrict__ tw4_g,
-                                                          int* __restrict__ err) {
+                                                          int* __restrict__ err, unsigned poll) {
   using C = typename RT<R>::C;
   constexpr int TX = 8, T = 256, STR = 33 * TX, TILE = 1024 * TX;
   constexpr unsigned kPoll = 1u << 22;
@@ -634,7 +635,7 @@ __global__ void __launch_bounds__(256, 1) k_col_fft4s_tma(const __grid_constant_
   int i = 0;
   for (long long tid = blockIdx.x; tid < total; tid += gridDim.x, ++i) {
     const int b = i & 1;
-    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kPoll);
+    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, poll);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicOr(err, 1);
@@ -1041,7 +1042,8 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
                                                    const Geo<float>* __restrict__ geo,
                                                    const float2* __restrict__ twz_g,
                                                    const float2* __restrict__ tw4_g,
-                                                   float4* __restrict__ part, int* __restrict__ err) {
+                                                   float4* __restrict__ part, int* __restrict__ err,
+                                                   unsigned poll) {
   using C = float2;
   constexpr int TX = 8, TILE = 1024 * TX, STR = 33 * TX;
   constexpr unsigned kPoll = 1u << 22;
@@ -1097,7 +1099,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
     }
-    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, kPoll);
+    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, poll);
     if (__syncthreads_or(!ok)) {
       if (t == 0) {
         atomicOr(err, 1);
@@ -1222,7 +1224,7 @@ __global__ void __launch_bounds__(PX / 2) k_ewald_tma(const typename RT<R>::C* _
                                                       const Geo<R>* __restrict__ geo,
                                                       const typename RT<R>::C* __restrict__ twz_g,
                                                       R dc0, R dc1, R dc2, R* __restrict__ img,
-                                                      int* __restrict__ err) {
+                                                      int* __restrict__ err, unsigned poll) {
   using C = typename RT<R>::C;
   constexpr unsigned kPoll = 1u << 22;
   constexpr unsigned kBytes = PX * sizeof(C);
@@ -1267,7 +1269,7 @@ __global__ void __launch_bounds__(PX / 2) k_ewald_tma(const typename RT<R>::C* _
   int failed_at = -1;
   for (int z = 0; z < nz; ++z) {
     const int st = z % S;
-    const bool ok = mbar_wait_bounded(&bar[st], (z / S) & 1, kPoll);
+    const bool ok = mbar_wait_bounded(&bar[st], (z / S) & 1, poll);
     if (__syncthreads_or(!ok)) {
       failed_at = z;
       break;
@@ -1812,7 +1814,7 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
 template <bool NT>
 static cudaError_t pol_fft4s_tma_impl(const void* src, int nx, int ny, int nz,
                                       const PolParams<float>& pp, void* p, const void* tw4, int* err,
-                                      int n_sm, cudaStream_t s) {
+                                      int n_sm, unsigned poll, cudaStream_t s) {
   // 2 row buffers, 4 polarisation warps, one transform group, 48 KB of
   // stages (3 x 16 KB of morphology or 6 x 8 KB of N_t): ~106 KB of shared
   // memory and 256 threads, two blocks per SM
@@ -1831,19 +1833,20 @@ static cudaError_t pol_fft4s_tma_impl(const void* src, int nx, int ny, int nz,
   if (e != cudaSuccess) return e;
   const long long grid = nrows < (long long)CPS * n_sm ? nrows : (long long)CPS * n_sm;
   kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>(src, N, nrows, pp, (float2*)p,
-                                                            (const float2*)tw4, err);
+                                                            (const float2*)tw4, err, poll);
   return cudaGetLastError();
 }
 
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
-                                 void* p, const void* tw4, int* err, int n_sm, cudaStream_t s) {
-  return pol_fft4s_tma_impl<false>(M, nx, ny, nz, pp, p, tw4, err, n_sm, s);
+                                 void* p, const void* tw4, int* err, int n_sm, unsigned poll,
+                                 cudaStream_t s) {
+  return pol_fft4s_tma_impl<false>(M, nx, ny, nz, pp, p, tw4, err, n_sm, poll, s);
 }
 
 cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
                                  const PolParams<float>& pp, void* p, const void* tw4, int* err,
-                                 int n_sm, cudaStream_t s) {
-  return pol_fft4s_tma_impl<true>(nt, nx, ny, nz, pp, p, tw4, err, n_sm, s);
+                                 int n_sm, unsigned poll, cudaStream_t s) {
+  return pol_fft4s_tma_impl<true>(nt, nx, ny, nz, pp, p, tw4, err, n_sm, poll, s);
 }
 
 bool yz_fusable(int nx, int ny, int nz) {
@@ -1852,7 +1855,7 @@ bool yz_fusable(int nx, int ny, int nz) {
 
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, void* part, int* err, int n_sm,
-                          long long* L_out, cudaStream_t s) {
+                          unsigned poll, long long* L_out, cudaStream_t s) {
   if (!yz_fusable(nx, ny, nz) || n_sm <= 0) return cudaErrorInvalidValue;
   if (nf != 3 && nf != 5) return cudaErrorInvalidValue;
   const long long ntiles = nx / 8, items = nf * (ntiles / 2), T = items * nz;
@@ -1867,7 +1870,7 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, cons
   k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles,
                                                      (int)L, (int)T, geo,
                                              (const float2*)twz, (const float2*)tw4, (float4*)part,
-                                             err);
+                                             err, poll);
   return cudaGetLastError();
 }
 
@@ -1908,7 +1911,7 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 
 cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long long W,
                                  const ColBatches& bt, const void* tw4, int* err, int n_sm,
-                                 cudaStream_t s) {
+                                 unsigned poll, cudaStream_t s) {
   using C = float2;
   constexpr int TX = 8;
   if (W % TX || bt.base != 0) return cudaErrorInvalidValue;
@@ -1921,7 +1924,7 @@ cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long lo
   if (e != cudaSuccess) return e;
   const long long grid = total < n_sm ? total : n_sm;
   kern<<<(unsigned)grid, 256, smem, s>>>(*(const CUtensorMap*)tmap, (C*)p, S, ntiles, total,
-                                         bt.bdiv, bt.stride_hi, bt.stride_lo, (const C*)tw4, err);
+                                         bt.bdiv, bt.stride_hi, bt.stride_lo, (const C*)tw4, err, poll);
   return cudaGetLastError();
 }
 
@@ -2036,7 +2039,7 @@ cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm
 template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
                          const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s,
-                         int* err) {
+                         int* err, unsigned poll) {
   using C = typename RT<R>::C;
   const long long npix = (long long)nx * ny;
   if (!pruned) {
@@ -2055,7 +2058,7 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)(npix / PX), PX / 2, smem, s>>>((const C*)p, nx, ny, nz, geo, (const C*)twz,
-                                                     dc[0], dc[1], dc[2], (R*)img, err);
+                                                     dc[0], dc[1], dc[2], (R*)img, err, poll);
     return cudaGetLastError();
   }
   const int tw_in_smem = nz <= 4096;
@@ -2177,7 +2180,7 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                        cudaStream_t);                                             \
   template cudaError_t launch_geometry<R>(Geo<R>*, int, int, int, double, double, cudaStream_t);  \
   template cudaError_t launch_ewald<R>(const void*, int, int, int, const Geo<R>*, const void*,     \
-                                       bool, const R*, void*, cudaStream_t, int*);                \
+                                       bool, const R*, void*, cudaStream_t, int*, unsigned);      \
   template cudaError_t launch_rotate_acc<R>(const void*, void*, int, int, double, bool,           \
                                             cudaStream_t);                                        \
   template cudaError_t launch_ewald_linear_many<R>(const void*, int, int, const Geo<R>*,          \

@@ -31,6 +31,11 @@ template <typename R> struct PolParams {
   int add_ref;  // 1: output full p; 0: p minus the constant -(c-1) e'/(4 pi)
 };
 
+// Polls of an mbarrier before a pipelined kernel gives up on a copy (the
+// default; a context may lower it to exercise the failure path).  Waits that
+// drain copies in flight before a block exits always use this bound.
+constexpr unsigned kWaitPolls = 1u << 22;
+
 // A batch of e-field angles for the linearity path's per-angle passes:
 // cos, sin of alpha and the detector rotation's fixed-point coefficients
 // (2^-48) of Q -> U(alpha) Q in pixel units.
@@ -148,13 +153,14 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 // (polarisation, transform, producer); M must be 16-byte aligned; two
 // persistent CTAs per SM (n_sm).
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
-                                 void* p, const void* tw4, int* err, int n_sm, cudaStream_t s);
+                                 void* p, const void* tw4, int* err, int n_sm, unsigned poll,
+                                 cudaStream_t s);
 // The same pipeline for Algorithm 2: p = N_t e from the five stored entries
 // of N_t ([5][N] complex float, 16-byte aligned; the reference constant
 // left out as k_nt_all stores it).
 cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
                                  const PolParams<float>& pp, void* p, const void* tw4, int* err,
-                                 int n_sm, cudaStream_t s);
+                                 int n_sm, unsigned poll, cudaStream_t s);
 // The y-FFT fused with the pruned z transform (FP32): yz_fusable says
 // whether the shape qualifies (ny = 1024, nx a multiple of 16, nz a power
 // of two up to 1024).
@@ -165,7 +171,7 @@ cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
 bool yz_fusable(int nx, int ny, int nz);
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, void* part, int* err, int n_sm,
-                          long long* L_out, cudaStream_t s);
+                          unsigned poll, long long* L_out, cudaStream_t s);
 // The linearity path's per-energy bins (k_zbins5 layout) from launch_yz_tma
 // run over the five FFT'd N_t entries (nf = 5); dc = -(c-1)/(4 pi) N.
 cudaError_t launch_bins5_from_part(const void* part, int nx, int ny, int nz, long long L,
@@ -179,7 +185,7 @@ cudaError_t launch_ewald_bins(const void* part, int nx, int ny, int nz, long lon
 // SM (n_sm).
 cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long long W,
                                  const ColBatches& bt, const void* tw4, int* err, int n_sm,
-                                 cudaStream_t s);
+                                 unsigned poll, cudaStream_t s);
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
                            const void* src = nullptr);
@@ -203,7 +209,7 @@ cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm
 template <typename R>
 cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* geo,
                          const void* twz, bool pruned, const R dc[3], void* img, cudaStream_t s,
-                         int* err = nullptr);
+                         int* err = nullptr, unsigned poll = kWaitPolls);
 // The linearity path's per-angle passes for a batch of angles: images of
 // every angle into imgs ([ab.n][ny][nx], fftshift order), then one
 // rotate-and-accumulate pass over all of them (same sums, same order as one

@@ -33,6 +33,7 @@ EXPORTED = (
     "rsx_set_morphology", "rsx_set_optical_constants", "rsx_run", "rsx_polarization",
     "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
     "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc", "rsx_nt",
+    "rsx_set_wait_limit",
 )
 NOALLOC_MAX_VOXELS = 1 << 20
 NOALLOC_MAX_PIXELS = 1 << 16
@@ -79,6 +80,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "rsx_rotate_accumulate": (ci, [vp, vp, cd, vp, vp]),
         "rsx_scatter_angle": (ci, [vp, ci, cd, vp, vp]),
         "rsx_set_timing": (ci, [vp, ci]),
+        "rsx_set_wait_limit": (ci, [vp, ctypes.c_longlong]),
         "rsx_phase_times": (ci, [vp, vp, vp]),
         "rsx_scatter_angle_noalloc": (ci, [vp, ci, ci, ci, ci, cd, cd, vp, cd, ci, vp, vp]),
         "rsx_nt": (ci, [vp, ci, vp, vp]),
@@ -236,6 +238,11 @@ class Context:
     # ------------------------------------------------------------ timing
     def set_timing(self, enable=True):
         _check(lib().rsx_set_timing(self._h, 1 if enable else 0))
+
+    def set_wait_limit(self, polls=None):
+        """Bound of the pipelined kernels' copy waits (None: the default);
+        0 makes them run out at once, to exercise the failure path."""
+        _check(lib().rsx_set_wait_limit(self._h, -1 if polls is None else int(polls)))
 
     def phase_times(self):
         """{phase: (total device ms, kernel launches)} since the last call."""

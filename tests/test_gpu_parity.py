@@ -381,6 +381,33 @@ def test_async_upload_needs_page_locked_memory(rsx):
 
 
 # ------------------------------------------------------------- error paths
+@pytest.mark.parametrize("algorithm", [1, 2, 3])
+def test_pipeline_wait_timeout_is_reported_and_recoverable(rsx, algorithm):
+    """The pipelined kernels' copy waits are bounded.  With a bound of zero
+    polls every such wait runs out at once: each kernel gives up cleanly (its
+    copies in flight drained under the default bound), the run reports
+    RSX_ERR_CUDA, and with the default bound restored the same context gives
+    the same result as a fresh one.  No fault is involved."""
+    shape, c = (2, 1024, 1024), 2   # FP32, nx = ny = 1024: bulk-copy x pass, fused y+z pass
+    nz, ny, nx = shape
+    M, K = _inputs(shape, c, 32, seed=22)
+    dev = torch.from_numpy(M).cuda()
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=32, algorithm=algorithm) as ctx:
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants(ENERGIES[:1], K[:1])
+        ref = ctx.run((0.0, 90.0, 90.0))
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=32, algorithm=algorithm) as ctx:
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants(ENERGIES[:1], K[:1])
+        ctx.set_wait_limit(0)   # before the energy's first run: per-energy passes run too
+        with pytest.raises(rsx.RsxError) as e:
+            ctx.run((0.0, 90.0, 90.0))
+        assert e.value.code == rsx.RSX_ERR_CUDA and "timed out" in str(e.value)
+        ctx.set_wait_limit()
+        np.testing.assert_array_equal(ctx.run((0.0, 90.0, 90.0)), ref)
+
+
+
 def test_errors_are_reported_and_write_nothing(rsx):
     shape, c = (2, 8, 8), 2
     M, K = _inputs(shape, c, 32, seed=12)
