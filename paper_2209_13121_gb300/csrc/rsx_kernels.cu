@@ -1,15 +1,20 @@
 // CUDA kernels of the GB300 P-RSoXS path (sm_103a).
 //
-// Per energy and e-field angle the hot path runs four kernels:
-//   k_pol_fftx   Eqs. (ncorr), (nrot), (polarization) and p <- U^T p for a
-//                block of x-rows, then the x-FFT of those rows in shared
-//                memory; p is never written before its first FFT pass.
-//   k_col_fft    y-FFT of column tiles in shared memory.
-//   k_ewald      the z-transform evaluated only at the two q_z bins each
-//                detector pixel needs (Eq. Ewald, linear interpolation),
-//                fused with Eq. (3Dscatter); no 3-D X array exists.
-//   k_rotate_acc detector rotation about q = 0 and accumulation (Sec. 4).
-// All of them are HBM-bound streaming kernels; none is a dense contraction.
+// Per energy and e-field angle the hot path (FP32, nx = ny = 1024) runs:
+//   k_pol_fft4s_tma  Eqs. (ncorr), (nrot), (polarization) and p <- U^T p for
+//                    whole x-rows, fed by bulk copies, then the rows' x-FFT;
+//                    p is never written before its first FFT pass.
+//   k_yz_tma         the y-FFT of each z-slice (tiles by 2-D tensor copies)
+//                    fused with the z-transform at the two q_z bins every
+//                    pixel needs (Eq. (Ewald)), accumulated across z.
+//   k_ewald_bins     Eqs. (3Dscatter) and (Ewald) from those bins; no 3-D X
+//                    array exists.
+//   k_rotate_acc     detector rotation about q = 0 and accumulation (Sec. 4).
+// The general-size kernels (Stockham FFTs in shared memory: k_pol_fftx,
+// k_col_fft, k_ewald_pruned / k_ewald_tma), the four-step variants with
+// plain loads (FP64), Algorithm 2's N_t kernels and the linearity path's
+// kernels follow.  None of the path is a dense contraction: the x pass is
+// HBM-bound, the fused y+z pass bound by instruction issue.
 #include <cuda.h>  // CUtensorMap (the type only; the library does not link libcuda)
 #include <math.h>
 
