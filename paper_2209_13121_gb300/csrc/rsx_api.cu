@@ -130,10 +130,10 @@ struct rsx_context {
   void* tw4 = nullptr;  // four-step twiddles [k2][n1] for 1024-point axes
   // tensor maps of the p (3 fields) and, for algorithm 3, ft (5 fields)
   // buffers for the TMA y pass (FP32, ny = 1024); valid when the flag is set
-  alignas(64) CUtensorMap tmap_p;
-  alignas(64) CUtensorMap tmap_ft;
-  alignas(64) CUtensorMap tmap_pz;   // p for the fused y+z pass
-  alignas(64) CUtensorMap tmap_ftz;  // ft (five N_t entries) for the fused y+z pass
+  CUtensorMap tmap_p;
+  CUtensorMap tmap_ft;
+  CUtensorMap tmap_pz;   // p for the fused y+z pass
+  CUtensorMap tmap_ftz;  // ft (five N_t entries) for the fused y+z pass
   bool has_tmap_ftz = false;
   bool has_tmap_p = false, has_tmap_ft = false;
   // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
