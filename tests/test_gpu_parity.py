@@ -499,6 +499,35 @@ def test_full_size_sampled_pixels_match_oracle(rsx, algorithm):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("shape,c", [((1024, 1024, 16), 2), ((64, 1024, 1024), 1)])
+def test_sampled_pixels_at_the_fused_pass_limits(rsx, shape, c):
+    """nz = 1024 (the largest the fused y+z pass takes: the whole 227 KB of
+    shared memory) and one component (one bulk-copy stage per row), vacuum
+    except at sparse voxels: sampled pixels against the oracle's sampled
+    path."""
+    nz, ny, nx = shape
+    E = 285.0
+    sp = synth.sparse_voxels(shape, c, 3000, seed=23)
+    # with one component the background is that material (v = 1, s = 0)
+    K = synth.optical_constants([E], c, seed=24, vacuum_last=c > 1)
+    dev = synth.morphology_sparse_torch(shape, c, sp)
+    g = np.random.default_rng(25)
+    iy = np.concatenate([[0, 1, ny - 1], g.integers(0, ny, 60)])
+    ix = np.concatenate([[0, 3, nx - 1], g.integers(0, nx, 60)])
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=32) as ctx:
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants([E], K)
+        img = torch.empty((ny, nx), dtype=torch.float32, device="cuda")
+        ctx.scatter_angle(0, 0.4, img)
+        full = img.cpu().numpy().astype(np.float64)
+    got = full[(iy + ny // 2) % ny, (ix + nx // 2) % nx]
+    ref = O.scatter_sparse_pixels(sp, shape, K[0], E, VOXEL, 0.4, iy, ix)
+    rest = ~((iy == 0) & (ix == 0))
+    rel = np.linalg.norm(got[rest] - ref[rest]) / np.linalg.norm(ref[rest])
+    assert rel < 1e-4, rel
+    np.testing.assert_allclose(got[~rest], ref[~rest], rtol=1e-5)
+
+
 # ------------------------------------------ full benchmark size (property)
 def test_full_size_z_uniform_reduces_to_film(rsx):
     """At 1024 x 1024 x 128, c = 4, FP32 (the benchmark's launch shape), a
