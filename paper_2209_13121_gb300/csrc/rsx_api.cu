@@ -134,10 +134,9 @@ struct rsx_context {
   CUtensorMap tmap_ft;
   CUtensorMap tmap_pz;   // p for the fused y+z pass
   CUtensorMap tmap_ftz;  // ft (five N_t entries) for the fused y+z pass
-  bool has_tmap_ftz = false;
-  bool has_tmap_p = false, has_tmap_ft = false;
+  bool has_tmap_p = false, has_tmap_ft = false, has_tmap_pz = false, has_tmap_ftz = false;
   // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
-  // [2 slots][3][ny][nx] float4
+  // [kYzSlots][nf][ny][nx] float4
   void* part = nullptr;
   // linearity path: the images of a batch of angles ([kMaxAngleBatch][ny][nx])
   void* imgs = nullptr;
@@ -233,9 +232,10 @@ int upload_tw4(rsx_context* c) {
 }
 
 // A tensor map over `ncomp` fields of [nz][ny][nx] complex float viewed as
-// [ncomp nz][ny][2 nx] floats with 16 x 256 x 1 boxes (TMA y pass).
-bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m,
-               CUtensorMapL2promotion promo = CU_TENSOR_MAP_L2_PROMOTION_L2_256B) {
+// [ncomp nz][ny][2 nx] floats with box_x x 256 x 1 boxes (box_x floats: 16
+// for 8-column tiles, 32 for 16-column tiles).
+bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m, unsigned box_x,
+               CUtensorMapL2promotion promo) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -250,7 +250,7 @@ bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m,
   const cuuint64_t dims[3] = {2 * (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)(ncomp * g.nz)};
   const cuuint64_t strides[2] = {2 * (cuuint64_t)g.nx * sizeof(float),
                                  (cuuint64_t)g.ny * 2 * g.nx * sizeof(float)};
-  const cuuint32_t box[3] = {16, 256, 1};
+  const cuuint32_t box[3] = {box_x, 256, 1};
   const cuuint32_t estr[3] = {1, 1, 1};
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
@@ -370,6 +370,18 @@ int ensure_nt(rsx_context* c, int ie, cudaStream_t s) {
   return RSX_OK;
 }
 
+// The fused y-FFT + q_z bins pass over nf fields (3: p; 5: the linearity
+// path's N_t entries) through the tensor map `map`: the 1024-row kernel or
+// the 512-row one.
+cudaError_t fused_yz(rsx_context* c, const CUtensorMap* map, int nf, long long* L, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  if (g.ny == 512)
+    return rsx::launch_yz512_tma(map, g.nx, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->twy,
+                                 c->part, c->err, c->n_sm, c->wait_polls, L, s);
+  return rsx::launch_yz_tma(map, g.nx, g.ny, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->tw4,
+                            c->part, c->err, c->n_sm, c->wait_polls, L, s);
+}
+
 // Linearity fast path, once per energy: FFT (x and y) of N_t's five
 // entries, then their two q_z bins per pixel.
 template <typename R>
@@ -392,9 +404,7 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
       long long L = 0;
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-        RSX_CK(rsx::launch_yz_tma(&c->tmap_ftz, g.nx, g.ny, g.nz, 5, (const Geo<float>*)c->geo,
-                                  c->twz, c->tw4, c->part, c->err, c->n_sm, c->wait_polls, &L, s),
-               "y-FFT + z-bins kernel");
+        RSX_CK(fused_yz(c, &c->tmap_ftz, 5, &L, s), "y-FFT + z-bins kernel");
       }
       PhaseTimer pt(c, RSX_PHASE_EWALD, s);
       RSX_CK(rsx::launch_bins5_from_part(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
@@ -477,13 +487,11 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
     dc[0] = (R)(ref * cos(alpha)); dc[1] = (R)(ref * sin(alpha)); dc[2] = (R)0;
   }
   if constexpr (sizeof(R) == 4) {
-    if (c->part && c->has_tmap_p) {  // y-FFT and the pruned z transform in one pass
+    if (c->part && c->has_tmap_pz) {  // y-FFT and the pruned z transform in one pass
       long long L = 0;
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-        RSX_CK(rsx::launch_yz_tma(&c->tmap_pz, g.nx, g.ny, g.nz, 3, (const Geo<float>*)c->geo,
-                                  c->twz, c->tw4, c->part, c->err, c->n_sm, c->wait_polls, &L, s),
-               "y-FFT + z-bins kernel");
+        RSX_CK(fused_yz(c, &c->tmap_pz, 3, &L, s), "y-FFT + z-bins kernel");
       }
       PhaseTimer pt(c, RSX_PHASE_EWALD, s);
       RSX_CK(rsx::launch_ewald_bins(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
@@ -544,9 +552,9 @@ const char* rsx_last_error(void) { return g_err.c_str(); }
 static bool uses_yz(const rsx_config* cfg) {
   return cfg->precision == 32 && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
 }
-// two slots of (3 fields of p, or the linearity path's 5 N_t entries) x 2 bins
+// kYzSlots slots of (3 fields of p, or the linearity path's 5 N_t entries) x 2 bins
 static size_t part_bytes(const rsx_config* cfg) {
-  return 2 * (size_t)(cfg->algorithm == 3 ? 5 : 3) * cfg->nx * cfg->ny * 16;
+  return rsx::kYzSlots * (size_t)(cfg->algorithm == 3 ? 5 : 3) * cfg->nx * cfg->ny * 16;
 }
 
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
@@ -646,14 +654,20 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
   if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
     c->n_sm = 0;
   if (cfg->precision == 32 && cfg->ny == 1024 && cfg->nx % 8 == 0 && c->n_sm > 0) {
-    c->has_tmap_p = make_tmap(c, c->p, 3, &c->tmap_p);
-    // the fused y+z pass reads 64-byte halves of 128-byte lines from two
-    // blocks at once: promote to 128 bytes, not 256
-    c->has_tmap_p = c->has_tmap_p &&
-                    make_tmap(c, c->p, 3, &c->tmap_pz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
-    if (c->ft) c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft);
+    c->has_tmap_p = make_tmap(c, c->p, 3, &c->tmap_p, 16, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
     if (c->ft)
-      c->has_tmap_ftz = make_tmap(c, c->ft, 5, &c->tmap_ftz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+      c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft, 16, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
+  }
+  if (uses_yz(cfg) && c->n_sm > 0) {
+    // the fused y+z pass: 1024-row tiles are 8 columns wide and two blocks
+    // read the halves of each 128-byte line at once, 512-row tiles are 16
+    // columns (whole lines); promote to 128 bytes, not 256
+    const unsigned box = cfg->ny == 512 ? 32 : 16;
+    c->has_tmap_pz =
+        make_tmap(c, c->p, 3, &c->tmap_pz, box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    if (c->ft)
+      c->has_tmap_ftz =
+          make_tmap(c, c->ft, 5, &c->tmap_ftz, box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
   }
   if (cfg->algorithm == 3 &&
       (e = cudaMalloc(&c->imgs, (size_t)rsx::kMaxAngleBatch * c->npix * R)) != cudaSuccess) {

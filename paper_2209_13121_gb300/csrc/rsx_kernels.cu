@@ -1163,7 +1163,10 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         acc1[k] = cadd(acc1[k], cmul(qq, wz));
       }
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
-        const int slot = st - z >= s0 ? 0 : 1;
+        // slot: this segment's place among the item's segments (0 if it
+        // began at z = 0); L >= nz / 3 keeps it below kYzSlots
+        const int item_start = st - z;
+        const int slot = item_start >= s0 ? 0 : s0 / L - item_start / L;
         const int f = item >> loghalf;
         float4* dst = part + ((size_t)slot * nf + f) * npix + (size_t)ti * TX + col;
 #pragma unroll
@@ -1173,6 +1176,147 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         }
       }
     }
+  }
+}
+
+// The fused y-FFT + q_z bins pass for ny = 512 (FP32, nx a multiple of 16,
+// nz a power of two up to 1024).  Work items are (field, 16-column tile), so
+// every row segment a tile reads is a whole 128-byte line; the items'
+// z-slices are cut into equal contiguous ranges, one per persistent block
+// (slots as in k_yz_tma).  512 = 16 x 32 with n = n1 + 16 n2 and
+// k = k2 + 32 k1:
+//  stage 1: half hw (warps 0-7 / 8-15) takes the samples n2 = 2m + hw of
+//           row n1 (16 x 16 columns per half) and stores its 16-point DFT,
+//           the odd half times W32^k;
+//  stage 2: thread (k2, column) forms X1[n1][k2] = E +- O' for all 16 n1,
+//           applies W512^(n1 k2) and does the 16-point DFT over n1 in
+//           registers, which leaves it the 16 pixels k2 + 32 k1 (no swap);
+// then the two q_z bins of those pixels are accumulated across z as in
+// k_yz_tma.  The consumed input buffer is refilled (slice + 2) right after
+// stage 1.  Waits are bounded as in k_col_fft4s_tma.
+__global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CUtensorMap tmap,
+                                                      int nx, int nz, int nf, int ntiles, int L,
+                                                      int T, const Geo<float>* __restrict__ geo,
+                                                      const float2* __restrict__ twz_g,
+                                                      const float2* __restrict__ twy_g,
+                                                      float4* __restrict__ part,
+                                                      int* __restrict__ err, unsigned poll) {
+  using C = float2;
+  constexpr int TX = 16, NY = 512, TILE = NY * TX, STR = 33 * 8;
+  constexpr unsigned kPoll = 1u << 22;
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  C* in = reinterpret_cast<C*>(smem_a128);  // [2][512][16], dense (TMA boxes)
+  C* tr = in + 2 * TILE;                     // [32][STR]: (16 hw + k) x (n1 * 16 + col)
+  C* twy = tr + 32 * STR;                    // [512]: W512^j
+  C* twz = twy + NY;                         // [nz]
+  unsigned short* btab = reinterpret_cast<unsigned short*>(twz + nz);  // [512][16]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(btab + TILE);
+  const int t = threadIdx.x, w = t >> 5;
+  const int col = t & 15;
+  const int s0 = (int)blockIdx.x * L;
+  const int s1 = s0 + L < T ? s0 + L : T;
+  if (s0 >= s1) return;
+  const long long npix = (long long)NY * nx;
+  const int lognz = __ffs(nz) - 1;
+  if (t == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_proxy_async();
+  }
+  for (int i = t; i < NY; i += 512) twy[i] = twy_g[i];
+  for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
+  __syncthreads();
+  auto issue = [&](int st, int b) {
+    const int item = st >> lognz;
+    const int z = st & (nz - 1), f = item / ntiles, ti = item - f * ntiles;
+    mbar_expect_tx(&bar[b], TILE * sizeof(C));
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+      tma_load_3d(in + b * TILE + k * 256 * TX, &tmap, ti * 2 * TX, k * 256, f * nz + z, &bar[b]);
+  };
+  if (t == 0) {
+    issue(s0, 0);
+    if (s0 + 1 < s1) issue(s0 + 1, 1);
+  }
+  C acc0[16], acc1[16];
+  int i = 0;
+  for (int st = s0; st < s1; ++st, ++i) {
+    const int b = i & 1;
+    const int item = st >> lognz;
+    const int z = st & (nz - 1);
+    const int ti = item % ntiles;
+    if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
+      __syncthreads();  // the previous step's reads of the bins are done
+      for (int e = t; e < TILE; e += 512) {
+        const int b0 = geo[(size_t)(e >> 4) * nx + ti * TX + (e & 15)].b0;
+        btab[e] = (unsigned short)(b0 < 0 ? 0 : b0);
+      }
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
+    }
+    const bool ok = mbar_wait_bounded(&bar[b], (i >> 1) & 1, poll);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        atomicOr(err, 1);
+        for (int d = 0; d < 2; ++d)
+          if (st + d < s1) mbar_wait_bounded(&bar[(i + d) & 1], ((i + d) >> 1) & 1, kPoll);
+      }
+      return;
+    }
+    // stage 1: 16-point DFT of the samples n2 = 2m + hw of row n1
+    {
+      const int hw = w >> 3, n1 = (t >> 4) & 15;
+      const C* src = in + b * TILE;
+      C v[16];
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = src[(n1 + 16 * hw + 32 * m) * TX + col];
+      dft_reg<16>(v);
+      if (hw) w32_outputs<0>(v);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) tr[(16 * hw + k) * STR + n1 * TX + col] = v[out_pos<16>(k)];
+    }
+    __syncthreads();  // stage-1 halves in tr, bins in place; the input buffer consumed
+    if (t == 0 && st + 2 < s1) {
+      fence_proxy_async();
+      issue(st + 2, b);
+    }
+    // stage 2: X1[n1][k2] = E +- O' (minus for k2 >= 16), times W512^(n1 k2),
+    // then the 16-point DFT over n1: pixels k2 + 32 k1
+    {
+      const int k2 = t >> 4, k = k2 & 15;
+      const float sg = k2 >= 16 ? -1.f : 1.f;  // warp-uniform
+      C v[16];
+#pragma unroll
+      for (int n1 = 0; n1 < 16; ++n1) {
+        const C e = tr[k * STR + n1 * TX + col];
+        const C o = tr[(16 + k) * STR + n1 * TX + col];
+        v[n1] = cmul(make_float2(fmaf(sg, o.x, e.x), fmaf(sg, o.y, e.y)), twy[n1 * k2]);
+      }
+      dft_reg<16>(v);
+      const C wz = twz[z];
+#pragma unroll
+      for (int k1 = 0; k1 < 16; ++k1) {
+        const int row = k2 + 32 * k1;
+        const int b0 = btab[row * TX + col];
+        const C qq = cmul(v[out_pos<16>(k1)], twz[(b0 * z) & (nz - 1)]);
+        acc0[k1] = cadd(acc0[k1], qq);
+        acc1[k1] = cadd(acc1[k1], cmul(qq, wz));
+      }
+      if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
+        // slot: this segment's place among the item's segments (0 if it
+        // began at z = 0); L >= nz / 3 keeps it below kYzSlots
+        const int item_start = st - z;
+        const int slot = item_start >= s0 ? 0 : s0 / L - item_start / L;
+        const int f = item / ntiles;
+        float4* dst = part + ((size_t)slot * nf + f) * npix + (size_t)ti * TX + col;
+#pragma unroll
+        for (int k1 = 0; k1 < 16; ++k1) {
+          const int row = k2 + 32 * k1;
+          dst[(size_t)row * nx] = make_float4(acc0[k1].x, acc0[k1].y, acc1[k1].x, acc1[k1].y);
+        }
+      }
+    }
+    __syncthreads();  // tr is rewritten by the next step
   }
 }
 
@@ -1200,9 +1344,11 @@ __global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, in
 #pragma unroll
   for (int f = 0; f < 3; ++f) {
     float4 v = part[(size_t)f * npix + pix];
-    const int item = f * (ntiles >> 1) + (ti >> 1);  // the tile pair's work item
-    if ((item * nz) / L != ((item + 1) * nz - 1) / L) {
-      const float4 u = part[(size_t)(3 + f) * npix + pix];
+    // the 16-column work item; its segments (one per block it met)
+    const int item = f * (ntiles >> 1) + (ti >> 1);
+    const int nseg = ((item + 1) * nz - 1) / L - (item * nz) / L + 1;
+    for (int sl = 1; sl < nseg; ++sl) {
+      const float4 u = part[(size_t)(sl * 3 + f) * npix + pix];
       v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
     }
     a0[f] = make_float2(v.x, v.y);
@@ -1460,8 +1606,9 @@ __global__ void __launch_bounds__(256) k_bins5_from_part(const float4* __restric
     if (g.b0 >= 0) {
       v = part[(size_t)q * npix + pix];
       const int item = q * (ntiles >> 1) + (ti >> 1);
-      if ((item * nz) / L != ((item + 1) * nz - 1) / L) {
-        const float4 u = part[(size_t)(5 + q) * npix + pix];
+      const int nseg = ((item + 1) * nz - 1) / L - (item * nz) / L + 1;
+      for (int sl = 1; sl < nseg; ++sl) {
+        const float4 u = part[(size_t)(sl * 5 + q) * npix + pix];
         v.x += u.x; v.y += u.y; v.z += u.z; v.w += u.w;
       }
       if (pix == 0 && (q == 0 || q == 2)) {
@@ -1855,7 +2002,30 @@ cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
 }
 
 bool yz_fusable(int nx, int ny, int nz) {
-  return ny == 1024 && nx % 16 == 0 && nz >= 1 && nz <= 1024 && (nz & (nz - 1)) == 0;
+  return (ny == 1024 || ny == 512) && nx % 16 == 0 && nz >= 1 && nz <= 1024 &&
+         (nz & (nz - 1)) == 0;
+}
+
+cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
+                             const void* twz, const void* twy, void* part, int* err, int n_sm,
+                             unsigned poll, long long* L_out, cudaStream_t s) {
+  if (!yz_fusable(nx, 512, nz) || n_sm <= 0 || (nf != 3 && nf != 5)) return cudaErrorInvalidValue;
+  const long long ntiles = nx / 16, items = nf * ntiles, T = items * nz;
+  // equal step ranges over as many blocks as SMs, but at least nz / 3 steps
+  // each, so an item meets at most kYzSlots blocks
+  const long long L0 = (T + n_sm - 1) / n_sm, Lmin = (nz + kYzSlots - 2) / (kYzSlots - 1);
+  const long long L = L0 > Lmin ? L0 : Lmin;
+  const long long grid = (T + L - 1) / L;
+  *L_out = L;
+  const size_t smem = (2 * 8192 + 32 * 33 * 8 + 512 + (size_t)nz) * sizeof(float2) +
+                      8192 * sizeof(unsigned short) + 2 * 8;
+  cudaError_t e = cudaFuncSetAttribute(k_yz512_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  k_yz512_tma<<<(unsigned)grid, 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles,
+                                                (int)L, (int)T, geo, (const float2*)twz,
+                                                (const float2*)twy, (float4*)part, err, poll);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
@@ -1864,9 +2034,13 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, cons
   if (!yz_fusable(nx, ny, nz) || n_sm <= 0) return cudaErrorInvalidValue;
   if (nf != 3 && nf != 5) return cudaErrorInvalidValue;
   const long long ntiles = nx / 8, items = nf * (ntiles / 2), T = items * nz;
-  const long long pairs = items < n_sm / 2 ? items : n_sm / 2;
-  if (pairs < 1) return cudaErrorInvalidValue;
-  const long long L = (T + pairs - 1) / pairs;  // >= nz: an item meets at most two pairs
+  if (n_sm < 2) return cudaErrorInvalidValue;
+  // equal step ranges over as many block pairs as SMs allow, but at least
+  // nz / 3 steps each, so an item meets at most kYzSlots pairs
+  const long long P0 = n_sm / 2;
+  const long long L0 = (T + P0 - 1) / P0, Lmin = (nz + kYzSlots - 2) / (kYzSlots - 1);
+  const long long L = L0 > Lmin ? L0 : Lmin;
+  const long long pairs = (T + L - 1) / L;
   *L_out = L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 1024 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;

@@ -162,16 +162,24 @@ cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
                                  const PolParams<float>& pp, void* p, const void* tw4, int* err,
                                  int n_sm, unsigned poll, cudaStream_t s);
 // The y-FFT fused with the pruned z transform (FP32): yz_fusable says
-// whether the shape qualifies (ny = 1024, nx a multiple of 16, nz a power
-// of two up to 1024).
+// whether the shape qualifies (ny = 1024 or 512, nx a multiple of 16, nz a
+// power of two up to 1024).
 // launch_yz_tma writes the two q_z bins of every pixel and of each of the nf
-// fields (3: p; 5: the linearity path's N_t entries) into part ([2 slots][nf]
-// [ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
+// fields (3: p; 5: the linearity path's N_t entries) into part ([kYzSlots]
+// [nf][ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
 // the step count per block that launch_ewald_bins needs to add the slots.
 bool yz_fusable(int nx, int ny, int nz);
+// Partial-bin slots of the fused pass: a work item's z-slices meet at most
+// this many blocks (their step ranges hold at least nz / (kYzSlots - 1)).
+constexpr int kYzSlots = 4;
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, void* part, int* err, int n_sm,
                           unsigned poll, long long* L_out, cudaStream_t s);
+// The same for ny = 512 (16-column tiles, tensor map boxes of 32 floats x
+// 256 rows; twy the 512-point twiddle table).
+cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
+                             const void* twz, const void* twy, void* part, int* err, int n_sm,
+                             unsigned poll, long long* L_out, cudaStream_t s);
 // The linearity path's per-energy bins (k_zbins5 layout) from launch_yz_tma
 // run over the five FFT'd N_t entries (nf = 5); dc = -(c-1)/(4 pi) N.
 cudaError_t launch_bins5_from_part(const void* part, int nx, int ny, int nz, long long L,

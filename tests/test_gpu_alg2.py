@@ -127,7 +127,7 @@ def test_polarization_from_nt(rsx, prec, frame):
 @pytest.mark.parametrize("prec", [32, 64])
 @pytest.mark.parametrize("where", ["device", "host"])
 @pytest.mark.parametrize("shape,c", [((4, 16, 16), 3), ((6, 32, 128), 4), ((1, 64, 64), 2),
-                                     ((2, 8, 1024), 3), ((3, 256, 1024), 2)])
+                                     ((2, 8, 1024), 3), ((3, 256, 1024), 2), ((2, 512, 32), 2)])
 def test_alg2_run_matches_oracle_and_alg1(rsx, shape, c, prec, where):
     M = synth.morphology_random(shape, c, seed=57, dtype=_real(prec))
     K = synth.optical_constants(ENERGIES, c, seed=58)
@@ -160,7 +160,8 @@ def test_nt_refused_in_algorithm1_context(rsx):
 @pytest.mark.parametrize("prec", [32, 64])
 @pytest.mark.parametrize("frame", [0, 1])
 @pytest.mark.parametrize("shape,c", [((4, 16, 16), 3), ((6, 32, 128), 4), ((1, 64, 64), 2),
-                                     ((5, 8, 32), 2), ((2, 1024, 8), 2), ((4, 1024, 64), 2)])
+                                     ((5, 8, 32), 2), ((2, 1024, 8), 2), ((4, 1024, 64), 2),
+                                     ((2, 512, 32), 2)])
 def test_linear_path_matches_oracle_and_alg1(rsx, shape, c, prec, frame):
     M = synth.morphology_random(shape, c, seed=61, dtype=_real(prec))
     K = synth.optical_constants(ENERGIES, c, seed=62)

@@ -238,9 +238,11 @@ def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
 # pass at its edges: nz = 1 (both q_z bins are plane 0), the narrowest
 # width (one tile pair), a field split between two block pairs, a 2048-wide
 # grid (Stockham x pass feeding the fused y+z pass); one component (one
-# bulk-copy stage per row).
+# bulk-copy stage per row); 512-row grids (the 16-column variant of the
+# fused pass, with items split between blocks).
 MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2), ((1, 1024, 64), 3), ((4, 1024, 16), 2),
-         ((2, 1024, 512), 2), ((1, 1024, 2048), 2), ((3, 8, 1024), 1)]
+         ((2, 1024, 512), 2), ((1, 1024, 2048), 2), ((3, 8, 1024), 1), ((4, 512, 64), 2),
+         ((2, 512, 1024), 2)]
 
 
 @pytest.mark.parametrize("shape,c", MULTI, ids=["x".join(map(str, s)) for s, _ in MULTI])
