@@ -435,15 +435,17 @@ int x_pass(rsx_context* c, const PolParams<R>& pp, cudaStream_t s) {
   const rsx_config& g = c->cfg;
   PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
   if constexpr (sizeof(R) == 4) {
-    if (g.nx == 1024 && c->n_sm > 0 && g.algorithm == 1 && ((uintptr_t)c->M & 15) == 0) {
-      RSX_CK(rsx::launch_pol_fft4s_tma(c->M, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err, c->n_sm,
+    const bool fast = (g.nx == 1024 || g.nx == 512) && c->n_sm > 0;
+    const void* tw = g.nx == 1024 ? c->tw4 : c->twx;
+    if (fast && g.algorithm == 1 && ((uintptr_t)c->M & 15) == 0) {
+      RSX_CK(rsx::launch_pol_fft4s_tma(c->M, g.nx, g.ny, g.nz, pp, c->p, tw, c->err, c->n_sm,
                                        c->wait_polls, s),
              "polarisation + x-FFT kernel");
       return RSX_OK;
     }
-    if (g.nx == 1024 && c->n_sm > 0 && g.algorithm == 2) {
-      RSX_CK(rsx::launch_ntp_fft4s_tma(c->nt, g.nx, g.ny, g.nz, pp, c->p, c->tw4, c->err,
-                                       c->n_sm, c->wait_polls, s),
+    if (fast && g.algorithm == 2) {
+      RSX_CK(rsx::launch_ntp_fft4s_tma(c->nt, g.nx, g.ny, g.nz, pp, c->p, tw, c->err, c->n_sm,
+                                       c->wait_polls, s),
              "N_t polarisation + x-FFT kernel");
       return RSX_OK;
     }

@@ -370,15 +370,18 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
 // roles skip their work but still complete the barrier protocol (which has
 // no unbounded wait left), the producer waits (bounded) for its copies in
 // flight, and the block exits.
-template <int S, int NP, int PW, int FG, bool NT>
+template <int S, int NP, int PW, int FG, bool NT, int NX>
 __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
     const void* __restrict__ src, long long N, long long nrows, PolParams<float> pp,
     float2* __restrict__ p, const float2* __restrict__ tw4_g, int* __restrict__ err,
     unsigned poll) {
   using C = float2;
   using SrcT = typename std::conditional<NT, float2, float4>::type;
-  constexpr int NX = 1024, TP = 32 * PW, SL = NX / TP, FS = 32 * 33, NB = TP + 96;
-  static_assert(NX % TP == 0 && 1 + 2 * NP <= 15, "layout");
+  static_assert(NX == 1024 || NX == 512, "row length");
+  // row buffers: the 1024-point transform's 32 x 33 transpose; 512 points
+  // transpose 16 x 33 (tw4_g: W1024^(ab) as [32][32], or W512^j for 512)
+  constexpr int TP = 32 * PW, SL = NX / TP, FS = (NX / 32) * 33, NB = TP + 96;
+  static_assert(NX % TP == 0 && 1 + 2 * NP <= 15 && NP % FG == 0, "layout");
   constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(SrcT);
   extern __shared__ __align__(128) unsigned char smem_a128[];
   SrcT* stage = reinterpret_cast<SrcT*>(smem_a128);        // [S][NX]
@@ -396,7 +399,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
     *abort_flag = 0;
     fence_proxy_async();
   }
-  for (int i = t; i < 1024; i += blockDim.x) tw4[i] = tw4_g[i];
+  for (int i = t; i < (NX == 1024 ? 1024 : 512); i += blockDim.x) tw4[i] = tw4_g[i];
   __syncthreads();
   const long long nmine =
       blockIdx.x < nrows ? (nrows - 1 - blockIdx.x) / gridDim.x + 1 : 0;
@@ -531,23 +534,50 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
       const long long row = blockIdx.x + rr * gridDim.x;
       C* F = P + i * 3 * FS + f * FS;
       C v[32];
+      if constexpr (NX == 1024) {
 #pragma unroll
-      for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
-      dft32(v);
+        for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
+        dft32(v);
 #pragma unroll
-      for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
-      __syncwarp();
+        for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+        __syncwarp();
 #pragma unroll
-      for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
-      __syncwarp();
+        for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
+        __syncwarp();
 #pragma unroll
-      for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
-      __syncwarp();
-      if (rr + NP < nmine) named_bar_arrive(1 + NP + i, NB);
-      dft32(v);
-      C* out = p + (size_t)f * N + (size_t)row * NX + lane;
+        for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+        __syncwarp();
+        if (rr + NP < nmine) named_bar_arrive(1 + NP + i, NB);
+        dft32(v);
+        C* out = p + (size_t)f * N + (size_t)row * NX + lane;
 #pragma unroll
-      for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+        for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+      } else {
+        // 512 = 32 x 16 with n = n1 + 32 n2, k = k2 + 16 k1: lane n1 does the
+        // 16-point DFT over n2 and the twiddles W512^(n1 k2); after the
+        // transpose, lanes k2 and k2 + 16 share the 32-point DFT over n1
+        // (even n1 on the lower lane, odd on the upper), which leaves
+        // k1 = k and k1 = 16 + k on the two lanes
+#pragma unroll
+        for (int n2 = 0; n2 < 16; ++n2) v[n2] = F[lane + 32 * n2];
+        dft_reg<16>(v);
+        C u[16];
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) u[k2] = cmul(v[out_pos<16>(k2)], tw4[lane * k2]);
+        __syncwarp();
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) F[k2 * 33 + lane] = u[k2];
+        __syncwarp();
+        const int k2 = lane & 15, h = lane >> 4;
+#pragma unroll
+        for (int m = 0; m < 16; ++m) v[m] = F[k2 * 33 + 2 * m + h];
+        __syncwarp();
+        if (rr + NP < nmine) named_bar_arrive(1 + NP + i, NB);
+        dft32_pair(v, u, h);
+        C* out = p + (size_t)f * N + (size_t)row * NX + k2 + 256 * h;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) out[16 * k] = u[k];
+      }
     } else if (rr + NP < nmine) {
       named_bar_arrive(1 + NP + i, NB);
     }
@@ -1963,21 +1993,22 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
   return cudaGetLastError();
 }
 
-template <bool NT>
+template <bool NT, int NX>
 static cudaError_t pol_fft4s_tma_impl(const void* src, int nx, int ny, int nz,
                                       const PolParams<float>& pp, void* p, const void* tw4, int* err,
                                       int n_sm, unsigned poll, cudaStream_t s) {
   // 2 row buffers, 4 polarisation warps, one transform group, 48 KB of
-  // stages (3 x 16 KB of morphology or 6 x 8 KB of N_t): ~106 KB of shared
-  // memory and 256 threads, two blocks per SM
-  constexpr int S = NT ? 6 : 3, NP = 2, PW = 4, FG = 1, CPS = 2;
+  // stages (rows of morphology components or of N_t entries): ~106 KB of
+  // shared memory for 1024-point rows, ~78 KB for 512, 256 threads, two
+  // blocks per SM
   constexpr size_t elem = NT ? sizeof(float2) : sizeof(float4);
-  if (nx != 1024 || n_sm <= 0 || ((uintptr_t)src & 15)) return cudaErrorInvalidValue;
+  constexpr int S = (int)(48 * 1024 / (NX * elem)), NP = 2, PW = 4, FG = 1, CPS = 2;
+  if (nx != NX || n_sm <= 0 || ((uintptr_t)src & 15)) return cudaErrorInvalidValue;
   const long long N = (long long)nx * ny * nz, nrows = (long long)ny * nz;
   if (nrows <= 0) return cudaSuccess;
-  const size_t smem = (size_t)S * 1024 * elem + (NP * 3 * 32 * 33 + 1024) * sizeof(float2) +
+  const size_t smem = (size_t)S * NX * elem + (NP * 3 * (NX / 32) * 33 + 1024) * sizeof(float2) +
                       2 * S * 8 + 16;
-  auto kern = k_pol_fft4s_tma<S, NP, PW, FG, NT>;
+  auto kern = k_pol_fft4s_tma<S, NP, PW, FG, NT, NX>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -1990,15 +2021,17 @@ static cudaError_t pol_fft4s_tma_impl(const void* src, int nx, int ny, int nz,
 }
 
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
-                                 void* p, const void* tw4, int* err, int n_sm, unsigned poll,
+                                 void* p, const void* tw, int* err, int n_sm, unsigned poll,
                                  cudaStream_t s) {
-  return pol_fft4s_tma_impl<false>(M, nx, ny, nz, pp, p, tw4, err, n_sm, poll, s);
+  return nx == 512 ? pol_fft4s_tma_impl<false, 512>(M, nx, ny, nz, pp, p, tw, err, n_sm, poll, s)
+                   : pol_fft4s_tma_impl<false, 1024>(M, nx, ny, nz, pp, p, tw, err, n_sm, poll, s);
 }
 
 cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
-                                 const PolParams<float>& pp, void* p, const void* tw4, int* err,
+                                 const PolParams<float>& pp, void* p, const void* tw, int* err,
                                  int n_sm, unsigned poll, cudaStream_t s) {
-  return pol_fft4s_tma_impl<true>(nt, nx, ny, nz, pp, p, tw4, err, n_sm, poll, s);
+  return nx == 512 ? pol_fft4s_tma_impl<true, 512>(nt, nx, ny, nz, pp, p, tw, err, n_sm, poll, s)
+                   : pol_fft4s_tma_impl<true, 1024>(nt, nx, ny, nz, pp, p, tw, err, n_sm, poll, s);
 }
 
 bool yz_fusable(int nx, int ny, int nz) {

@@ -148,10 +148,11 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
 template <typename R>
 cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
                              const void* tw4, cudaStream_t s);
-// The Algorithm-1 x pass (FP32, nx = 1024) streaming the morphology
+// The Algorithm-1 x pass (FP32, nx = 1024 or 512) streaming the morphology
 // through a ring of bulk-copy stages into warp-specialised blocks
 // (polarisation, transform, producer); M must be 16-byte aligned; two
-// persistent CTAs per SM (n_sm).
+// persistent CTAs per SM (n_sm).  tw: the four-step table W1024^(ab) as
+// [32][32] for nx = 1024, the 512-point table W512^j for nx = 512.
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, unsigned poll,
                                  cudaStream_t s);

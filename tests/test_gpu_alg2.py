@@ -127,7 +127,8 @@ def test_polarization_from_nt(rsx, prec, frame):
 @pytest.mark.parametrize("prec", [32, 64])
 @pytest.mark.parametrize("where", ["device", "host"])
 @pytest.mark.parametrize("shape,c", [((4, 16, 16), 3), ((6, 32, 128), 4), ((1, 64, 64), 2),
-                                     ((2, 8, 1024), 3), ((3, 256, 1024), 2), ((2, 512, 32), 2)])
+                                     ((2, 8, 1024), 3), ((3, 256, 1024), 2), ((2, 512, 32), 2),
+                                     ((3, 64, 512), 2), ((2, 512, 512), 3)])
 def test_alg2_run_matches_oracle_and_alg1(rsx, shape, c, prec, where):
     M = synth.morphology_random(shape, c, seed=57, dtype=_real(prec))
     K = synth.optical_constants(ENERGIES, c, seed=58)

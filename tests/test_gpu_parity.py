@@ -239,10 +239,12 @@ def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
 # width (one tile pair), a field split between two block pairs, a 2048-wide
 # grid (Stockham x pass feeding the fused y+z pass); one component (one
 # bulk-copy stage per row); 512-row grids (the 16-column variant of the
-# fused pass, with items split between blocks).
+# fused pass, with items split between blocks); 512-wide rows (the 32 x 16
+# transform of the bulk-copy x pass) with one and three components, alone
+# and feeding the 512-row fused pass.
 MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2), ((1, 1024, 64), 3), ((4, 1024, 16), 2),
          ((2, 1024, 512), 2), ((1, 1024, 2048), 2), ((3, 8, 1024), 1), ((4, 512, 64), 2),
-         ((2, 512, 1024), 2)]
+         ((2, 512, 1024), 2), ((5, 64, 512), 3), ((3, 8, 512), 1), ((4, 512, 512), 2)]
 
 
 @pytest.mark.parametrize("shape,c", MULTI, ids=["x".join(map(str, s)) for s, _ in MULTI])
@@ -502,11 +504,12 @@ def test_full_size_sampled_pixels_match_oracle(rsx, algorithm):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("shape,c", [((1024, 1024, 16), 2)])
+@pytest.mark.parametrize("shape,c", [((1024, 1024, 16), 2), ((64, 512, 512), 4)])
 def test_sampled_pixels_at_the_fused_pass_limits(rsx, shape, c):
     """nz = 1024, the largest the fused y+z pass takes (the whole 227 KB of
-    shared memory), vacuum except at sparse voxels: sampled pixels against
-    the oracle's sampled path."""
+    shared memory), and the 512 x 512 x 64, c = 4 grid (the 512-point x
+    pass and the 512-row fused pass at their launch shape), vacuum except at
+    sparse voxels: sampled pixels against the oracle's sampled path."""
     nz, ny, nx = shape
     E = 285.0
     sp = synth.sparse_voxels(shape, c, 3000, seed=23)
