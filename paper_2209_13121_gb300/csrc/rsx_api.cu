@@ -427,9 +427,9 @@ int ensure_bins(rsx_context* c, int ie, cudaStream_t s) {
 }
 
 // The x pass (polarisation fused with the x-FFT) into c->p: the bulk-copy
-// pipelines for FP32 with nx = 1024 (morphology or N_t), the four-step
-// kernel with plain loads for other nx = 1024 cases, the Stockham kernels
-// for other sizes.
+// pipelines for FP32 with nx = 1024 or 512 (morphology or N_t), the
+// four-step kernel with plain loads for other nx = 1024 cases, the Stockham
+// kernels for other sizes.
 template <typename R>
 int x_pass(rsx_context* c, const PolParams<R>& pp, cudaStream_t s) {
   const rsx_config& g = c->cfg;

@@ -1,11 +1,11 @@
 // CUDA kernels of the GB300 P-RSoXS path (sm_103a).
 //
-// Per energy and e-field angle the hot path (FP32, nx = ny = 1024) runs:
+// Per energy and e-field angle the hot path (FP32, nx and ny 1024 or 512) runs:
 //   k_pol_fft4s_tma  Eqs. (ncorr), (nrot), (polarization) and p <- U^T p for
 //                    whole x-rows, fed by bulk copies, then the rows' x-FFT;
 //                    p is never written before its first FFT pass.
 //   k_yz_tma         the y-FFT of each z-slice (tiles by 2-D tensor copies)
-//                    fused with the z-transform at the two q_z bins every
+//   (k_yz512_tma)    fused with the z-transform at the two q_z bins every
 //                    pixel needs (Eq. (Ewald)), accumulated across z.
 //   k_ewald_bins     Eqs. (3Dscatter) and (Ewald) from those bins; no 3-D X
 //                    array exists.
@@ -349,20 +349,21 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
   for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
 }
 
-// x pass (FP32, nx = 1024) as a warp-specialised bulk-copy pipeline, for
-// Algorithm 1 (NT = false: the morphology, c slices of 16 KB per row) or
-// Algorithm 2 (NT = true: the five stored entries of N_t, 8 KB each).
+// x pass (FP32, nx = NX = 1024 or 512) as a warp-specialised bulk-copy
+// pipeline, for Algorithm 1 (NT = false: the morphology, c slices of 16 NX
+// bytes per row) or Algorithm 2 (NT = true: the five stored entries of N_t,
+// 8 NX bytes each).
 // Three roles per block:
 //  * a producer lane streams (row, component or entry) slices into a ring
 //    of S shared-memory stages (full/empty mbarrier pairs), up to S slices
 //    ahead;
-//  * PW polarisation warps accumulate 1024 / (32 PW) voxels per thread from
+//  * PW polarisation warps accumulate NX / (32 PW) voxels per thread from
 //    each stage (Algorithm 1: pol_add per component; Algorithm 2: p = N_t e
 //    entry by entry), release it per warp, and write the row's three fields
 //    into one of NP row buffers;
 //  * FG groups of three transform warps (group g takes the rows r with
-//    r mod FG = g) run the four-step FFT of k_pol_fft4s on a filled buffer
-//    and store the spectrum.
+//    r mod FG = g) run a four-step FFT on a filled buffer (32 x 32 as in
+//    k_pol_fft4s, or 32 x 16 for 512 points) and store the spectrum.
 // Row buffers pass between the roles on named barriers (full: 1 + i, empty:
 // 1 + NP + i), so polarisation of the next rows overlaps the transforms.
 // CTAs are persistent and walk rows with a grid stride.  Every mbarrier wait
@@ -1050,9 +1051,10 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 // steps per pair of persistent CTAs (blocks 2j and 2j + 1 take the even and
 // the odd tile of the same steps, so the two 64-byte halves of every
 // 128-byte row segment are read at about the same time: DRAM fetches whole
-// lines).  Every CTA does the same number of steps and an item is split
-// between at most two CTA pairs: the part that starts at z = 0 goes to slot
-// 0 of `part`, the other to slot 1, and k_ewald_bins adds them.
+// lines).  Every CTA does the same number of steps; with L >= nz / 3 an item
+// is split between at most four CTA pairs: the part that starts at z = 0
+// goes to slot 0 of `part`, the others to slots 1-3 in order, and
+// k_ewald_bins adds them.
 //
 // Per step the slice's 8 x 1024 tile arrives by 2-D tensor TMA (two
 // buffers).  The four-step 32 x 32 FFT is split between the two halves of
@@ -1351,7 +1353,7 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
 }
 
 // Eqs. (3Dscatter)/(Ewald) from the bins of k_yz_tma: per pixel, the two
-// q_z bins of the three fields (slot 1 added where the item was split), the
+// q_z bins of the three fields (slots 1-3 added where the item was split), the
 // constant part returned at q = 0, the projection and the interpolation;
 // written in fftshift order.
 __global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, int nz,
