@@ -12,7 +12,8 @@
  * ---------------------------------------
  *  - Return value: RSX_OK (0) on success, a negative RSX_ERR_* code
  *    otherwise.  rsx_last_error() then returns a message for the failing
- *    call on this host thread.  A failing call writes none of its outputs.
+ *    call on this host thread.  A failing call writes none of its outputs
+ *    (rsx_run with device output: see there).
  *  - Real: float when the context was created with precision 32, double with
  *    precision 64 (the paper's float4 / double4 builds, Sec. 4.1).  Complex
  *    values are (re, im) pairs of Real.
@@ -139,7 +140,13 @@ int rsx_set_optical_constants(rsx_context* ctx, int n_energies, const double* en
  * and no image rotation when rotation is 0).
  * energy_idx[n_sel] selects energies by index (NULL: all, in order; this is
  * the sharding hook: disjoint subsets give the matching rows bit for bit).
- * out: [n_sel][ny][nx] Real, in host or device memory per `where`. */
+ * out: [n_sel][ny][nx] Real, in host or device memory per `where`.
+ * Host output is staged and copied into `out` only after the stream has
+ * finished every energy and no pipelined kernel reported a timeout, so a
+ * failing call leaves it untouched.  Device output is written in stream
+ * order, energy by energy: a launch that fails part-way leaves the rows of
+ * the energies already finished written, and a pipeline timeout is
+ * reported by the next call with host output (rsx_set_wait_limit). */
 int rsx_run(rsx_context* ctx, double start_deg, double increment_deg, double end_deg,
             int rotation, const int* energy_idx, int n_sel, void* out, int where,
             void* stream);

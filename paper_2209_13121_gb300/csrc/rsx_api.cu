@@ -941,6 +941,10 @@ template <typename R>
 int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
              const std::vector<int>& sel, void* out, int where, cudaStream_t s) {
   const size_t img_bytes = (size_t)c->npix * sizeof(R);
+  // host output lands in `out` only once every energy has succeeded and no
+  // pipelined kernel reported a timeout: until then it is staged here
+  std::vector<unsigned char> staged;
+  if (where == RSX_HOST) staged.resize(sel.size() * img_bytes);
   for (size_t o = 0; o < sel.size(); ++o) {
     const int ie = sel[o];
     RSX_CK(cudaMemsetAsync(c->acc, 0, img_bytes, s), "clear average");
@@ -955,8 +959,8 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
              "average kernel");
     } else {
       RSX_CK(rsx::launch_scale<R>(c->acc, c->acc, c->npix, inv, s), "average kernel");
-      RSX_CK(cudaMemcpyAsync((char*)out + o * img_bytes, c->acc, img_bytes, cudaMemcpyDeviceToHost,
-                             s),
+      RSX_CK(cudaMemcpyAsync(staged.data() + o * img_bytes, c->acc, img_bytes,
+                             cudaMemcpyDeviceToHost, s),
              "result download");
     }
   }
@@ -970,6 +974,7 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
       c->bins_energy = -1;
       return fail(RSX_ERR_CUDA, "a kernel pipeline wait timed out; the result is not valid");
     }
+    memcpy(out, staged.data(), staged.size());
   }
   return RSX_OK;
 }

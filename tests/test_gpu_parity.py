@@ -391,8 +391,9 @@ def test_pipeline_wait_timeout_is_reported_and_recoverable(rsx, algorithm):
     """The pipelined kernels' copy waits are bounded.  With a bound of zero
     polls every such wait runs out at once: each kernel gives up cleanly (its
     copies in flight drained under the default bound), the run reports
-    RSX_ERR_CUDA, and with the default bound restored the same context gives
-    the same result as a fresh one.  No fault is involved."""
+    RSX_ERR_CUDA without touching its host output, and with the default
+    bound restored the same context gives the same result as a fresh one.
+    No fault is involved."""
     shape, c = (2, 1024, 1024), 2   # FP32, nx = ny = 1024: bulk-copy x pass, fused y+z pass
     nz, ny, nx = shape
     M, K = _inputs(shape, c, 32, seed=22)
@@ -405,9 +406,11 @@ def test_pipeline_wait_timeout_is_reported_and_recoverable(rsx, algorithm):
         ctx.set_morphology(dev)
         ctx.set_optical_constants(ENERGIES[:1], K[:1])
         ctx.set_wait_limit(0)   # before the energy's first run: per-energy passes run too
+        out = np.full((1, ny, nx), 7.0, dtype=np.float32)
         with pytest.raises(rsx.RsxError) as e:
-            ctx.run((0.0, 90.0, 90.0))
+            ctx.run((0.0, 90.0, 90.0), out=out)
         assert e.value.code == rsx.RSX_ERR_CUDA and "timed out" in str(e.value)
+        assert np.all(out == 7.0)   # the failing call left its host output untouched
         ctx.set_wait_limit()
         np.testing.assert_array_equal(ctx.run((0.0, 90.0, 90.0)), ref)
 
