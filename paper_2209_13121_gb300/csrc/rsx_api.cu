@@ -7,6 +7,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <new>
 #include <string>
 #include <vector>
 
@@ -592,7 +593,8 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
   *out = nullptr;
   int rc = check_config(cfg);
   if (rc) return rc;
-  rsx_context* c = new rsx_context();
+  rsx_context* c = new (std::nothrow) rsx_context();
+  if (!c) return fail(RSX_ERR_OOM, "no host memory for the context");
   c->cfg = *cfg;
   c->N = (long long)cfg->nx * cfg->ny * cfg->nz;
   c->npix = (long long)cfg->nx * cfg->ny;
@@ -944,7 +946,13 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
   // host output lands in `out` only once every energy has succeeded and no
   // pipelined kernel reported a timeout: until then it is staged here
   std::vector<unsigned char> staged;
-  if (where == RSX_HOST) staged.resize(sel.size() * img_bytes);
+  if (where == RSX_HOST) {
+    try {
+      staged.resize(sel.size() * img_bytes);
+    } catch (const std::bad_alloc&) {
+      return fail(RSX_ERR_OOM, "no host memory to stage %zu result bytes", sel.size() * img_bytes);
+    }
+  }
   for (size_t o = 0; o < sel.size(); ++o) {
     const int ie = sel[o];
     RSX_CK(cudaMemsetAsync(c->acc, 0, img_bytes, s), "clear average");
