@@ -1,7 +1,9 @@
 """Benchmark of the GB300 P-RSoXS hot path (Algorithm 1).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload p1-1024|p1-512|p2-2048|p0-small] [--precision 32|64]
+                    [--workload NAME] [--precision 32|64] [--algorithm 1|2|3]
+                    [--components C] [--angle-batch K]
+    python bench.py --cpu-report      # the oracle on this host, single and all cores
 
 One step = one photon energy of Algorithm 1: the morphology of the workload
 (c components, seeded synthetic, resident in HBM) through polarisation, FFT,
@@ -9,6 +11,8 @@ Ewald projection and the detector-rotation average over the e-field angles
 0:2:180 (91 angles).  The metric is voxel-angle throughput, the voxel count
 times angles times energies per second, summed over ranks.  Multi-GPU runs
 shard energies across ranks (independent units, no collective): weak scaling.
+With --gpus N > 1 and no torchrun environment, the script starts N ranks of
+itself under torch.distributed.run (127.0.0.1 rendezvous).
 
 Prints one JSON line on rank 0.
 """
@@ -28,16 +32,29 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# energies: (count, lo, hi) eV, uniform; one energy per step
 WORKLOADS = {
     # Sec. 6.1 voxel scaling, largest case (1024^2 x 128, 4 materials, 0:2:180)
-    "p1-1024": dict(shape=(128, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0)),
-    "p1-512": dict(shape=(64, 512, 512), c=4, angles=(0.0, 2.0, 180.0)),
-    # Sec. 6.2 material scaling (2048^2 x 64)
-    "p2-2048": dict(shape=(64, 2048, 2048), c=4, angles=(0.0, 2.0, 180.0)),
-    "p0-small": dict(shape=(16, 128, 128), c=4, angles=(0.0, 2.0, 180.0)),
+    "p1-1024": dict(shape=(128, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0),
+                    energies=(150, 270.0, 320.0)),
+    "p1-512": dict(shape=(64, 512, 512), c=4, angles=(0.0, 2.0, 180.0),
+                   energies=(150, 270.0, 320.0)),
+    # Sec. 6.2 material scaling (2048^2 x 64, 9 energies; c swept 2..10 with
+    # --components)
+    "p2-2048": dict(shape=(64, 2048, 2048), c=4, angles=(0.0, 2.0, 180.0),
+                    energies=(9, 270.0, 320.0)),
+    # Sec. 5.1 sphere cases: the 2-D film (41 energies 270-310 eV, FP64
+    # against FP32) and the 3-D stack at one energy
+    "p3-2048-film": dict(shape=(1, 2048, 2048), c=2, angles=(0.0, 2.0, 180.0),
+                         energies=(41, 270.0, 310.0)),
+    "p4-2048": dict(shape=(128, 2048, 2048), c=2, angles=(0.0, 2.0, 180.0),
+                    energies=(1, 285.0, 285.0)),
+    "p0-small": dict(shape=(16, 128, 128), c=4, angles=(0.0, 2.0, 180.0),
+                     energies=(150, 270.0, 320.0)),
     # P1's lateral size with a shorter stack: the same kernel shapes in ~3 GB,
     # small enough for full ncu captures
-    "p1-1024-z32": dict(shape=(32, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0)),
+    "p1-1024-z32": dict(shape=(32, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0),
+                        energies=(150, 270.0, 320.0)),
 }
 VOXEL_NM = 5.0
 METRIC = "P-RSoXS voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s')"
@@ -119,41 +136,90 @@ def _dist():
     return ws, rank, local
 
 
+def _free_port():
+    import socket
+    with socket.socket() as sk:
+        sk.bind(("127.0.0.1", 0))
+        return sk.getsockname()[1]
+
+
+def launch_ranks(n, argv):
+    """Runs this script as n ranks under torch.distributed.run on this node
+    (rendezvous on 127.0.0.1) and returns its exit status."""
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+           f"--nproc-per-node={n}", "--master-addr=127.0.0.1", f"--master-port={_free_port()}",
+           os.path.abspath(__file__), *argv]
+    return subprocess.call(cmd)
+
+
+class _Ranks:
+    """The control plane of a multi-rank run: barrier and max over ranks.
+    NCCL when every rank has its own GPU; gloo (CPU tensors) when ranks
+    share a device or there is none (a functional check of the launch)."""
+
+    def __init__(self, ws, backend):
+        import torch.distributed as dist
+        self.ws, self.backend, self.dist = ws, backend, dist
+        if ws > 1:
+            dist.init_process_group(backend)
+
+    def barrier(self):
+        if self.ws > 1:
+            self.dist.barrier()
+
+    def max(self, x):
+        if self.ws == 1:
+            return x
+        import torch
+        t = torch.tensor([float(x)], device="cuda" if self.backend == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.ws > 1:
+            self.dist.destroy_process_group()
+
+
 def run_ours(args):
     import numpy as np
     import torch
-    import torch.distributed as dist
 
     import __graft_entry__
     from paper_2209_13121_gb300 import rsx, synth
 
     ws, rank, local = _dist()
-    if ws > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+    ndev = torch.cuda.device_count()
+    dev = local % ndev
+    ranks = _Ranks(ws, "nccl" if ws <= ndev else "gloo")
+    torch.cuda.set_device(dev)
     if rank == 0:
         __graft_entry__.build()
-    if ws > 1:
-        dist.barrier()
+    ranks.barrier()
     __graft_entry__.build()
 
     W = WORKLOADS[args.workload]
     nz, ny, nx = W["shape"]
-    c = W["c"]
+    c = args.components or W["c"]
     prec = args.precision
     real = 4 if prec == 32 else 8
     n_ang = rsx.angle_count(*W["angles"])
     n_steps = args.warmup + args.steps
-    # 150 energies over 270..320 eV (Sec. 6.1), sharded across ranks with no
-    # data-path collective; each step is one energy of this rank's shard.
+    # the workload's energies (Sec. 6.1: 150 over 270..320 eV), sharded
+    # across ranks with no data-path collective; each step is one energy of
+    # this rank's shard (repeated when the shard is shorter than the run).
     from paper_2209_13121_gb300.shard import energy_shard
-    energies_all = synth.energies_uniform(150)
-    shard = energy_shard(150, rank, ws, "strided")
+    n_e, e_lo, e_hi = W["energies"]
+    energies_all = synth.energies_uniform(n_e, e_lo, e_hi)
+    shard = energy_shard(n_e, rank, ws, "strided")
+    if len(shard) == 0:
+        shard = [rank % n_e]
     mine = [energies_all[shard[i % len(shard)]] for i in range(n_steps)]
     K = synth.optical_constants(mine, c, seed=2)
     M = synth.morphology_random_torch((nz, ny, nx), c, seed=1, device="cuda",
                                       dtype=torch.float32 if prec == 32 else torch.float64)
-    ctx = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm)
+    ctx = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm,
+                      angle_batch=args.angle_batch)
+    angle_batch = ctx.angle_batch
     ctx.set_morphology(M)
     ctx.set_optical_constants(mine, K)
     out = torch.empty((1, ny, nx), device="cuda", dtype=M.dtype)
@@ -167,10 +233,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     ctx.phase_times()  # discard
     ctx.set_timing(True)
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(dev)
     clocks.start()
-    if ws > 1:
-        dist.barrier()
+    ranks.barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -178,16 +243,15 @@ def run_ours(args):
         step(i)
     ev1.record(stream)
     torch.cuda.synchronize()
-    if ws > 1:
-        dist.barrier()
+    # the timed runs wrote device output asynchronously: a pipelined kernel
+    # that ran out of a bounded wait would make them invalid (raises)
+    ctx.check()
+    ranks.barrier()
     ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     phases = ctx.phase_times()
     ctx.set_timing(False)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = ranks.max(ms)
 
     N = nx * ny * nz
     units = N * n_ang * args.steps * ws
@@ -213,6 +277,13 @@ def run_ours(args):
         src_bytes = c * 4 * real if args.algorithm == 1 else 5 * cplx  # M, or N_t's 5 entries
         per_voxel = {"pol_fftx": src_bytes + 3 * cplx, "ffty": y_bytes, "ewald": z_bytes,
                      "rotate": 0, "other": 0, "nt": c * 4 * real + 5 * cplx}
+    kx = angle_batch if args.algorithm == 1 else 1
+    if kx > 1:
+        # the x pass reads the morphology once per batch of kx angles and
+        # writes every angle's p: per launch, on average over the energy's
+        # ceil(n_ang / kx) launches
+        n_x = -(-n_ang // kx)
+        per_voxel["pol_fftx"] = (src_bytes * n_x + 3 * cplx * n_ang) / n_x
     bytes_per_voxel = per_voxel[top]
     t_ms, n_l = phases[top]
     if args.algorithm == 3 and top == "ewald":
@@ -225,7 +296,10 @@ def run_ours(args):
         t_ms, n_l = phases[top]
         bytes_per_voxel = per_voxel[top]
         achieved = (bytes_per_voxel * N * n_l) / (t_ms / 1e3) / 1e9 if n_l else None
-    traffic = _traffic_from_profiles(args.workload, top, prec) if args.algorithm == 1 else None
+    # DRAM bytes per launch from an ncu capture of this kernel (the
+    # multi-angle x pass is recorded per batch size)
+    tkey = f"{top}-k{kx}" if (top == "pol_fftx" and kx > 1) else top
+    traffic = _traffic_from_profiles(args.workload, tkey, prec) if args.algorithm == 1 else None
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s",
                 "frac": (achieved / peak) if achieved else None, "traffic": traffic,
@@ -259,8 +333,8 @@ def run_ours(args):
         del M
         ctx.close()
         torch.cuda.empty_cache()
-        ctxs = [rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm)
-                for _ in range(2)]
+        ctxs = [rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm,
+                            angle_batch=args.angle_batch) for _ in range(2)]
         for cx in ctxs:
             cx.set_optical_constants(mine, K)
         streams = [torch.cuda.Stream(), torch.cuda.Stream()]
@@ -287,16 +361,11 @@ def run_ours(args):
         h2d_gbs = Mh_np.nbytes / (e0.elapsed_time(e1) / 1e3) / 1e9
         del dbuf
         torch.cuda.empty_cache()
-        if ws > 1:
-            dist.barrier()
+        ranks.barrier()
         t0 = time.perf_counter()
         e2e_steps(args.warmup, n_steps)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if ws > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = ranks.max(time.perf_counter() - t0)
         e2e = {"value": units / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(Mh_np.nbytes), "d2h_bytes_per_step": int(host_out.nbytes),
                "h2d_gbs": round(h2d_gbs, 1)}
@@ -312,10 +381,12 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: Algorithm {args.algorithm}, {nx}x{ny}x{nz} voxels, "
-                                   f"c={c}, 91 e-field angles 0:2:180 per energy, one energy "
-                                   f"per step (of 150 over 270-320 eV)",
+                                   f"c={c}, {n_ang} e-field angles 0:2:180 per energy, one energy "
+                                   f"per step (of {n_e} over {e_lo:g}-{e_hi:g} eV)",
                        "voxels": N, "components": c, "angles_per_energy": n_ang,
+                       "angle_batch": angle_batch,
                        "precision": prec, "parallelism": f"energy-sharded x{ws}",
+                       "ranks_per_gpu": -(-ws // ndev),
                        "l2": f"inputs larger than L2 (morphology {N * c * 4 * real / 1e9:.1f} GB)"},
             "roofline": roofline,
             "phases_ms": {k: round(v[0], 3) for k, v in phases.items()},
@@ -324,10 +395,9 @@ def run_ours(args):
             "e2e": e2e,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(W, args)
+            line["cpu_baseline"] = cpu_baseline(W, args, c)
         print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+    ranks.close()
 
 
 def _traffic_from_profiles(workload, kernel, prec):
@@ -345,30 +415,105 @@ def _traffic_from_profiles(workload, kernel, prec):
     return None
 
 
-def cpu_baseline(W, args, angles_sample=10):
-    """The FP64 oracle, as it stands, on a bounded sample of the workload:
-    128 x 128 x 16 voxels with the same c, one energy, the first
-    `angles_sample` angles of 0:2:180.  Voxel-angle/s scales linearly in N
-    (Sec. 6.1), so the sample's throughput stands for the workload's."""
+def _oracle_angles(job):
+    """Worker of the CPU baseline: the oracle's Algorithm 1 inner loop for a
+    list of angles of one energy, summed (runs in a spawned process)."""
+    shape, c, seed_m, seed_k, E, alphas = job
     import numpy as np
 
     from oracle import cyrsoxs_oracle as O
     from paper_2209_13121_gb300 import synth
-
-    shape = (16, 128, 128)
-    c = W["c"]
-    M = synth.morphology_random(shape, c, seed=1, dtype=np.float64)
-    K = synth.optical_constants([285.0], c, seed=2)
-    alphas = O.angle_list(*W["angles"])[:angles_sample]
-    t0 = time.perf_counter()
+    M = synth.morphology_random(shape, c, seed=seed_m, dtype=np.float64)
+    K = synth.optical_constants([E], c, seed=seed_k)
     acc = np.zeros(shape[1:])
     for a in alphas:
-        acc += O.rotate_image(O.scatter_one_angle(M, K[0], 285.0, VOXEL_NM, a), a)
-    dt = time.perf_counter() - t0
-    units = math.prod(shape) * len(alphas)
-    return {"value": units / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle, {shape[2]}x{shape[1]}x{shape[0]} voxels, c={c}, "
-                      f"1 energy x {len(alphas)} of the 91 angles, {dt:.1f} s"}
+        acc += O.rotate_image(O.scatter_one_angle(M, K[0], E, VOXEL_NM, a), a)
+    return acc
+
+
+def time_oracle(shape, c, angles_deg, n_angles, cores):
+    """Wall time of the FP64 oracle (as it stands) over the first n_angles
+    angles of one energy of a seeded morphology, on `cores` processes
+    (spawned, each a share of the angles; cores = 1 runs in this process).
+    Returns (voxel-angle/s in G units, seconds)."""
+    import multiprocessing as mp
+
+    import numpy as np
+
+    from oracle import cyrsoxs_oracle as O
+    alphas = list(O.angle_list(*angles_deg)[:n_angles])
+    jobs = [(shape, c, 1, 2, 285.0, alphas[i::cores]) for i in range(cores)]
+    jobs = [j for j in jobs if j[-1]]
+    if cores == 1:
+        t0 = time.perf_counter()
+        _oracle_angles(jobs[0])
+        dt = time.perf_counter() - t0
+    else:
+        with mp.get_context("spawn").Pool(len(jobs)) as pool:
+            pool.map(_oracle_angles, [(shape, c, 1, 2, 285.0, alphas[:1])] * len(jobs))  # warm
+            t0 = time.perf_counter()
+            parts = pool.map(_oracle_angles, jobs)
+            dt = time.perf_counter() - t0
+        np.sum(parts, axis=0)
+    return math.prod(shape) * len(alphas) / dt / 1e9, dt
+
+
+def _host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(W, args, c):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    128 x 128 x 16 voxels with the same c and one energy; all 91 angles on
+    every host core (one spawned process per core, each a share of the
+    angles), and 8 angles on one core beside it.  Voxel-angle/s scales
+    linearly in N (Sec. 6.1), so the sample's throughput stands for the
+    workload's."""
+    shape = (16, 128, 128)
+    cores = _host_cores()
+    v_all, t_all = time_oracle(shape, c, W["angles"], 91, cores)
+    v_one, t_one = time_oracle(shape, c, W["angles"], 8, 1)
+    return {"value": v_all, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "single_core_value": v_one,
+            "sample": f"FP64 numpy oracle, {shape[2]}x{shape[1]}x{shape[0]} voxels, c={c}, 1 energy: "
+                      f"91 angles on {cores} processes in {t_all:.1f} s; 8 angles on 1 core in "
+                      f"{t_one:.1f} s"}
+
+
+def cpu_report(args):
+    """The oracle's CPU baselines of the survey's plan: 128^2 x 16 and
+    256^2 x 32 (c = 4) and the 2048^2 x 1 film (c = 2), one energy and the 91
+    angles of 0:2:180, on one core and on every host core; seconds per
+    energy extrapolate linearly to the workloads' energy counts."""
+    cores = _host_cores()
+    rows = []
+    for shape, c, n_one in (((16, 128, 128), 4, 91), ((32, 256, 256), 4, 23),
+                            ((1, 2048, 2048), 2, 12)):
+        v1, t1 = time_oracle(shape, c, (0.0, 2.0, 180.0), n_one, 1)
+        va, ta = time_oracle(shape, c, (0.0, 2.0, 180.0), 91, cores)
+        n = math.prod(shape)
+        rows.append({"shape_zyx": shape, "components": c, "voxels": n,
+                     "single_core": {"angles_timed": n_one, "s": round(t1, 2),
+                                     "value": v1, "s_per_energy": round(n * 91 / v1 / 1e9, 2)},
+                     "all_cores": {"cores": cores, "angles_timed": 91, "s": round(ta, 2),
+                                   "value": va, "s_per_energy": round(ta, 2)}})
+    print(json.dumps({"kind": "oracle CPU baselines", "unit": UNIT, "host_cores": cores,
+                      "rows": rows}), flush=True)
+
+
+def check_launcher(args):
+    """The multi-rank control plane without a GPU: each rank (gloo) reports
+    a different time, rank 0 prints the world size and the maximum."""
+    ws, rank, _ = _dist()
+    ranks = _Ranks(ws, "gloo")
+    ranks.barrier()
+    t = ranks.max(1.0 + rank)
+    if rank == 0:
+        print(json.dumps({"n_gpus": ws, "max_ms": t, "rank": rank}), flush=True)
+    ranks.close()
 
 
 def run_reference(args):
@@ -378,22 +523,25 @@ def run_reference(args):
     if rank != 0:
         return
     W = WORKLOADS[args.workload]
-    vals = []
+    c = args.components or W["c"]
+    shape = (16, 128, 128)
+    cores = _host_cores()
     for _ in range(args.warmup):
-        cpu_baseline(W, args, angles_sample=2)
+        time_oracle(shape, c, W["angles"], cores, cores)
     t0 = time.perf_counter()
-    samples = [cpu_baseline(W, args, angles_sample=4) for _ in range(args.steps)]
+    samples = [time_oracle(shape, c, W["angles"], 2 * cores, cores) for _ in range(args.steps)]
     dt = time.perf_counter() - t0
-    vals = [s["value"] for s in samples]
-    value = statistics.mean(vals)
+    value = statistics.mean(v for v, _ in samples)
+    sample = (f"FP64 numpy oracle, 128x128x16 voxels, c={c}, 1 energy x {2 * cores} of the 91 "
+              f"angles per step on {cores} processes")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload} (oracle on a bounded sample per step)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": samples[0]["sample"]},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -409,14 +557,34 @@ def main():
     ap.add_argument("--algorithm", type=int, default=1, choices=[1, 2, 3],
                     help="1: Algorithm 1 (headline); 2: Algorithm 2 (N_t); 3: Algorithm 2 "
                          "restated by linearity (five FFTs per energy), reported beside")
+    ap.add_argument("--angle-batch", type=int, default=0,
+                    help="Algorithm 1: e-field angles per read of the morphology (0: the "
+                         "library default)")
+    ap.add_argument("--components", type=int, default=0,
+                    help="material count c (0: the workload's; Sec. 6.2 sweeps 2..10)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-report", action="store_true",
+                    help="time the oracle on this host (single core and all cores) and exit")
+    ap.add_argument("--check-launcher", action="store_true",
+                    help="run the multi-rank control plane only (gloo, no GPU)")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "ours":
-        print("note: fewer than 3 warm-up steps", file=sys.stderr)
-    if args.impl == "reference":
+    if "WORLD_SIZE" in os.environ:
+        if args.gpus not in (1, int(os.environ["WORLD_SIZE"])):
+            raise SystemExit(f"--gpus {args.gpus} disagrees with WORLD_SIZE={os.environ['WORLD_SIZE']}")
+    elif args.gpus > 1:
+        sys.exit(launch_ranks(args.gpus, sys.argv[1:]))
+    if args.cpu_report:
+        cpu_report(args)
+    elif args.check_launcher:
+        check_launcher(args)
+    elif args.impl == "reference":
+        if args.warmup < 3:
+            print("note: fewer than 3 warm-up steps", file=sys.stderr)
         run_reference(args)
     else:
+        if args.warmup < 3:
+            print("note: fewer than 3 warm-up steps", file=sys.stderr)
         run_ours(args)
 
 

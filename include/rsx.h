@@ -27,8 +27,11 @@
  *  - Detector images are [ny][nx] Real in fftshift order: the pixel (iy, ix)
  *    holds q = (2 pi (ix - nx/2) / (nx D), 2 pi (iy - ny/2) / (ny D)), with D
  *    the voxel edge in nm and integer division.
- *  - Supported sizes: nx and ny powers of two in [1, 4096], nz in [1, 65535],
- *    1 <= n_components <= RSX_MAX_COMPONENTS.
+ *  - Supported sizes: nx and ny in [1, 4096], nz in [1, 65535],
+ *    1 <= n_components <= RSX_MAX_COMPONENTS.  Any nx and ny are
+ *    transformed exactly (mixed-radix passes; a prime factor p above 7 costs
+ *    an O(p) pass per element); the fastest kernels serve FP32 grids with nx
+ *    and ny 512 or 1024.
  */
 #ifndef RSX_H
 #define RSX_H
@@ -74,12 +77,24 @@ typedef struct rsx_config {
   int validate;       /* nonzero: rsx_set_morphology rejects v or s outside */
                       /* [0, 1] and non-finite angles (Sec. 3.1); the sum   */
                       /* of v over components is never checked.             */
+  int angle_batch;    /* Algorithm 1: e-field angles whose p is formed from  */
+                      /* one read of the morphology (1..RSX_MAX_ANGLE_BATCH; */
+                      /* 0 = RSX_DEFAULT_ANGLE_BATCH).  Each extra angle     */
+                      /* holds another 3 N complex p buffer.  Used on FP32   */
+                      /* grids with nx and ny 512 or 1024, nx a multiple of  */
+                      /* 16 and nz a power of two up to 1024; elsewhere 1.   */
+                      /* Each angle's arithmetic is unchanged (Algorithm 1's */
+                      /* angle loop, the morphology sums shared).            */
 } rsx_config;
+
+#define RSX_MAX_ANGLE_BATCH 8
+#define RSX_DEFAULT_ANGLE_BATCH 4
 
 typedef struct rsx_context rsx_context;
 
 /* Create a context for one grid and material count.  Allocates the device
- * workspace: 3 N complex for p, two nx*ny Real images, per-pixel Ewald
+ * workspace: 3 N complex for p (times the angle batch), two nx*ny Real
+ * images, per-pixel Ewald
  * geometry, FFT twiddle tables, for Algorithms 2 and 3 the stored N_t entries
  * (Table 2) and, for FP32 grids with ny = 1024, nx a multiple of 16 and nz a
  * power of two up to 1024, the two q_z bins per pixel of the fused y-FFT +
@@ -100,6 +115,10 @@ const char* rsx_last_error(void);
  * (Tables 1 and 2, plus the buffers listed under rsx_create).  Returns 0 for
  * an invalid cfg. */
 size_t rsx_workspace_bytes(const rsx_config* cfg);
+
+/* The angle batch in effect for ctx (rsx_config.angle_batch after the
+ * default and the shape rules above), or -1 for a NULL context. */
+int rsx_angle_batch(const rsx_context* ctx);
 
 /* Number of e-field angles in the inclusive list start:increment:end
  * (degrees, Algorithm 1 "E_Angle [start, increment, end]"); 1 when rotation
@@ -144,9 +163,10 @@ int rsx_set_optical_constants(rsx_context* ctx, int n_energies, const double* en
  * Host output is staged and copied into `out` only after the stream has
  * finished every energy and no pipelined kernel reported a timeout, so a
  * failing call leaves it untouched.  Device output is written in stream
- * order, energy by energy: a launch that fails part-way leaves the rows of
- * the energies already finished written, and a pipeline timeout is
- * reported by the next call with host output (rsx_set_wait_limit). */
+ * order, energy by energy, and the call returns before the GPU is done: a
+ * launch that fails part-way leaves the rows of the energies already
+ * finished written, and a pipeline timeout (rsx_set_wait_limit) is reported
+ * by the next rsx_check, or by the next call with host output. */
 int rsx_run(rsx_context* ctx, double start_deg, double increment_deg, double end_deg,
             int rotation, const int* energy_idx, int n_sel, void* out, int where,
             void* stream);
@@ -175,6 +195,18 @@ int rsx_set_timing(rsx_context* ctx, int enable);
  * run out at once, so the failure path can be exercised without any fault.
  * Values above 2^32 - 1 are clamped.  The context stays usable afterwards. */
 int rsx_set_wait_limit(rsx_context* ctx, long long polls);
+
+/* Completion check for the asynchronous calls (device-output rsx_run,
+ * rsx_scatter_angle, the single steps): synchronises `stream`, then reads
+ * and clears the context's kernel error flag.  Returns RSX_OK when no
+ * pipelined kernel of this context ran out of a bounded wait since the flag
+ * was last read; otherwise RSX_ERR_CUDA ("a kernel pipeline wait timed
+ * out"): every device result written since then is not valid, and the
+ * per-energy data the context caches (Algorithm 2's N_t, the linearity
+ * path's bins, the Ewald geometry) is dropped so the next call recomputes
+ * it.  The context stays usable.  (The paper runs synchronously and has no
+ * counterpart.) */
+int rsx_check(rsx_context* ctx, void* stream);
 
 /* Waits for the recorded events, writes the summed device time of each
  * phase in ms to ms[RSX_N_PHASES] and the number of kernel launches to

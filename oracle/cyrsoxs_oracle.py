@@ -314,6 +314,65 @@ def rotate_image(img: np.ndarray, alpha: float) -> np.ndarray:
     return out
 
 
+def rotate_sampled(pixel_fn, shape2, alpha: float, oy, ox) -> np.ndarray:
+    """rotate_image evaluated only at the output pixels (oy, ox) (fftshift
+    order): the same source positions and bilinear weights (R6), with the
+    unrotated image read through pixel_fn(sy, sx) -> values at fftshift-order
+    pixels (called once, on the in-grid corners)."""
+    Ny, Nx = shape2
+    cx, cy = Nx // 2, Ny // 2
+    ca, sa = math.cos(alpha), math.sin(alpha)
+    ix = np.asarray(ox, dtype=np.float64)
+    iy = np.asarray(oy, dtype=np.float64)
+    fx = cx + ca * (ix - cx) - sa * (Nx / Ny) * (iy - cy)
+    fy = cy + sa * (Ny / Nx) * (ix - cx) + ca * (iy - cy)
+    x0 = np.floor(fx)
+    y0 = np.floor(fy)
+    tx = fx - x0
+    ty = fy - y0
+    x0 = x0.astype(np.int64)
+    y0 = y0.astype(np.int64)
+    corners = []
+    for dy, wy in ((0, 1.0 - ty), (1, ty)):
+        for dx, wx in ((0, 1.0 - tx), (1, tx)):
+            xx, yy = x0 + dx, y0 + dy
+            ok = (xx >= 0) & (xx < Nx) & (yy >= 0) & (yy < Ny)
+            corners.append((yy, xx, wy * wx, ok))
+    sy = np.concatenate([c[0][c[3]] for c in corners])
+    sx = np.concatenate([c[1][c[3]] for c in corners])
+    vals = np.asarray(pixel_fn(sy, sx), dtype=np.float64) if sy.size else np.zeros(0)
+    out = np.zeros(ix.shape)
+    pos = 0
+    for yy, xx, wt, ok in corners:
+        n = int(ok.sum())
+        contrib = np.zeros(ix.shape)
+        contrib[ok] = vals[pos:pos + n]
+        pos += n
+        out += wt * contrib
+    return out
+
+
+def run_alg1_sparse_pixels(sparse, shape, constants_e, E_eV, voxel_nm, angles_deg, oy, ox,
+                           rotation=True, uT_mode="literal") -> np.ndarray:
+    """Algorithm 1's Ewald_Avg for one energy at the output pixels (oy, ox)
+    (fftshift order) of a vacuum-plus-sparse morphology: for each angle the
+    unrotated image is evaluated (scatter_sparse_pixels) at the corners the
+    rotation reads (rotate_sampled), then averaged over the angles."""
+    Nz, Ny, Nx = shape
+    alphas = angle_list(*angles_deg, rotation=rotation)
+    acc = np.zeros(np.asarray(ox).shape)
+    for a in alphas:
+        def pix(sy, sx, a=a):
+            return scatter_sparse_pixels(sparse, shape, constants_e, E_eV, voxel_nm, a,
+                                         np.mod(sy - Ny // 2, Ny), np.mod(sx - Nx // 2, Nx),
+                                         uT_mode)
+        if rotation:
+            acc += rotate_sampled(pix, (Ny, Nx), a, oy, ox)
+        else:
+            acc += pix(np.asarray(oy), np.asarray(ox))
+    return acc / len(alphas)
+
+
 def angle_list(start_deg: float, inc_deg: float, end_deg: float,
                rotation: bool = True) -> np.ndarray:
     """E_Angle = [start, increment, end] in degrees -> radians (R7).

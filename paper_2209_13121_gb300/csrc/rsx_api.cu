@@ -46,8 +46,6 @@ int cuda_fail(cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(e_, what); \
   } while (0)
 
-bool is_pow2(long long n) { return n >= 1 && (n & (n - 1)) == 0; }
-
 const double kPi = 3.14159265358979323846264338327950288;
 const double kHcEvNm = 1239.84198;  // lambda = hc / E
 
@@ -67,9 +65,8 @@ struct DeviceGuard {
 
 int check_config(const rsx_config* c) {
   if (!c) return fail(RSX_ERR_INVALID, "config is NULL");
-  if (!is_pow2(c->nx) || c->nx > 4096 || !is_pow2(c->ny) || c->ny > 4096)
-    return fail(RSX_ERR_INVALID, "nx=%d, ny=%d: each must be a power of two in [1, 4096]", c->nx,
-                c->ny);
+  if (c->nx < 1 || c->nx > 4096 || c->ny < 1 || c->ny > 4096)
+    return fail(RSX_ERR_INVALID, "nx=%d, ny=%d: each must lie in [1, 4096]", c->nx, c->ny);
   if (c->nz < 1 || c->nz > 65535) return fail(RSX_ERR_INVALID, "nz=%d outside [1, 65535]", c->nz);
   if (c->n_components < 1 || c->n_components > RSX_MAX_COMPONENTS)
     return fail(RSX_ERR_INVALID, "n_components=%d outside [1, %d]", c->n_components,
@@ -82,6 +79,9 @@ int check_config(const rsx_config* c) {
     return fail(RSX_ERR_INVALID, "algorithm=%d: must be 1, 2 or 3", c->algorithm);
   if (c->frame != RSX_FRAME_LITERAL && c->frame != RSX_FRAME_LAB)
     return fail(RSX_ERR_INVALID, "frame=%d: must be RSX_FRAME_LITERAL or RSX_FRAME_LAB", c->frame);
+  if (c->angle_batch < 0 || c->angle_batch > RSX_MAX_ANGLE_BATCH)
+    return fail(RSX_ERR_INVALID, "angle_batch=%d outside [0, %d]", c->angle_batch,
+                RSX_MAX_ANGLE_BATCH);
   return RSX_OK;
 }
 
@@ -96,7 +96,29 @@ size_t geo_size(int precision) {
 namespace rsx {
 // Lets other translation units of the library report through rsx_last_error.
 void set_last_error(const char* msg) { g_err = msg; }
+
+int check_device_pointer(const void* p, int dev, const char* what) {
+  if (!p) return fail(RSX_ERR_INVALID, "%s is NULL", what);
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear the error an unknown pointer leaves behind
+    return fail(RSX_ERR_INVALID, "%s is not a CUDA device pointer", what);
+  }
+  if (at.type == cudaMemoryTypeManaged) return RSX_OK;
+  if (at.type != cudaMemoryTypeDevice)
+    return fail(RSX_ERR_INVALID, "%s is host memory, not device memory", what);
+  if (at.device != dev)
+    return fail(RSX_ERR_INVALID, "%s lives on device %d, the work runs on device %d", what,
+                at.device, dev);
+  return RSX_OK;
+}
 }  // namespace rsx
+
+#define RSX_DEVPTR(ptr, dev, what)                                   \
+  do {                                                               \
+    const int rc_ = rsx::check_device_pointer((ptr), (dev), (what)); \
+    if (rc_) return rc_;                                             \
+  } while (0)
 
 struct rsx_context {
   rsx_config cfg{};
@@ -105,7 +127,8 @@ struct rsx_context {
   void* M_owned = nullptr;  // device copy of a host morphology
   const void* M = nullptr;  // morphology in use (owned or borrowed)
   std::vector<double> energies, constants;
-  void* p = nullptr;    // 3 N complex workspace
+  void* p = nullptr;    // kx x 3 N complex workspace (one p per angle of a batch)
+  int kx = 1;           // angle batch of the Algorithm 1 x pass
   void* img = nullptr;  // one detector image
   void* acc = nullptr;  // running sum of rotated images
   void* geo = nullptr;  // per-pixel Ewald geometry of energy geo_energy
@@ -133,7 +156,7 @@ struct rsx_context {
   // buffers for the TMA y pass (FP32, ny = 1024); valid when the flag is set
   CUtensorMap tmap_p;
   CUtensorMap tmap_ft;
-  CUtensorMap tmap_pz;   // p for the fused y+z pass
+  CUtensorMap tmap_pz[RSX_MAX_ANGLE_BATCH];  // each angle's p for the fused y+z pass
   CUtensorMap tmap_ftz;  // ft (five N_t entries) for the fused y+z pass
   bool has_tmap_p = false, has_tmap_ft = false, has_tmap_pz = false, has_tmap_ftz = false;
   // bins of the fused y-FFT + pruned z pass (FP32, Algorithms 1 and 2):
@@ -494,7 +517,7 @@ int scatter_angle(rsx_context* c, int ie, double alpha, void* img, cudaStream_t 
       long long L = 0;
       {
         PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-        RSX_CK(fused_yz(c, &c->tmap_pz, 3, &L, s), "y-FFT + z-bins kernel");
+        RSX_CK(fused_yz(c, &c->tmap_pz[0], 3, &L, s), "y-FFT + z-bins kernel");
       }
       PhaseTimer pt(c, RSX_PHASE_EWALD, s);
       RSX_CK(rsx::launch_ewald_bins(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
@@ -525,6 +548,20 @@ int check_energy(const rsx_context* c, int ie) {
   if (ie < 0 || ie >= (int)c->energies.size())
     return fail(RSX_ERR_INVALID, "energy index %d outside [0, %d)", ie, (int)c->energies.size());
   return RSX_OK;
+}
+
+// Reads and clears the kernel error flag (the caller has synchronised the
+// work it covers).  When it was set, per-energy data an aborted kernel may
+// have produced is dropped and RSX_ERR_CUDA returned.
+int take_kernel_error(rsx_context* c) {
+  int h = 0;
+  RSX_CK(cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost), "kernel error flag");
+  if (!h) return RSX_OK;
+  RSX_CK(cudaMemset(c->err, 0, sizeof(int)), "kernel error flag");
+  c->nt_energy = -1;
+  c->bins_energy = -1;
+  c->geo_energy = -1;
+  return fail(RSX_ERR_CUDA, "a kernel pipeline wait timed out; the result is not valid");
 }
 
 bool host_morphology_ok(const void* M, int prec, long long n) {
@@ -560,6 +597,15 @@ static size_t part_bytes(const rsx_config* cfg) {
   return rsx::kYzSlots * (size_t)(cfg->algorithm == 3 ? 5 : 3) * cfg->nx * cfg->ny * 16;
 }
 
+// The angle batch a config gets: the multi-angle x pass serves FP32
+// Algorithm 1 on the shapes of the bulk-copy x pass and the fused y+z pass.
+static int angle_batch_of(const rsx_config* cfg) {
+  const bool ok = cfg->precision == 32 && cfg->algorithm == 1 &&
+                  (cfg->nx == 1024 || cfg->nx == 512) && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
+  if (!ok) return 1;
+  return cfg->angle_batch == 0 ? RSX_DEFAULT_ANGLE_BATCH : cfg->angle_batch;
+}
+
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
   if (check_config(cfg) != RSX_OK) return 0;
   const long long N = (long long)cfg->nx * cfg->ny * cfg->nz;
@@ -570,7 +616,7 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
                  ? (size_t)cfg->n_components * N * 4 * R  // morphology copy (Table 1: 4c N)
                  : 5 * (size_t)N * Cs + 2 * (size_t)stage_vox * 4 * R;  // N_t + staging (Table 2)
   if (cfg->algorithm == 3) b += 5 * (size_t)N * Cs + 10 * (size_t)npix * Cs;  // FFT'd N_t, bins
-  b += 3 * (size_t)N * Cs;                           // p_x, p_y, p_z (Table 1: 6 N)
+  b += 3 * (size_t)N * Cs * angle_batch_of(cfg);     // p_x, p_y, p_z (Table 1: 6 N) per angle
   b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
   b += (size_t)npix * geo_size(cfg->precision);
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
@@ -578,6 +624,8 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
   if (cfg->algorithm == 3) b += (size_t)rsx::kMaxAngleBatch * npix * R;  // a batch of images
   return b;
 }
+
+int rsx_angle_batch(const rsx_context* c) { return c ? c->kx : -1; }
 
 int rsx_angle_count(double start, double inc, double end, int rotation) {
   if (!rotation) return 1;
@@ -598,6 +646,7 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
   c->cfg = *cfg;
   c->N = (long long)cfg->nx * cfg->ny * cfg->nz;
   c->npix = (long long)cfg->nx * cfg->ny;
+  c->kx = angle_batch_of(cfg);
   cudaError_t e = cudaGetDevice(&c->dev);
   if (e != cudaSuccess) {
     delete c;
@@ -609,7 +658,7 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     size_t bytes;
     const char* what;
   } allocs[] = {
-      {&c->p, 3 * (size_t)c->N * Cs, "p workspace"},
+      {&c->p, 3 * (size_t)c->N * Cs * c->kx, "p workspace"},
       {&c->img, (size_t)c->npix * R, "Ewald image"},
       {&c->acc, (size_t)c->npix * R, "Ewald average"},
       {&c->geo, (size_t)c->npix * geo_size(cfg->precision), "Ewald geometry"},
@@ -667,8 +716,11 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     // read the halves of each 128-byte line at once, 512-row tiles are 16
     // columns (whole lines); promote to 128 bytes, not 256
     const unsigned box = cfg->ny == 512 ? 32 : 16;
-    c->has_tmap_pz =
-        make_tmap(c, c->p, 3, &c->tmap_pz, box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+    c->has_tmap_pz = true;
+    for (int k = 0; k < c->kx; ++k)
+      c->has_tmap_pz = c->has_tmap_pz &&
+                       make_tmap(c, (char*)c->p + (size_t)k * 3 * c->N * Cs, 3, &c->tmap_pz[k],
+                                 box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
     if (c->ft)
       c->has_tmap_ftz =
           make_tmap(c, c->ft, 5, &c->tmap_ftz, box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
@@ -742,6 +794,7 @@ int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
     c->bins_energy = -1;
     return RSX_OK;
   }
+  RSX_DEVPTR(M, c->dev, "device morphology");
   if (((uintptr_t)M) % (4 * real_size(prec)) != 0)
     return fail(RSX_ERR_INVALID, "device morphology must be aligned to %d bytes",
                 (int)(4 * real_size(prec)));
@@ -783,6 +836,7 @@ int rsx_polarization(rsx_context* c, int ie, double alpha, void* p_out, void* st
   if (rc) return rc;
   if ((rc = check_energy(c, ie))) return rc;
   if (!p_out) return fail(RSX_ERR_INVALID, "p_out is NULL");
+  RSX_DEVPTR(p_out, c->dev, "p_out");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   const rsx_config& g = c->cfg;
@@ -822,7 +876,7 @@ int fft3d_impl(rsx_context* c, void* p, cudaStream_t s) {
   RSX_CK(rsx::launch_col_fft<R>(p, g.ny, g.nx, g.nx, {3LL * g.nz, g.nz, c->N, c->npix, 0}, c->twy, s),
          "y-FFT kernel");
   if (g.nz == 1) return RSX_OK;
-  if (is_pow2(g.nz) && g.nz <= 4096) {
+  if (g.nz <= 4096) {
     RSX_CK(rsx::launch_col_fft<R>(p, g.nz, c->npix, c->npix, {3, 1, c->N, 0, 0}, c->twz, s),
            "z-FFT kernel");
   } else {
@@ -838,6 +892,7 @@ int rsx_fft3d(rsx_context* c, void* p, void* stream) {
   if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
   if (!p) return fail(RSX_ERR_INVALID, "p is NULL");
   if (p == c->p) return fail(RSX_ERR_INVALID, "p must be a caller buffer");
+  RSX_DEVPTR(p, c->dev, "p");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   return c->cfg.precision == 32 ? fft3d_impl<float>(c, p, s) : fft3d_impl<double>(c, p, s);
@@ -849,6 +904,8 @@ int rsx_ewald(rsx_context* c, int ie, const void* pt, void* img, void* stream) {
   int rc = check_energy(c, ie);
   if (rc) return rc;
   if (!pt || !img) return fail(RSX_ERR_INVALID, "NULL buffer");
+  RSX_DEVPTR(pt, c->dev, "p_tilde");
+  RSX_DEVPTR(img, c->dev, "img_out");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   const rsx_config& g = c->cfg;
@@ -872,6 +929,8 @@ int rsx_rotate_accumulate(rsx_context* c, const void* img, double alpha, void* a
   if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
   if (!img || !acc) return fail(RSX_ERR_INVALID, "NULL buffer");
   if (!isfinite(alpha)) return fail(RSX_ERR_INVALID, "alpha not finite");
+  RSX_DEVPTR(img, c->dev, "img");
+  RSX_DEVPTR(acc, c->dev, "acc");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   const rsx_config& g = c->cfg;
@@ -887,6 +946,7 @@ int rsx_scatter_angle(rsx_context* c, int ie, double alpha, void* img, void* str
   if ((rc = check_energy(c, ie))) return rc;
   if (!img) return fail(RSX_ERR_INVALID, "img_out is NULL");
   if (!isfinite(alpha)) return fail(RSX_ERR_INVALID, "alpha not finite");
+  RSX_DEVPTR(img, c->dev, "img_out");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   return c->cfg.precision == 32 ? scatter_angle<float>(c, ie, alpha, img, s)
@@ -896,9 +956,68 @@ int rsx_scatter_angle(rsx_context* c, int ie, double alpha, void* img, void* str
 namespace {
 // All angles of one energy, one after the other: the image of each angle
 // (scatter_angle), rotated into the average.
+// Algorithm 1 with the morphology read once per batch of kx angles: the
+// multi-angle x pass writes each angle's x-transformed p to its own buffer,
+// then every angle of the batch goes through the fused y+z pass, the Ewald
+// image and the rotation into the average, in angle order.
+int run_energy_angles_batched(rsx_context* c, int ie, double start, double inc, int nang,
+                              int rotation, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  int rc = ensure_geo<float>(c, ie, s);
+  if (rc) return rc;
+  const PolParams<float> pp = make_params<float>(c, ie, 0.0, 0);
+  const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
+  const void* tw = g.nx == 1024 ? c->tw4 : c->twx;
+  for (int a0 = 0; a0 < nang; a0 += c->kx) {
+    const int nk = nang - a0 < c->kx ? nang - a0 : c->kx;
+    rsx::XAngles ang;
+    memset(&ang, 0, sizeof(ang));
+    ang.n = nk;
+    double alpha[RSX_MAX_ANGLE_BATCH];
+    for (int k = 0; k < nk; ++k) {
+      alpha[k] = rotation ? (start + inc * (a0 + k)) * (kPi / 180.0) : 0.0;
+      ang.ce[k] = (float)cos(alpha[k]);
+      ang.se[k] = (float)sin(alpha[k]);
+    }
+    {
+      PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
+      RSX_CK(rsx::launch_pol_fft4s_tma_multi(c->M, g.nx, g.ny, g.nz, pp, ang, c->p, 3 * c->N, tw,
+                                             c->err, c->n_sm, c->wait_polls, s),
+             "polarisation + x-FFT kernel");
+    }
+    for (int k = 0; k < nk; ++k) {
+      float dc[3] = {(float)ref, 0.f, 0.f};
+      if (g.frame != RSX_FRAME_LITERAL) {
+        dc[0] = (float)(ref * cos(alpha[k]));
+        dc[1] = (float)(ref * sin(alpha[k]));
+      }
+      long long L = 0;
+      {
+        PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+        RSX_CK(fused_yz(c, &c->tmap_pz[k], 3, &L, s), "y-FFT + z-bins kernel");
+      }
+      {
+        PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+        RSX_CK(rsx::launch_ewald_bins(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
+                                      dc[0], dc[1], dc[2], (float*)c->img, s),
+               "Ewald kernel");
+      }
+      PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
+      RSX_CK(rsx::launch_rotate_acc<float>(c->img, c->acc, g.nx, g.ny, alpha[k], rotation != 0, s),
+             "rotation kernel");
+    }
+  }
+  return RSX_OK;
+}
+
 template <typename R>
 int run_energy_angles(rsx_context* c, int ie, double start, double inc, int nang, int rotation,
                       cudaStream_t s) {
+  if constexpr (sizeof(R) == 4) {
+    if (c->kx > 1 && c->cfg.algorithm == 1 && c->part && c->has_tmap_pz && c->n_sm > 0 &&
+        ((uintptr_t)c->M & 15) == 0)
+      return run_energy_angles_batched(c, ie, start, inc, nang, rotation, s);
+  }
   for (int a = 0; a < nang; ++a) {
     const double alpha = rotation ? (start + inc * a) * (kPi / 180.0) : 0.0;
     int rc = scatter_angle<R>(c, ie, alpha, c->img, s);
@@ -974,14 +1093,8 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
   }
   if (where == RSX_HOST) {
     RSX_CK(cudaStreamSynchronize(s), "result download");
-    int h = 0;
-    RSX_CK(cudaMemcpy(&h, c->err, sizeof(int), cudaMemcpyDeviceToHost), "kernel error flag");
-    if (h) {
-      cudaMemset(c->err, 0, sizeof(int));
-      c->nt_energy = -1;  // per-energy data computed by an aborted kernel is not kept
-      c->bins_energy = -1;
-      return fail(RSX_ERR_CUDA, "a kernel pipeline wait timed out; the result is not valid");
-    }
+    const int rc = take_kernel_error(c);
+    if (rc) return rc;
     memcpy(out, staged.data(), staged.size());
   }
   return RSX_OK;
@@ -995,6 +1108,7 @@ int rsx_nt(rsx_context* c, int ie, void* nt_out, void* stream) {
   if (!nt_out) return fail(RSX_ERR_INVALID, "nt_out is NULL");
   if (c->cfg.algorithm < 2)
     return fail(RSX_ERR_STATE, "N_t needs a context made with algorithm 2 or 3");
+  RSX_DEVPTR(nt_out, c->dev, "nt_out");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   const double ref = -(double)(c->cfg.n_components - 1) / (4.0 * kPi);
@@ -1006,6 +1120,14 @@ int rsx_nt(rsx_context* c, int ie, void* nt_out, void* stream) {
     RSX_CK(rsx::launch_nt_restore<double>(c->nt, nt_out, c->N, ref, s), "N_t output");
   }
   return RSX_OK;
+}
+
+int rsx_check(rsx_context* c, void* stream) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  DeviceGuard dg(c->dev);
+  if (!dg.ok) return fail(RSX_ERR_CUDA, "cannot select the context's device");
+  RSX_CK(cudaStreamSynchronize((cudaStream_t)stream), "stream");
+  return take_kernel_error(c);
 }
 
 int rsx_set_timing(rsx_context* c, int enable) {
@@ -1066,6 +1188,7 @@ int rsx_run(rsx_context* c, double start, double inc, double end, int rotation,
     for (int i = 0; i < (int)c->energies.size(); ++i) sel.push_back(i);
   }
   if (sel.empty()) return RSX_OK;
+  if (where == RSX_DEVICE) RSX_DEVPTR(out, c->dev, "device output");
   DeviceGuard dg(c->dev);
   cudaStream_t s = (cudaStream_t)stream;
   return c->cfg.precision == 32 ? run_impl<float>(c, start, inc, nang, rotation, sel, out, where, s)

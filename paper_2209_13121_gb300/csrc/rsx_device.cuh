@@ -493,4 +493,75 @@ __device__ __forceinline__ void block_fft_ct(typename RT<R>::C* buf, const typen
   block_fft_ct_from<R, LOGN, 0, NFFT, FSTRIDE, ESTRIDE, T, F_FAST>(buf, tw);
 }
 
+// ---------------------------------------------------------------------------
+// Mixed-radix Stockham FFT for any length n (the general-size path).
+//
+// The radices r_0, r_1, ... (product n) are applied in order.  The pass
+// with radix RAD and span Ns = r_0 ... r_(p-1) maps x to y with
+//   butterfly j < n / RAD,  k = j mod Ns:
+//   v_r = x[j + r n / RAD] W_n^(r k n / (Ns RAD)),  V = DFT_RAD(v),
+//   y[(j - k) RAD + k + r Ns] = V_r,
+// which leaves the spectrum in natural order after the last pass (the same
+// self-sorting scheme as the power-of-two passes above, with any radix).
+// x and y are different buffers.  tw[t] = exp(-2 pi i t / n); the twiddle
+// index r k n / (Ns RAD) stays below n.
+// ---------------------------------------------------------------------------
+
+// RAD-point forward DFT by its definition, natural order in and out, with
+// W_RAD^q = tw[q * tstep] (tstep = n / RAD).
+template <int RAD, typename C>
+__device__ __forceinline__ void dft_def(C* v, const C* tw, int tstep) {
+  C out[RAD];
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) {
+    out[r] = v[0];
+#pragma unroll
+    for (int m = 1; m < RAD; ++m) out[r] = cadd(out[r], cmul(v[m], tw[((r * m) % RAD) * tstep]));
+  }
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) v[r] = out[r];
+}
+
+// One butterfly of a pass with a radix known at compile time (2, 4, 8, 16
+// by the register DFTs, 3, 5, 7 by definition).
+template <int RAD, typename C>
+__device__ __forceinline__ void any_butterfly(const C* x, C* y, int j, int n, int Ns, const C* tw) {
+  const int nb = n / RAD, k = j % Ns, ts = n / (Ns * RAD);
+  C v[RAD];
+#pragma unroll
+  for (int r = 0; r < RAD; ++r) v[r] = x[j + r * nb];
+  if (k) {
+#pragma unroll
+    for (int r = 1; r < RAD; ++r) v[r] = cmul(v[r], tw[r * k * ts]);
+  }
+  const int o = (j - k) * RAD + k;
+  if constexpr (RAD == 2 || RAD == 4 || RAD == 8 || RAD == 16) {
+    dft_reg<RAD>(v);
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) y[o + r * Ns] = v[out_pos<RAD>(r)];
+  } else {
+    dft_def<RAD>(v, tw, nb);
+#pragma unroll
+    for (int r = 0; r < RAD; ++r) y[o + r * Ns] = v[r];
+  }
+}
+
+// One butterfly for any other radix (a prime above 7): each output is
+// summed straight from x, O(RAD^2) work; the combined exponent of the
+// pass twiddle and W_RAD^(r m) is reduced modulo n.
+template <typename C>
+__device__ __forceinline__ void any_butterfly_prime(const C* x, C* y, int j, int rad, int n,
+                                                    int Ns, const C* tw) {
+  const int nb = n / rad, k = j % Ns, ts = n / (Ns * rad);
+  const int o = (j - k) * rad + k;
+  for (int r = 0; r < rad; ++r) {
+    C acc = x[j];
+    for (int m = 1; m < rad; ++m) {
+      const long long e = (long long)m * k * ts + (long long)((r * m) % rad) * nb;
+      acc = cadd(acc, cmul(x[j + m * nb], tw[(int)(e % n)]));
+    }
+    y[o + r * Ns] = acc;
+  }
+}
+
 }  // namespace rsx

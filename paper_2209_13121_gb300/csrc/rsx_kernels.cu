@@ -17,6 +17,7 @@
 // HBM-bound, the fused y+z pass bound by instruction issue.
 #include <cuda.h>  // CUtensorMap (the type only; the library does not link libcuda)
 #include <math.h>
+#include <string.h>
 
 #include <type_traits>
 
@@ -54,10 +55,23 @@ __device__ __forceinline__ void pol_zero(PolAcc<R>& a) {
   for (int k = 0; k < 3; ++k) a.b[k][0] = a.b[k][1] = 0;
 }
 
-// FP32: the SFU approximation (absolute error below 1e-6 for the angles of
-// a morphology, |x| <= 2 pi), far below the FP32 contrast tolerance.  FP64
-// keeps the correctly rounded library call.
-__device__ __forceinline__ void sincos_r(float x, float* s, float* c) { __sincosf(x, s, c); }
+// FP32: the SFU approximation, which is accurate (absolute error ~1e-6) only
+// near [-pi, pi].  The Euler angles of Sec. 3.1 are not restricted, so x is
+// first reduced to r = x - n 2 pi, n = rint(x / 2 pi), by Cody and Waite's
+// method with a two-part constant: hi = float(2 pi), lo = float(2 pi - hi),
+// each product subtracted in one fused multiply-add.  For |x| up to ~1e4
+// the reduced angle is off by less than one ulp of pi, far below the FP32
+// contrast tolerance.  FP64 keeps the library call, which reduces any range.
+__device__ __forceinline__ float reduce_2pi(float x) {
+  constexpr double two_pi = 6.283185307179586476925286766559;
+  constexpr float hi = (float)two_pi;
+  constexpr float lo = (float)(two_pi - (double)hi);
+  const float n = rintf(x * (float)(1.0 / two_pi));
+  return fmaf(-n, lo, fmaf(-n, hi, x));
+}
+__device__ __forceinline__ void sincos_r(float x, float* s, float* c) {
+  __sincosf(reduce_2pi(x), s, c);
+}
 __device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
 
 template <typename R>
@@ -349,6 +363,62 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
   for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
 }
 
+// One warp's x-FFT of one field of a row held in shared memory (F, padded
+// as [NX / 32][33]) and its store to out_row[0 .. NX).  release() runs once
+// the warp has read F for the last time, before the second DFT and the
+// stores, so the row buffer can be refilled while they run.
+//  NX = 1024 = 32 x 32: as k_pol_fft4s.
+//  NX = 512 = 32 x 16 with n = n1 + 32 n2, k = k2 + 16 k1: lane n1 does the
+//  16-point DFT over n2 and the twiddles W512^(n1 k2) (tw4: W512^j); after
+//  the transpose, lanes k2 and k2 + 16 share the 32-point DFT over n1 (even
+//  n1 on the lower lane, odd on the upper), which leaves k1 = k and
+//  k1 = 16 + k on the two lanes.
+template <int NX, typename Release>
+__device__ __forceinline__ void xfft_row(float2* F, const float2* tw4, float2* out_row, int lane,
+                                         Release release) {
+  using C = float2;
+  C v[32];
+  if constexpr (NX == 1024) {
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
+    dft32(v);
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
+    __syncwarp();
+#pragma unroll
+    for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+    __syncwarp();
+    release();
+    dft32(v);
+    C* out = out_row + lane;
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+  } else {
+#pragma unroll
+    for (int n2 = 0; n2 < 16; ++n2) v[n2] = F[lane + 32 * n2];
+    dft_reg<16>(v);
+    C u[16];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) u[k2] = cmul(v[out_pos<16>(k2)], tw4[lane * k2]);
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) F[k2 * 33 + lane] = u[k2];
+    __syncwarp();
+    const int k2 = lane & 15, h = lane >> 4;
+#pragma unroll
+    for (int m = 0; m < 16; ++m) v[m] = F[k2 * 33 + 2 * m + h];
+    __syncwarp();
+    release();
+    dft32_pair(v, u, h);
+    C* out = out_row + k2 + 256 * h;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) out[16 * k] = u[k];
+  }
+}
+
 // x pass (FP32, nx = NX = 1024 or 512) as a warp-specialised bulk-copy
 // pipeline, for Algorithm 1 (NT = false: the morphology, c slices of 16 NX
 // bytes per row) or Algorithm 2 (NT = true: the five stored entries of N_t,
@@ -533,54 +603,226 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1)) k_pol_fft4s_tma(
     named_bar_sync(1 + i, NB);
     if (*abort_flag == 0) {
       const long long row = blockIdx.x + rr * gridDim.x;
-      C* F = P + i * 3 * FS + f * FS;
-      C v[32];
-      if constexpr (NX == 1024) {
-#pragma unroll
-        for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
-        dft32(v);
-#pragma unroll
-        for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
-        __syncwarp();
-#pragma unroll
-        for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
-        __syncwarp();
-#pragma unroll
-        for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
-        __syncwarp();
+      xfft_row<NX>(P + i * 3 * FS + f * FS, tw4, p + (size_t)f * N + (size_t)row * NX, lane, [&] {
         if (rr + NP < nmine) named_bar_arrive(1 + NP + i, NB);
-        dft32(v);
-        C* out = p + (size_t)f * N + (size_t)row * NX + lane;
-#pragma unroll
-        for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
-      } else {
-        // 512 = 32 x 16 with n = n1 + 32 n2, k = k2 + 16 k1: lane n1 does the
-        // 16-point DFT over n2 and the twiddles W512^(n1 k2); after the
-        // transpose, lanes k2 and k2 + 16 share the 32-point DFT over n1
-        // (even n1 on the lower lane, odd on the upper), which leaves
-        // k1 = k and k1 = 16 + k on the two lanes
-#pragma unroll
-        for (int n2 = 0; n2 < 16; ++n2) v[n2] = F[lane + 32 * n2];
-        dft_reg<16>(v);
-        C u[16];
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) u[k2] = cmul(v[out_pos<16>(k2)], tw4[lane * k2]);
-        __syncwarp();
-#pragma unroll
-        for (int k2 = 0; k2 < 16; ++k2) F[k2 * 33 + lane] = u[k2];
-        __syncwarp();
-        const int k2 = lane & 15, h = lane >> 4;
-#pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = F[k2 * 33 + 2 * m + h];
-        __syncwarp();
-        if (rr + NP < nmine) named_bar_arrive(1 + NP + i, NB);
-        dft32_pair(v, u, h);
-        C* out = p + (size_t)f * N + (size_t)row * NX + k2 + 256 * h;
-#pragma unroll
-        for (int k = 0; k < 16; ++k) out[16 * k] = u[k];
-      }
+      });
     } else if (rr + NP < nmine) {
       named_bar_arrive(1 + NP + i, NB);
+    }
+  }
+}
+
+// ------------------------------------------- x pass for several angles
+// The angle-independent part of Eq. (polarization) at one voxel, summed
+// over components j with g_j = b_j (2 a_j + b_j) (a_j = v (1 + tau'_j),
+// b_j = v s dpar_j) and the director d_j:
+//   p(e) = [ ((sum_j v_j^2 - 1) + sum_j v_j^2 tau'_j (2 + tau'_j)) e + T e ] / (4 pi),
+//   T = sum_j g_j d_j d_j^T  (complex symmetric),
+// of which e = (cos a, sin a, 0) meets only the entries xx, xy, yy, xz, yz.
+// Summing T instead of T e lets one read of the morphology serve several
+// e-field angles; each angle's p is then formed exactly as Eq.
+// (polarization) prescribes (the same products, summed in another order).
+struct TAcc {
+  float aw;        // sum_j v_j^2
+  float as[2];     // sum_j v_j^2 tau'_j (2 + tau'_j)
+  float t[5][2];   // T: xx, xy, yy, xz, yz
+};
+
+__device__ __forceinline__ void tacc_zero(TAcc& a) {
+  a.aw = 0.f;
+  a.as[0] = a.as[1] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 5; ++q) a.t[q][0] = a.t[q][1] = 0.f;
+}
+
+__device__ __forceinline__ void tacc_add(TAcc& acc, float v, float s, float phi, float theta,
+                                         const PolParams<float>& pp, int j) {
+  const float v2 = v * v, v2s = v2 * s, v2s2 = v2s * s;
+  acc.aw += v2;
+  acc.as[0] += v2 * pp.q[j][0][0] + v2s * pp.q[j][1][0] + v2s2 * pp.q[j][2][0];
+  acc.as[1] += v2 * pp.q[j][0][1] + v2s * pp.q[j][1][1] + v2s2 * pp.q[j][2][1];
+  const float gr = v2s * pp.q[j][3][0] + v2s2 * pp.q[j][4][0];
+  const float gi = v2s * pp.q[j][3][1] + v2s2 * pp.q[j][4][1];
+  float sp, cp, st, ct;
+  sincos_r(phi, &sp, &cp);
+  sincos_r(theta, &st, &ct);
+  const float dx = cp * st, dy = sp * st, dz = ct;
+  const float hxr = gr * dx, hxi = gi * dx, hyr = gr * dy, hyi = gi * dy;
+  acc.t[0][0] += hxr * dx; acc.t[0][1] += hxi * dx;
+  acc.t[1][0] += hxr * dy; acc.t[1][1] += hxi * dy;
+  acc.t[2][0] += hyr * dy; acc.t[2][1] += hyi * dy;
+  acc.t[3][0] += hxr * dz; acc.t[3][1] += hxi * dz;
+  acc.t[4][0] += hyr * dz; acc.t[4][1] += hyi * dz;
+}
+
+// p for e = (ce, se, 0) from the sums (ar + i ai = (sum v^2 - 1) +
+// sum v^2 tau'(2 + tau'), the reference constant left out), in the frame of
+// `literal`, as pol_final forms it from T e.
+__device__ __forceinline__ void p_from_tacc(float ar, float ai, const float (&t)[5][2], float ce,
+                                            float se, bool literal, float2 out[3]) {
+  const float inv = float(1.0 / kFourPi);
+  const float b0r = ce * t[0][0] + se * t[1][0], b0i = ce * t[0][1] + se * t[1][1];
+  const float b1r = ce * t[1][0] + se * t[2][0], b1i = ce * t[1][1] + se * t[2][1];
+  const float b2r = ce * t[3][0] + se * t[4][0], b2i = ce * t[3][1] + se * t[4][1];
+  float p0r, p0i, p1r, p1i;
+  if (literal) {
+    p0r = ar + ce * b0r + se * b1r;
+    p0i = ai + ce * b0i + se * b1i;
+    p1r = -se * b0r + ce * b1r;
+    p1i = -se * b0i + ce * b1i;
+  } else {
+    p0r = ar * ce + b0r;
+    p0i = ai * ce + b0i;
+    p1r = ar * se + b1r;
+    p1i = ai * se + b1i;
+  }
+  out[0] = make_float2(p0r * inv, p0i * inv);
+  out[1] = make_float2(p1r * inv, p1i * inv);
+  out[2] = make_float2(b2r * inv, b2i * inv);
+}
+
+// The Algorithm 1 x pass for up to KMAX e-field angles per read of the
+// morphology (FP32, nx = NX = 1024 or 512): the roles and the bulk-copy
+// ring of k_pol_fft4s_tma, but the polarisation warps accumulate the
+// angle-independent sums (TAcc) of their voxels over the c component
+// stages, then form p for each angle k < ang.n in turn and hand it to the
+// transform warps through a ring of NPB row buffers; the transform groups
+// write angle k's spectrum to p + k * pstride.  Row buffer u = rr * n + k
+// (row rr of this block, angle k) is slot u mod NPB, passed on named
+// barriers (full: 1 + slot, empty: 1 + NPB + slot); NPB a multiple of FG
+// keeps each slot with one transform group.  Per voxel and angle this
+// reads 16 c / n bytes of morphology instead of 16 c.  One persistent CTA
+// per SM.  Waits are bounded as in k_pol_fft4s_tma.
+template <int S, int NPB, int PW, int FG, int NX, int KMAX>
+__global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_multi(
+    const float4* __restrict__ M, long long N, long long nrows, PolParams<float> pp,
+    XAngles ang, float2* __restrict__ p, long long pstride, const float2* __restrict__ tw4_g,
+    int* __restrict__ err, unsigned poll) {
+  using C = float2;
+  static_assert(NX == 1024 || NX == 512, "row length");
+  static_assert(KMAX <= kMaxXAngles, "angle set");
+  constexpr int TP = 32 * PW, SL = NX / TP, FS = (NX / 32) * 33, NB = TP + 96;
+  static_assert(NX % TP == 0 && 1 + 2 * NPB <= 16 && NPB % FG == 0, "layout");
+  constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(float4);
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  float4* stage = reinterpret_cast<float4*>(smem_a128);  // [S][NX]
+  C* P = reinterpret_cast<C*>(stage + S * NX);            // [NPB][3][FS]
+  C* tw4 = P + NPB * 3 * FS;                               // [32][32] or [512]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(tw4 + 1024);
+  unsigned long long* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  if (t == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], PW);
+    }
+    *abort_flag = 0;
+    fence_proxy_async();
+  }
+  for (int i = t; i < (NX == 1024 ? 1024 : 512); i += blockDim.x) tw4[i] = tw4_g[i];
+  __syncthreads();
+  __shared__ float ang_ce[KMAX], ang_se[KMAX];  // indexed by a run-time angle
+  if (t < KMAX) {
+    ang_ce[t] = ang.ce[t];
+    ang_se[t] = ang.se[t];
+  }
+  __syncthreads();
+  const int nk = ang.n;
+  const long long nmine =
+      blockIdx.x < nrows ? (nrows - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int per_row = pp.c;
+
+  if (w == PW + 3 * FG) {  // producer warp, one lane (as in k_pol_fft4s_tma)
+    if (lane != 0) return;
+    const int G = (int)nmine * per_row;
+    int g = 0, slot = 0, k = 0, j = 0;
+    long long row = blockIdx.x;
+    for (; g < G; ++g) {
+      if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), poll)) {
+        atomicOr(err, 1);
+        *abort_flag = 1;
+        break;
+      }
+      mbar_expect_tx(&full[slot], kStageBytes);
+      bulk_g2s(stage + slot * NX, M + (size_t)j * N + (size_t)row * NX, kStageBytes, &full[slot]);
+      if (++slot == S) slot = 0, ++k;
+      if (++j == per_row) j = 0, row += gridDim.x;
+    }
+    for (int d = g - 1; d >= 0 && d >= g - S; --d)
+      mbar_wait_bounded(&full[d % S], (unsigned)((d / S) & 1), kPoll);
+    return;
+  }
+
+  if (w < PW) {  // polarisation warps
+    bool failed = false;
+    int slot = 0, ph = 0;
+    int u = 0;  // row buffers handed on so far
+    for (int rr = 0; rr < (int)nmine; ++rr) {
+      TAcc acc[SL];
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) tacc_zero(acc[sl]);
+      for (int j = 0; j < per_row; ++j) {
+        const int cs = slot, cph = ph;
+        if (++slot == S) slot = 0, ph ^= 1;
+        failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
+        if (failed) break;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, poll))) {
+          failed = true;
+          atomicOr(err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        const float4* st = stage + cs * NX;
+        float4 cur[SL];
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[cs]);
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl)
+          tacc_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
+      }
+      // (sum v^2 - 1) first, then the small optical part (FP32 accuracy)
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) acc[sl].aw = (acc[sl].aw - 1.f) + acc[sl].as[0];
+      for (int k = 0; k < nk; ++k, ++u) {
+        const int i = u % NPB;
+        if (u >= NPB) named_bar_sync(1 + NPB + i, NB);  // slot's previous transforms done
+        if (!failed) {
+          C* Pi = P + i * 3 * FS;
+          const float ce = ang_ce[k], se = ang_se[k];
+#pragma unroll
+          for (int sl = 0; sl < SL; ++sl) {
+            const int e = t + sl * TP;
+            C out[3];
+            p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, out);
+            Pi[e] = out[0];
+            Pi[FS + e] = out[1];
+            Pi[2 * FS + e] = out[2];
+          }
+        }
+        named_bar_arrive(1 + i, NB);
+      }
+    }
+    return;
+  }
+
+  // transform warps: group fg, field f; buffers u = fg, fg + FG, ...
+  const int fg = (w - PW) / 3, f = (w - PW) % 3;
+  const int U = (int)nmine * nk;
+  for (int u = fg; u < U; u += FG) {
+    const int i = u % NPB;
+    named_bar_sync(1 + i, NB);
+    if (*abort_flag == 0) {
+      const int rr = u / nk, k = u - rr * nk;
+      const long long row = blockIdx.x + (long long)rr * gridDim.x;
+      xfft_row<NX>(P + i * 3 * FS + f * FS, tw4,
+                   p + (size_t)k * pstride + (size_t)f * N + (size_t)row * NX, lane, [&] {
+                     if (u + NPB < U) named_bar_arrive(1 + NPB + i, NB);
+                   });
+    } else if (u + NPB < U) {
+      named_bar_arrive(1 + NPB + i, NB);
     }
   }
 }
@@ -820,7 +1062,77 @@ __global__ void __launch_bounds__(T, 3) k_col_fft(typename RT<R>::C* __restrict_
   }
 }
 
-// Direct DFT along z for any nz (out of place): out[k][m][pix] =
+// ------------------------------------------------ general-size transforms
+// Up to kAnyMaxPass radices whose product is the transform length.
+constexpr int kAnyMaxPass = 24;
+struct AnyPlan {
+  int n, np;
+  int rad[kAnyMaxPass];
+};
+
+__device__ __forceinline__ long long any_line_start(const AnyLines& ln, long long l) {
+  const long long b = l / ln.W, x = l - b * ln.W;
+  return ln.base + (b / ln.bdiv) * ln.stride_hi + (b % ln.bdiv) * ln.stride_lo + x * ln.xstride;
+}
+
+// lpc lines per CTA, loaded whole into shared memory (buffer A), then the
+// plan's passes alternate between A and B (the Stockham scheme of
+// rsx_device.cuh with any radix), and the spectra are stored back.
+// lines_fast: consecutive threads take consecutive lines (columns, whose
+// lines are adjacent in memory) rather than consecutive elements (rows).
+template <typename R>
+__global__ void __launch_bounds__(256) k_fft_any(const typename RT<R>::C* src,
+                                                 typename RT<R>::C* dst, AnyPlan plan, AnyLines ln,
+                                                 int lpc, int lines_fast,
+                                                 const typename RT<R>::C* __restrict__ tw_g) {
+  using C = typename RT<R>::C;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = plan.n;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* B = A + (size_t)lpc * n;
+  C* tw = B + (size_t)lpc * n;
+  const long long l0 = (long long)blockIdx.x * lpc;
+  const int nl = ln.nlines - l0 < lpc ? (int)(ln.nlines - l0) : lpc;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) tw[i] = tw_g[i];
+  const int tot = nl * n;
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int t = lines_fast ? e % nl : e / n, i = lines_fast ? e / nl : e % n;
+    A[t * n + i] = src[any_line_start(ln, l0 + t) + (long long)i * ln.estride];
+  }
+  __syncthreads();
+  C* x = A;
+  C* y = B;
+  int Ns = 1;
+  for (int ps = 0; ps < plan.np; ++ps) {
+    const int rad = plan.rad[ps], nb = n / rad, total = nl * nb;
+    for (int it = threadIdx.x; it < total; it += blockDim.x) {
+      const int t = lines_fast ? it % nl : it / nb, j = lines_fast ? it / nl : it % nb;
+      const C* xl = x + t * n;
+      C* yl = y + t * n;
+      switch (rad) {
+        case 2: any_butterfly<2>(xl, yl, j, n, Ns, tw); break;
+        case 3: any_butterfly<3>(xl, yl, j, n, Ns, tw); break;
+        case 4: any_butterfly<4>(xl, yl, j, n, Ns, tw); break;
+        case 5: any_butterfly<5>(xl, yl, j, n, Ns, tw); break;
+        case 7: any_butterfly<7>(xl, yl, j, n, Ns, tw); break;
+        case 8: any_butterfly<8>(xl, yl, j, n, Ns, tw); break;
+        case 16: any_butterfly<16>(xl, yl, j, n, Ns, tw); break;
+        default: any_butterfly_prime(xl, yl, j, rad, n, Ns, tw); break;
+      }
+    }
+    __syncthreads();
+    C* tmp = x;
+    x = y;
+    y = tmp;
+    Ns *= rad;
+  }
+  for (int e = threadIdx.x; e < tot; e += blockDim.x) {
+    const int t = lines_fast ? e % nl : e / n, i = lines_fast ? e / nl : e % n;
+    dst[any_line_start(ln, l0 + t) + (long long)i * ln.estride] = x[t * n + i];
+  }
+}
+
+// Direct DFT along z for any nz (out of place): out[k][m][pix] =// Direct DFT along z for any nz (out of place): out[k][m][pix] =
 //   sum_z in[k][z][pix] exp(-2 pi i m z / nz).
 template <typename R>
 __global__ void k_dft_z(const typename RT<R>::C* __restrict__ in, typename RT<R>::C* __restrict__ out,
@@ -844,6 +1156,16 @@ __global__ void k_dft_z(const typename RT<R>::C* __restrict__ in, typename RT<R>
   out[k * N + (size_t)m * npix + pix] = acc;
 }
 
+// Position in fftshift order (q = 0 at (ny / 2, nx / 2)) of the pixel with
+// FFT-order index pix = my nx + mx, for any nx and ny.
+__device__ __forceinline__ size_t shifted_pixel(long long pix, int nx, int ny) {
+  const int my = (int)(pix / nx), mx = (int)(pix - (long long)my * nx);
+  int sy = my + ny / 2, sx = mx + nx / 2;
+  if (sy >= ny) sy -= ny;
+  if (sx >= nx) sx -= nx;
+  return (size_t)sy * nx + sx;
+}
+
 // --------------------------------------------------------------- geometry
 // Eq. (Ewald) per pixel, in double: q from the FFT index (FFT order),
 // q_z = -k + sqrt(k^2 - q_x^2 - q_y^2), t = q_z / dq_z, bins floor(t) and
@@ -853,7 +1175,7 @@ __global__ void k_geometry(Geo<R>* __restrict__ geo, int nx, int ny, int nz, dou
                            double k) {
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= (long long)nx * ny) return;
-  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
+  const int my = (int)(pix / nx), mx = (int)(pix - (long long)my * nx);
   const int fx = mx < (nx + 1) / 2 ? mx : mx - nx;
   const int fy = my < (ny + 1) / 2 ? my : my - ny;
   const double two_pi = 6.283185307179586476925286766559;
@@ -929,8 +1251,7 @@ __global__ void __launch_bounds__(256) k_ewald_full(const typename RT<R>::C* __r
   const long long npix = (long long)nx * ny;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
-  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
-  R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
+  R* dst = img + shifted_pixel(pix, nx, ny);
   const Geo<R> g = geo[pix];
   if (g.b0 < 0) {
     *dst = R(0);
@@ -1038,9 +1359,7 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const long long pix = pix0 + q;
-    const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
-    R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
-    *dst = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
+    img[shifted_pixel(pix, nx, ny)] = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
   }
 }
 
@@ -1364,8 +1683,8 @@ __global__ void k_ewald_bins(const float4* __restrict__ part, int nx, int ny, in
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
   const Geo<float> g = geo[pix];
-  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);
-  float* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
+  const int mx = (int)(pix % nx);
+  float* dst = img + shifted_pixel(pix, nx, ny);
   if (g.b0 < 0) {
     *dst = 0.f;
     return;
@@ -1502,29 +1821,35 @@ __global__ void __launch_bounds__(PX / 2) k_ewald_tma(const typename RT<R>::C* _
 #pragma unroll
   for (int q = 0; q < 2; ++q) {
     const long long pix = pix0 + q;
-    const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);
-    R* dst = img + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1));
-    *dst = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
+    img[shifted_pixel(pix, nx, ny)] = g[q].b0 < 0 ? R(0) : ewald_value<R>(g[q], a0[q], a1[q]);
   }
 }
 
-// One thread per pixel, for a 1 x 1 detector (npix odd).
+// One thread per pixel with plain loads: the pruned z transform for grids
+// with an odd pixel count (where pixel pairs are not 16-byte aligned).
 template <typename R>
-__global__ void k_ewald_single(const typename RT<R>::C* __restrict__ p, int nz,
-                               const Geo<R>* __restrict__ geo, const typename RT<R>::C* __restrict__ twz,
-                               R dc0, R dc1, R dc2, R* __restrict__ img) {
+__global__ void __launch_bounds__(256) k_ewald_each(const typename RT<R>::C* __restrict__ p,
+                                                    int nx, int ny, int nz,
+                                                    const Geo<R>* __restrict__ geo,
+                                                    const typename RT<R>::C* __restrict__ twz,
+                                                    R dc0, R dc1, R dc2, R* __restrict__ img) {
   using C = typename RT<R>::C;
-  const Geo<R> g = geo[0];
+  const long long npix = (long long)nx * ny;
+  const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pix >= npix) return;
+  const Geo<R> g = geo[pix];
+  R* dst = img + shifted_pixel(pix, nx, ny);
   if (g.b0 < 0) {
-    img[0] = R(0);
+    *dst = R(0);
     return;
   }
+  const size_t N = (size_t)npix * nz;
   C a0[3], a1[3];
   for (int k = 0; k < 3; ++k) a0[k] = a1[k] = RT<R>::mk(0, 0);
   int i0 = 0, i1 = 0;
   for (int z = 0; z < nz; ++z) {
     for (int k = 0; k < 3; ++k) {
-      const C v = p[(size_t)k * nz + z];
+      const C v = p[k * N + (size_t)z * npix + pix];
       a0[k] = cadd(a0[k], cmul(v, twz[i0]));
       a1[k] = cadd(a1[k], cmul(v, twz[i1]));
     }
@@ -1533,12 +1858,14 @@ __global__ void k_ewald_single(const typename RT<R>::C* __restrict__ p, int nz,
     i1 += g.b1;
     if (i1 >= nz) i1 -= nz;
   }
-  const R dcs[3] = {dc0, dc1, dc2};
-  for (int k = 0; k < 3; ++k) {
-    if (g.b0 == 0) a0[k].x += dcs[k];
-    if (g.b1 == 0) a1[k].x += dcs[k];
+  if (pix == 0) {
+    const R dcs[3] = {dc0, dc1, dc2};
+    for (int k = 0; k < 3; ++k) {
+      if (g.b0 == 0) a0[k].x += dcs[k];
+      if (g.b1 == 0) a1[k].x += dcs[k];
+    }
   }
-  img[0] = ewald_value<R>(g, a0, a1);
+  *dst = ewald_value<R>(g, a0, a1);
 }
 
 // ------------------------------------------------ linearity fast path
@@ -1631,7 +1958,7 @@ __global__ void __launch_bounds__(256) k_bins5_from_part(const float4* __restric
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
   const Geo<float> g = geo[pix];
-  const int ti = ((int)pix & (nx - 1)) >> 3;
+  const int ti = (int)(pix % nx) >> 3;
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1690,9 +2017,7 @@ __global__ void __launch_bounds__(256) k_ewald_linear(const typename RT<R>::C* _
   const long long npix = (long long)nx * ny;
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
-  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);  // nx = 2^k
-  img[(size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1))] =
-      linear_pixel<R>(bins, npix, pix, geo[pix], ce, se, literal);
+  img[shifted_pixel(pix, nx, ny)] = linear_pixel<R>(bins, npix, pix, geo[pix], ce, se, literal);
 }
 
 // The same for a batch of angles: imgs[a] for a = blockIdx.y.
@@ -1706,8 +2031,7 @@ __global__ void __launch_bounds__(256) k_ewald_linear_many(const typename RT<R>:
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= npix) return;
   const int a = blockIdx.y;
-  const int mx = (int)pix & (nx - 1), my = (int)pix >> (__ffs(nx) - 1);
-  imgs[(size_t)a * npix + (size_t)((my + ny / 2) & (ny - 1)) * nx + ((mx + nx / 2) & (nx - 1))] =
+  imgs[(size_t)a * npix + shifted_pixel(pix, nx, ny)] =
       linear_pixel<R>(bins, npix, pix, geo[pix], ab.ce[a], ab.se[a], literal);
 }
 
@@ -1941,6 +2265,15 @@ static cudaError_t pol_fftx_dispatch(const void* M, int nx, int ny, int nz, cons
                                      long long rb, long long rc, cudaStream_t s) {
   if (!do_fft)
     return pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+  if (nx & (nx - 1)) {
+    // other lengths: polarisation alone, then the mixed-radix x-FFT of the
+    // 3 ny nz rows in place
+    if (rc >= 0) return cudaErrorInvalidValue;
+    cudaError_t e =
+        pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, 0, -1, s);
+    if (e != cudaSuccess) return e;
+    return launch_row_fft<R>(p, nx, 3LL * ny * nz, twx, s);
+  }
 #define RSX_POL(L)                                                                                \
   case L:                                                                                         \
     return pol_fftx_impl<R, 256, 1024, true, L, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
@@ -2036,9 +2369,47 @@ cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
                    : pol_fft4s_tma_impl<true, 1024>(nt, nx, ny, nz, pp, p, tw, err, n_sm, poll, s);
 }
 
+template <int NX>
+static cudaError_t pol_fft4s_tma_multi_impl(const void* M, int ny, int nz,
+                                            const PolParams<float>& pp, const XAngles& ang,
+                                            void* p, long long pstride, const void* tw,
+                                            int* err, int n_sm, unsigned poll, cudaStream_t s) {
+  // 4 stages of one (row, component) slice, 4 row buffers, 8 polarisation
+  // warps (NX / 256 voxels per thread), two transform groups and a producer
+  // warp: one block per SM, ~171 KB of shared memory for 1024-point rows
+  constexpr int S = 4, NPB = 4, PW = 8, FG = 2;
+  if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > kMaxXAngles)
+    return cudaErrorInvalidValue;
+  const long long N = (long long)NX * ny * nz, nrows = (long long)ny * nz;
+  if (nrows <= 0) return cudaSuccess;
+  const size_t smem = (size_t)S * NX * sizeof(float4) +
+                      (NPB * 3 * (NX / 32) * 33 + 1024) * sizeof(float2) + 2 * S * 8 + 16;
+  auto kern = k_pol_fft4s_tma_multi<S, NPB, PW, FG, NX, kMaxXAngles>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  const long long grid = nrows < (long long)n_sm ? nrows : (long long)n_sm;
+  kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>(
+      (const float4*)M, N, nrows, pp, ang, (float2*)p, pstride, (const float2*)tw, err, poll);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pol_fft4s_tma_multi(const void* M, int nx, int ny, int nz,
+                                       const PolParams<float>& pp, const XAngles& ang, void* p,
+                                       long long pstride, const void* tw, int* err, int n_sm,
+                                       unsigned poll, cudaStream_t s) {
+  if (nx == 1024)
+    return pol_fft4s_tma_multi_impl<1024>(M, ny, nz, pp, ang, p, pstride, tw, err, n_sm, poll, s);
+  if (nx == 512)
+    return pol_fft4s_tma_multi_impl<512>(M, ny, nz, pp, ang, p, pstride, tw, err, n_sm, poll, s);
+  return cudaErrorInvalidValue;
+}
+
 bool yz_fusable(int nx, int ny, int nz) {
-  return (ny == 1024 || ny == 512) && nx % 16 == 0 && nz >= 1 && nz <= 1024 &&
-         (nz & (nz - 1)) == 0;
+  return (ny == 1024 || ny == 512) && nx >= 16 && (nx & (nx - 1)) == 0 && nz >= 1 &&
+         nz <= 1024 && (nz & (nz - 1)) == 0;
 }
 
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
@@ -2178,6 +2549,10 @@ cudaError_t launch_row_fft4s(void* p, long long nrows, const void* tw4, cudaStre
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
                            const void* src) {
+  if (nx & (nx - 1)) {  // any other length: the mixed-radix passes
+    const AnyLines ln = {nrows, 1, 1, nx, 0, 0, 0, 1};
+    return launch_fft_any<R>(src ? src : p, p, nx, ln, twx, s);
+  }
   if (nx <= 2048) return row_fft_impl<R, 256, 2048>(p, nx, nrows, twx, s, src);
   return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s, src);
 }
@@ -2229,8 +2604,52 @@ template <typename R>
 cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
                            const void* tw, cudaStream_t s) {
   if (L == 1) return cudaSuccess;
+  if (L & (L - 1)) {  // any other length: the mixed-radix passes
+    const AnyLines ln = {bt.nbatch * W, W, bt.bdiv, bt.stride_hi, bt.stride_lo, bt.base, 1, S};
+    return launch_fft_any<R>(p, p, L, ln, tw, s);
+  }
   // 4096 elements per CTA: 34 KB (FP32) or 70 KB (FP64) of padded tile
   return col_fft_dispatch<R, 4096>(p, L, S, W, bt, tw, s);
+}
+
+// Radices for length n: 16s, then the rest of the power of two, then 7, 5,
+// 3, then the remaining primes (each its own O(p^2) pass).
+static AnyPlan any_plan(int n) {
+  AnyPlan pl;
+  memset(&pl, 0, sizeof(pl));
+  pl.n = n;
+  int m = n;
+  const int small[] = {16, 8, 4, 2, 7, 5, 3};
+  for (int r : small)
+    while (m % r == 0 && pl.np < kAnyMaxPass) pl.rad[pl.np++] = r, m /= r;
+  for (int p = 11; p * p <= m && pl.np < kAnyMaxPass; p += 2)
+    while (m % p == 0 && pl.np < kAnyMaxPass) pl.rad[pl.np++] = p, m /= p;
+  if (m > 1 && pl.np < kAnyMaxPass) pl.rad[pl.np++] = m, m = 1;
+  if (m != 1) pl.np = -1;  // not reachable for n <= 4096
+  return pl;
+}
+
+template <typename R>
+cudaError_t launch_fft_any(const void* src, void* dst, int n, const AnyLines& ln, const void* tw,
+                           cudaStream_t s) {
+  using C = typename RT<R>::C;
+  if (n < 1 || n > 4096 || ln.W < 1 || ln.bdiv < 1) return cudaErrorInvalidValue;
+  if (ln.nlines <= 0) return cudaSuccess;
+  const AnyPlan pl = any_plan(n);
+  if (pl.np < 0) return cudaErrorInvalidValue;
+  // both buffers hold at most 2 x 4096 elements; up to 64 lines per CTA
+  long long lpc = 4096 / n;
+  if (lpc < 1) lpc = 1;
+  if (lpc > 64) lpc = 64;
+  if (lpc > ln.nlines) lpc = ln.nlines;
+  const size_t smem = (2 * (size_t)lpc * n + n) * sizeof(C);
+  auto kern = k_fft_any<R>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int lines_fast = ln.estride != 1 && ln.xstride == 1;
+  kern<<<grid1(ln.nlines, (int)lpc), 256, smem, s>>>((const C*)src, (C*)dst, pl, ln, (int)lpc,
+                                                     lines_fast, (const C*)tw);
+  return cudaGetLastError();
 }
 
 template <typename R>
@@ -2260,9 +2679,9 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
     k_ewald_full<R><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo, (R*)img);
     return cudaGetLastError();
   }
-  if (npix == 1) {
-    k_ewald_single<R><<<1, 1, 0, s>>>((const C*)p, nz, geo, (const C*)twz, dc[0], dc[1], dc[2],
-                                      (R*)img);
+  if (npix % 2) {
+    k_ewald_each<R><<<grid1(npix, 256), 256, 0, s>>>((const C*)p, nx, ny, nz, geo, (const C*)twz,
+                                                     dc[0], dc[1], dc[2], (R*)img);
     return cudaGetLastError();
   }
   constexpr int PX = 512, S = 4;
@@ -2277,8 +2696,12 @@ cudaError_t launch_ewald(const void* p, int nx, int ny, int nz, const Geo<R>* ge
   }
   const int tw_in_smem = nz <= 4096;
   const size_t smem = tw_in_smem ? nz * sizeof(C) : 0;
-  k_ewald_pruned<R, 4><<<grid1(npix / 2, 256), 256, smem, s>>>(
-      (const C*)p, nx, ny, nz, geo, (const C*)twz, tw_in_smem, dc[0], dc[1], dc[2], (R*)img);
+  auto kern = k_ewald_pruned<R, 4>;
+  // FP64 tables above 3072 entries exceed the 48 KB default
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid1(npix / 2, 256), 256, smem, s>>>((const C*)p, nx, ny, nz, geo, (const C*)twz,
+                                               tw_in_smem, dc[0], dc[1], dc[2], (R*)img);
   return cudaGetLastError();
 }
 
@@ -2289,8 +2712,11 @@ cudaError_t launch_zbins5(const void* f, int nx, int ny, int nz, const Geo<R>* g
   const long long npix = (long long)nx * ny;
   const int tw_in_smem = nz <= 4096;
   const size_t smem = tw_in_smem ? nz * sizeof(C) : 0;
-  k_zbins5<R, 4><<<grid1(npix, 256), 256, smem, s>>>((const C*)f, nx, ny, nz, geo, (const C*)twz,
-                                                      tw_in_smem, (R)dc, (C*)bins);
+  auto kern = k_zbins5<R, 4>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid1(npix, 256), 256, smem, s>>>((const C*)f, nx, ny, nz, geo, (const C*)twz, tw_in_smem,
+                                           (R)dc, (C*)bins);
   return cudaGetLastError();
 }
 
@@ -2392,6 +2818,8 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                          const void*, cudaStream_t);                              \
   template cudaError_t launch_dft_z<R>(const void*, void*, int, int, int, const void*,            \
                                        cudaStream_t);                                             \
+  template cudaError_t launch_fft_any<R>(const void*, void*, int, const AnyLines&, const void*,   \
+                                         cudaStream_t);                                           \
   template cudaError_t launch_geometry<R>(Geo<R>*, int, int, int, double, double, cudaStream_t);  \
   template cudaError_t launch_ewald<R>(const void*, int, int, int, const Geo<R>*, const void*,     \
                                        bool, const R*, void*, cudaStream_t, int*, unsigned);      \

@@ -109,6 +109,11 @@ struct ColBatches {
 // Sets the message returned by rsx_last_error() on this host thread.
 void set_last_error(const char* msg);
 
+// RSX_OK when p is device memory of device `dev` or managed memory;
+// otherwise sets the message (naming `what`) and returns RSX_ERR_INVALID.
+// Uses cudaPointerGetAttributes, which allocates nothing.
+int check_device_pointer(const void* p, int dev, const char* what);
+
 // Rows are (z, y) pairs; row_begin / row_count restrict the launch to a
 // range of rows (a group of z-slices); row_count < 0 means all rows.
 template <typename R>
@@ -156,6 +161,22 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, unsigned poll,
                                  cudaStream_t s);
+// Up to kMaxXAngles e-field angles for one multi-angle x pass: cos and sin
+// of each, n of them in use.
+constexpr int kMaxXAngles = 8;
+struct XAngles {
+  float ce[kMaxXAngles], se[kMaxXAngles];
+  int n;
+};
+// The Algorithm-1 x pass for ang.n angles per read of the morphology (FP32,
+// nx = 1024 or 512, M 16-byte aligned): angle k's three x-transformed fields
+// go to p + k * pstride (complex elements; pstride >= 3 N).  pp supplies the
+// optical constants and the frame (its ce, se are not used).  One persistent
+// CTA per SM (n_sm).
+cudaError_t launch_pol_fft4s_tma_multi(const void* M, int nx, int ny, int nz,
+                                       const PolParams<float>& pp, const XAngles& ang, void* p,
+                                       long long pstride, const void* tw, int* err, int n_sm,
+                                       unsigned poll, cudaStream_t s);
 // The same pipeline for Algorithm 2: p = N_t e from the five stored entries
 // of N_t ([5][N] complex float, 16-byte aligned; the reference constant
 // left out as k_nt_all stores it).
@@ -195,6 +216,18 @@ cudaError_t launch_ewald_bins(const void* part, int nx, int ny, int nz, long lon
 cudaError_t launch_col_fft4s_tma(const void* tmap, void* p, long long S, long long W,
                                  const ColBatches& bt, const void* tw4, int* err, int n_sm,
                                  unsigned poll, cudaStream_t s);
+// Lines of a general-size FFT launch: line l = (b, x) with b = l / W and
+// x = l mod W starts at base + (b / bdiv) stride_hi + (b mod bdiv) stride_lo +
+// x xstride and holds its n elements estride apart (complex elements).
+struct AnyLines {
+  long long nlines, W, bdiv, stride_hi, stride_lo, base, xstride, estride;
+};
+// Forward, unnormalised DFTs of any length n in [1, 4096] along every line
+// (mixed-radix Stockham passes in shared memory), from src to dst (the same
+// buffer, or disjoint ones); tw[t] = exp(-2 pi i t / n).
+template <typename R>
+cudaError_t launch_fft_any(const void* src, void* dst, int n, const AnyLines& lines,
+                           const void* tw, cudaStream_t s);
 template <typename R>
 cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cudaStream_t s,
                            const void* src = nullptr);

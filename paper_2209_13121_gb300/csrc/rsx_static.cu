@@ -105,8 +105,17 @@ int rsx_scatter_angle_noalloc(const void* M, int nx, int ny, int nz, int n_compo
   for (int i = 0; i < 4 * n_components; ++i)
     if (!isfinite(constants[i])) return fail(RSX_ERR_INVALID, "optical constant %d not finite", i);
 
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RSX_ERR_INVALID, "M and img_out must be device memory (no CUDA device)");
+  }
+  int rc = rsx::check_device_pointer(M, dev, "M");
+  if (rc) return rc;
+  if ((rc = rsx::check_device_pointer(img_out, dev, "img_out"))) return rc;
+
   void* base = nullptr;
-  int rc = scratch_address(&base);
+  rc = scratch_address(&base);
   if (rc) return rc;
   char* sc = (char*)base;
   float2* p = (float2*)(sc + kOffP);

@@ -8,7 +8,6 @@ fallback.
 from __future__ import annotations
 
 import ctypes
-import math
 import os
 
 import numpy as np
@@ -33,8 +32,9 @@ EXPORTED = (
     "rsx_set_morphology", "rsx_set_optical_constants", "rsx_run", "rsx_polarization",
     "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
     "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc", "rsx_nt",
-    "rsx_set_wait_limit",
+    "rsx_set_wait_limit", "rsx_check", "rsx_angle_batch",
 )
+MAX_ANGLE_BATCH = 8
 NOALLOC_MAX_VOXELS = 1 << 20
 NOALLOC_MAX_PIXELS = 1 << 16
 PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other", "nt")
@@ -49,6 +49,7 @@ class RsxConfig(ctypes.Structure):
         ("algorithm", ctypes.c_int),
         ("frame", ctypes.c_int),
         ("validate", ctypes.c_int),
+        ("angle_batch", ctypes.c_int),
     ]
 
 
@@ -84,6 +85,8 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "rsx_phase_times": (ci, [vp, vp, vp]),
         "rsx_scatter_angle_noalloc": (ci, [vp, ci, ci, ci, ci, cd, cd, vp, cd, ci, vp, vp]),
         "rsx_nt": (ci, [vp, ci, vp, vp]),
+        "rsx_check": (ci, [vp, vp]),
+        "rsx_angle_batch": (ci, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -119,10 +122,33 @@ def angle_count(start, inc, end, rotation=True) -> int:
     return lib().rsx_angle_count(start, inc, end, 1 if rotation else 0)
 
 
+def _device_buffer(t, what, dtype_name, shape=None, numel=None, device=None):
+    """Address of a torch CUDA tensor the library will read or write, after
+    checking that it is one: on a CUDA device (the context's, when given),
+    of the context's real type, contiguous and of the expected size.  The
+    library borrows the address unchecked beyond that, so a wrong buffer
+    would be read or written out of bounds on the GPU."""
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)  # a raw device address: the caller vouches for it
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if device is not None and t.device.index != device:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, the context on cuda:{device}")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise ValueError(f"{what} must be {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{what} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} has {t.numel()} elements, expected {numel}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
 def make_config(nx, ny, nz, n_components, voxel_nm, precision=32, algorithm=1,
-                frame=RSX_FRAME_LITERAL, validate=False) -> RsxConfig:
+                frame=RSX_FRAME_LITERAL, validate=False, angle_batch=0) -> RsxConfig:
     return RsxConfig(nx, ny, nz, n_components, voxel_nm, precision, algorithm, frame,
-                     1 if validate else 0)
+                     1 if validate else 0, angle_batch)
 
 
 def workspace_bytes(cfg: RsxConfig) -> int:
@@ -136,14 +162,22 @@ class Context:
     integer addresses); host buffers are numpy arrays."""
 
     def __init__(self, nx, ny, nz, n_components, voxel_nm, precision=32, algorithm=1,
-                 frame=RSX_FRAME_LITERAL, validate=False):
+                 frame=RSX_FRAME_LITERAL, validate=False, angle_batch=0):
         self.cfg = make_config(nx, ny, nz, n_components, voxel_nm, precision, algorithm,
-                               frame, validate)
+                               frame, validate, angle_batch)
         self.real = np.float32 if precision == 32 else np.float64
+        self._dt = "float32" if precision == 32 else "float64"
         h = ctypes.c_void_p()
         _check(lib().rsx_create(ctypes.byref(self.cfg), ctypes.byref(h)))
         self._h = h
+        import torch
+        self.device = torch.cuda.current_device()
         self._keep = None  # keeps a borrowed device morphology alive
+
+    @property
+    def angle_batch(self):
+        """e-field angles per read of the morphology in rsx_run (Algorithm 1)."""
+        return lib().rsx_angle_batch(self._h)
 
     @property
     def shape(self):
@@ -185,11 +219,10 @@ class Context:
             # Algorithm 2 streams from this host array on every energy
             self._keep = A if self.cfg.algorithm >= 2 else None
             return
-        self._check_shape(tuple(M.shape))
-        if not M.is_contiguous():
-            raise ValueError("device morphology must be contiguous")
-        _check(lib().rsx_set_morphology(self._h, ctypes.c_void_p(M.data_ptr()), RSX_DEVICE,
-                                        _stream_handle(stream)))
+        c = self.cfg
+        ptr = _device_buffer(M, "device morphology", self._dt,
+                             shape=(c.n_components, c.nz, c.ny, c.nx, 4), device=self.device)
+        _check(lib().rsx_set_morphology(self._h, ptr, RSX_DEVICE, _stream_handle(stream)))
         self._keep = M
 
     def _check_shape(self, shp):
@@ -225,15 +258,20 @@ class Context:
             ptr, where = out.ctypes.data_as(ctypes.c_void_p), RSX_HOST
             st = _stream_handle(stream) if stream is not None else None
         else:
-            if tuple(out.shape) != shape or not out.is_contiguous():
-                raise ValueError("device output has the wrong shape or layout")
-            ptr, where = ctypes.c_void_p(out.data_ptr()), RSX_DEVICE
+            ptr = _device_buffer(out, "device output", self._dt, shape=shape, device=self.device)
+            where = RSX_DEVICE
             st = _stream_handle(stream)
         _check(lib().rsx_run(self._h, float(angles[0]), float(angles[1]), float(angles[2]),
                              1 if rotation else 0,
                              sel.ctypes.data_as(ctypes.c_void_p) if sel is not None else None,
                              n_sel, ptr, where, st))
         return out
+
+    def check(self, stream=None):
+        """rsx_check: waits for `stream` and raises RsxError (RSX_ERR_CUDA)
+        if a pipelined kernel of this context timed out since the last
+        check; device results written since then are then not valid."""
+        _check(lib().rsx_check(self._h, _stream_handle(stream)))
 
     # ------------------------------------------------------------ timing
     def set_timing(self, enable=True):
@@ -252,35 +290,50 @@ class Context:
         return {name: (ms[i], n[i]) for i, name in enumerate(PHASES)}
 
     # ------------------------------------------------------- single steps
+    def _buf(self, t, what, numel):
+        return _device_buffer(t, what, self._dt, numel=numel, device=self.device)
+
+    def _n(self):
+        return self.cfg.nx * self.cfg.ny * self.cfg.nz
+
+    def _npix(self):
+        return self.cfg.nx * self.cfg.ny
+
     def polarization(self, energy_index, alpha_rad, p_out, stream=None):
-        _check(lib().rsx_polarization(self._h, int(energy_index), float(alpha_rad),
-                                      ctypes.c_void_p(p_out.data_ptr()), _stream_handle(stream)))
+        """p_out: [3][nz][ny][nx][2] (complex as re, im pairs)."""
+        ptr = self._buf(p_out, "p_out", 6 * self._n())
+        _check(lib().rsx_polarization(self._h, int(energy_index), float(alpha_rad), ptr,
+                                      _stream_handle(stream)))
         return p_out
 
     def nt(self, energy_index, nt_out, stream=None):
         """Algorithm 3's N_t (entries xx, xy, yy, xz, yz) into nt_out [5][nz][ny][nx][2]."""
-        _check(lib().rsx_nt(self._h, int(energy_index), ctypes.c_void_p(nt_out.data_ptr()),
-                            _stream_handle(stream)))
+        ptr = self._buf(nt_out, "nt_out", 10 * self._n())
+        _check(lib().rsx_nt(self._h, int(energy_index), ptr, _stream_handle(stream)))
         return nt_out
 
     def fft3d(self, p, stream=None):
-        _check(lib().rsx_fft3d(self._h, ctypes.c_void_p(p.data_ptr()), _stream_handle(stream)))
+        ptr = self._buf(p, "p", 6 * self._n())
+        _check(lib().rsx_fft3d(self._h, ptr, _stream_handle(stream)))
         return p
 
     def ewald(self, energy_index, p_tilde, img_out, stream=None):
-        _check(lib().rsx_ewald(self._h, int(energy_index), ctypes.c_void_p(p_tilde.data_ptr()),
-                               ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
+        pt = self._buf(p_tilde, "p_tilde", 6 * self._n())
+        im = self._buf(img_out, "img_out", self._npix())
+        _check(lib().rsx_ewald(self._h, int(energy_index), pt, im, _stream_handle(stream)))
         return img_out
 
     def rotate_accumulate(self, img, alpha_rad, acc, stream=None):
-        _check(lib().rsx_rotate_accumulate(self._h, ctypes.c_void_p(img.data_ptr()),
-                                           float(alpha_rad), ctypes.c_void_p(acc.data_ptr()),
+        im = self._buf(img, "img", self._npix())
+        ac = self._buf(acc, "acc", self._npix())
+        _check(lib().rsx_rotate_accumulate(self._h, im, float(alpha_rad), ac,
                                            _stream_handle(stream)))
         return acc
 
     def scatter_angle(self, energy_index, alpha_rad, img_out, stream=None):
-        _check(lib().rsx_scatter_angle(self._h, int(energy_index), float(alpha_rad),
-                                       ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
+        im = self._buf(img_out, "img_out", self._npix())
+        _check(lib().rsx_scatter_angle(self._h, int(energy_index), float(alpha_rad), im,
+                                       _stream_handle(stream)))
         return img_out
 
 
@@ -291,20 +344,14 @@ def scatter_angle_noalloc(M, energy_ev, constants, alpha_rad, img_out, voxel_nm,
     scratch; see include/rsx.h for the size limits).  M: contiguous float32
     CUDA tensor [c][nz][ny][nx][4]; constants: [c][4]; img_out: float32 CUDA
     tensor [ny][nx]."""
-    c, nz, ny, nx, four = M.shape
-    if four != 4 or not M.is_contiguous() or tuple(img_out.shape) != (ny, nx):
-        raise ValueError("M must be [c][nz][ny][nx][4] contiguous and img_out [ny][nx]")
+    if len(M.shape) != 5 or M.shape[4] != 4:
+        raise ValueError("M must be [c][nz][ny][nx][4]")
+    c, nz, ny, nx, _ = M.shape
+    mp = _device_buffer(M, "M", "float32")
+    ip = _device_buffer(img_out, "img_out", "float32", shape=(ny, nx), device=M.device.index)
     K = np.ascontiguousarray(constants, dtype=np.float64).reshape(c, 4)
     _check(lib().rsx_scatter_angle_noalloc(
-        ctypes.c_void_p(M.data_ptr()), nx, ny, nz, c, float(voxel_nm), float(energy_ev),
-        K.ctypes.data_as(ctypes.c_void_p), float(alpha_rad), int(frame),
-        ctypes.c_void_p(img_out.data_ptr()), _stream_handle(stream)))
+        mp, nx, ny, nz, c, float(voxel_nm), float(energy_ev),
+        K.ctypes.data_as(ctypes.c_void_p), float(alpha_rad), int(frame), ip,
+        _stream_handle(stream)))
     return img_out
-
-
-def deg2rad_list(start, inc, end, rotation=True):
-    """Angles (radians) the library uses for start:inc:end (inclusive)."""
-    n = angle_count(start, inc, end, rotation)
-    if not rotation:
-        return [0.0]
-    return [(start + inc * i) * (math.pi / 180.0) for i in range(n)]

@@ -91,6 +91,12 @@ CASES = [
     ((3, 256, 32), 4),    # tall column tile
     ((3, 8, 1024), 3),    # four-step x pass (nx = 1024)
     ((2, 1024, 16), 2),   # four-step y pass (ny = 1024)
+    ((4, 6, 8), 2),       # the 8 x 6 x 4 parity grid: ny = 6 (radices 2 and 3)
+    ((3, 12, 10), 3),     # nx = 10, ny = 12 (radix 5; 4 x 3)
+    ((2, 9, 15), 2),      # odd lateral sizes: 9 = 3 x 3, 15 = 5 x 3 (odd pixel count)
+    ((5, 7, 14), 2),      # radix 7, ragged nz
+    ((1, 11, 13), 2),     # primes above 7 (the O(p) passes), 2-D film
+    ((2, 100, 96), 3),    # 100 = 4 x 5 x 5, 96 = 16 x 2 x 3
 ]
 IDS = ["x".join(map(str, s)) + f"c{c}" for s, c in CASES]
 
@@ -127,6 +133,50 @@ def test_polarization_matches_oracle(rsx, shape, c, prec):
                 assert rel < (1e-10 if prec == 64 else 2e-3)
 
 
+def _wide_angles(M, seed):
+    """Euler angles outside [0, 2 pi) x [0, pi] (Sec. 3.1 does not restrict
+    them): phi ~ U[-4 pi, 4 pi], theta ~ U[-pi, 2 pi], and one voxel in 16
+    with |phi| and |theta| near 100."""
+    g = np.random.default_rng(seed)
+    M = M.copy()
+    shp = M.shape[:-1]
+    M[..., 2] = g.uniform(-4 * np.pi, 4 * np.pi, shp)
+    M[..., 3] = g.uniform(-np.pi, 2 * np.pi, shp)
+    far = g.random(shp) < 1.0 / 16
+    M[..., 2][far] = g.choice([-1.0, 1.0], far.sum()) * g.uniform(99.0, 101.0, far.sum())
+    M[..., 3][far] = g.choice([-1.0, 1.0], far.sum()) * g.uniform(99.0, 101.0, far.sum())
+    return M
+
+
+WIDE = [((3, 16, 32), 3), ((2, 8, 1024), 4), ((2, 64, 512), 2), ((2, 1024, 64), 2)]
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape,c", WIDE, ids=["x".join(map(str, s)) for s, _ in WIDE])
+def test_wide_euler_angles_match_oracle(rsx, shape, c, prec):
+    """Angles far outside one turn through rsx_polarization and the fused
+    per-angle path (for nx = 1024 and 512 in FP32: the bulk-copy x pass),
+    at the usual tolerances."""
+    M, K = _inputs(shape, c, prec, seed=51)
+    M = _wide_angles(M, seed=52)
+    with _ctx(rsx, shape, c, prec) as ctx:
+        ctx.set_morphology(torch.from_numpy(M).cuda())
+        ctx.set_optical_constants(ENERGIES, K)
+        p = torch.empty((3,) + shape + (2,), dtype=_tdtype(prec), device="cuda")
+        img = torch.empty(shape[1:], dtype=_tdtype(prec), device="cuda")
+        for ie, alpha in ((0, 0.4), (2, 2.3)):
+            ctx.polarization(ie, alpha, p)
+            got = p.cpu().numpy()
+            got = got[..., 0] + 1j * got[..., 1]
+            ref = O.rotate_back(O.polarization(M, K[ie], O.e_field(alpha)), alpha)
+            scale = max(np.abs(ref).max(), 1.0 / (4 * np.pi))
+            np.testing.assert_allclose(got, ref, rtol=0,
+                                       atol=(1e-13 if prec == 64 else 3e-7) * scale)
+            ctx.scatter_angle(ie, alpha, img)
+            ref_img = O.scatter_one_angle(M, K[ie], ENERGIES[ie], VOXEL, alpha)
+            assert_image_close(img.cpu().numpy(), ref_img, prec)
+
+
 @pytest.mark.parametrize("prec", [32, 64])
 def test_polarization_lab_frame(rsx, prec):
     shape, c = (3, 8, 16), 3
@@ -144,7 +194,9 @@ def test_polarization_lab_frame(rsx, prec):
 
 
 # ------------------------------------------------------------------ row a4
-FFT_SHAPES = [(4, 8, 8), (5, 16, 32), (1, 64, 64), (3, 128, 16), (2, 1, 8), (1, 1, 1),
+FFT_SHAPES = [(4, 6, 8), (3, 12, 10), (5, 9, 15), (2, 11, 13), (7, 5, 3), (6, 100, 36),
+              (3, 1, 17), (2, 3, 1031), (2, 1031, 2), (1, 4095, 3),
+              (4, 8, 8), (5, 16, 32), (1, 64, 64), (3, 128, 16), (2, 1, 8), (1, 1, 1),
               (7, 4, 2048), (16, 32, 32), (6, 2, 4), (3, 4, 1024), (2, 1024, 8)]
 
 
@@ -301,6 +353,74 @@ def test_run_matches_oracle(rsx, shape, c, prec):
     np.testing.assert_allclose(host[:, center], ref[:, center], rtol=1e-9 if prec == 64 else 1e-4)
 
 
+ODD = [((4, 6, 8), 2), ((3, 12, 10), 3), ((2, 9, 15), 2), ((3, 25, 48), 2), ((1, 45, 35), 2)]
+
+
+@pytest.mark.parametrize("algorithm", [1, 2, 3])
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("shape,c", ODD, ids=["x".join(map(str, s)) for s, _ in ODD])
+def test_run_non_power_of_two_grids(rsx, shape, c, prec, algorithm):
+    """Any nx and ny (Sec. 3.3 step 4 puts no restriction on the grid): the
+    P0 parity grid 8 x 6 x 4 and other lateral sizes with factors 3, 5 and
+    7, through rsx_run for Algorithm 1, Algorithm 2 and the linearity path,
+    host and device output, against the oracle."""
+    M, K = _inputs(shape, c, prec, seed=71)
+    angles = (0.0, 45.0, 180.0)
+    nz, ny, nx = shape
+    ref = O.run_alg1(M, K, ENERGIES, VOXEL, angles_deg=angles)
+    with _ctx(rsx, shape, c, prec, algorithm=algorithm) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        host = ctx.run(angles)
+        dev = torch.empty(ref.shape, dtype=_tdtype(prec), device="cuda")
+        ctx.run(angles, out=dev)
+        ctx.check()
+        np.testing.assert_array_equal(dev.cpu().numpy(), host)
+    assert_image_close(host, ref, prec, mask=_center_mask(ny, nx, r=2.5))
+
+
+BATCHED = [((4, 512, 512), 3, 4), ((2, 1024, 1024), 2, 3), ((4, 512, 1024), 2, 8),
+           ((2, 1024, 512), 4, 2)]
+
+
+@pytest.mark.parametrize("frame", [0, 1])
+@pytest.mark.parametrize("shape,c,kx", BATCHED, ids=["x".join(map(str, s)) + f"k{k}"
+                                                    for s, _, k in BATCHED])
+def test_run_batched_angles_match_oracle(rsx, shape, c, kx, frame):
+    """Algorithm 1 with the morphology read once per batch of angles (the
+    multi-angle x pass, FP32): ten angles, so the last batch is partial,
+    against the oracle; and against the same context shape with one angle
+    per pass."""
+    M, K = _inputs(shape, c, 32, seed=61)
+    angles = (0.0, 20.0, 180.0)
+    nz, ny, nx = shape
+    ref = O.run_alg1(M, K[:1], ENERGIES[:1], VOXEL, angles_deg=angles,
+                     uT_mode="literal" if frame == 0 else "lab")
+    dev = torch.from_numpy(M).cuda()
+    outs = {}
+    for k in (kx, 1):
+        with rsx.Context(nx, ny, nz, c, VOXEL, precision=32, frame=frame, angle_batch=k) as ctx:
+            assert ctx.angle_batch == k
+            ctx.set_morphology(dev)
+            ctx.set_optical_constants(ENERGIES[:1], K[:1])
+            out = torch.empty((1, ny, nx), device="cuda")
+            ctx.run(angles, out=out)
+            ctx.check()
+            outs[k] = out.cpu().numpy()
+    mask = _center_mask(ny, nx, r=2.5)
+    assert_image_close(outs[kx], ref, 32, mask=mask)
+    assert_image_close(outs[kx], outs[1], 32, mask=mask)
+
+
+def test_angle_batch_applies_only_where_the_multi_angle_pass_runs(rsx):
+    for shape, prec, alg, want in (((4, 1024, 1024), 32, 1, 4), ((4, 1024, 1024), 64, 1, 1),
+                                   ((4, 1024, 1024), 32, 2, 1), ((3, 1024, 1024), 32, 1, 1),
+                                   ((4, 256, 1024), 32, 1, 1)):
+        nz, ny, nx = shape
+        with rsx.Context(nx, ny, nz, 2, VOXEL, precision=prec, algorithm=alg) as ctx:
+            assert ctx.angle_batch == want, (shape, prec, alg)
+
+
 @pytest.mark.parametrize("prec", [32, 64])
 def test_run_lab_frame_and_rotation_off(rsx, prec):
     shape, c = (4, 16, 16), 3
@@ -413,6 +533,21 @@ def test_pipeline_wait_timeout_is_reported_and_recoverable(rsx, algorithm):
         assert np.all(out == 7.0)   # the failing call left its host output untouched
         ctx.set_wait_limit()
         np.testing.assert_array_equal(ctx.run((0.0, 90.0, 90.0)), ref)
+        # device output: the call returns before the GPU is done, so the
+        # timeout is reported by rsx_check, which also drops the per-energy
+        # data an aborted kernel produced
+        dout = torch.full((1, ny, nx), 7.0, device="cuda")
+        ctx.set_optical_constants(ENERGIES[:1], K[:1])   # drops the per-energy data
+        ctx.set_wait_limit(0)
+        ctx.run((0.0, 90.0, 90.0), out=dout)
+        with pytest.raises(rsx.RsxError) as e:
+            ctx.check()
+        assert e.value.code == rsx.RSX_ERR_CUDA and "timed out" in str(e.value)
+        ctx.check()   # the flag was cleared by the report
+        ctx.set_wait_limit()
+        ctx.run((0.0, 90.0, 90.0), out=dout)
+        ctx.check()
+        np.testing.assert_array_equal(dout.cpu().numpy(), ref)
 
 
 
@@ -452,6 +587,58 @@ def test_errors_are_reported_and_write_nothing(rsx):
             assert np.all(o == 7.0)
         empty = ctx.run((0, 10, 20), energy_indices=[])
         assert empty.shape == (0, 8, 8)
+
+
+def test_device_entry_points_refuse_host_pointers(rsx):
+    """A host address where device memory is expected is refused by the C
+    entry points (cudaPointerGetAttributes) before anything is enqueued."""
+    shape, c = (2, 8, 8), 2
+    M, K = _inputs(shape, c, 32, seed=14)
+    host_p = np.zeros((3,) + shape + (2,), np.float32)
+    host_img = np.zeros(shape[1:], np.float32)
+    dev_img = torch.zeros(shape[1:], device="cuda")
+    with _ctx(rsx, shape, c, 32) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES, K)
+        calls = [lambda: ctx.polarization(0, 0.0, host_p.ctypes.data),
+                 lambda: ctx.fft3d(host_p.ctypes.data),
+                 lambda: ctx.scatter_angle(0, 0.0, host_img.ctypes.data),
+                 lambda: ctx.rotate_accumulate(host_img.ctypes.data, 0.0, dev_img),
+                 lambda: ctx.ewald(0, host_p.ctypes.data, dev_img),
+                 lambda: ctx.set_morphology(host_p.ctypes.data)]
+        for call in calls:
+            with pytest.raises((rsx.RsxError, ValueError)) as e:
+                call()
+            if isinstance(e.value, rsx.RsxError):
+                assert e.value.code == rsx.RSX_ERR_INVALID
+        lib = rsx.lib()
+        import ctypes
+        rc = lib.rsx_run(ctx._h, 0.0, 10.0, 20.0, 1, None, 3, ctypes.c_void_p(host_img.ctypes.data),
+                         rsx.RSX_DEVICE, None)
+        assert rc == rsx.RSX_ERR_INVALID
+        assert "host memory" in lib.rsx_last_error().decode()
+        # the context still works
+        ctx.scatter_angle(0, 0.0, dev_img)
+        torch.cuda.synchronize()
+        assert np.all(np.isfinite(dev_img.cpu().numpy()))
+
+
+@pytest.mark.parametrize("algorithm", [1, 3])
+def test_fp64_tall_stack_pruned_z_transform(rsx, algorithm):
+    """FP64 with nz = 4096 (the z twiddle table then needs 64 KB of shared
+    memory) on a lateral grid the bulk-copy Ewald kernel does not take:
+    the pruned z transform (Algorithm 1) and the linearity path's q_z bins
+    (Algorithm 3) against the oracle."""
+    shape, c = (4096, 4, 8), 2
+    M, K = _inputs(shape, c, 64, seed=15)
+    angles = (0.0, 90.0, 90.0)
+    ref = O.run_alg1(M, K, ENERGIES[:1], VOXEL, angles_deg=angles)
+    nz, ny, nx = shape
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=64, algorithm=algorithm) as ctx:
+        ctx.set_morphology(M)
+        ctx.set_optical_constants(ENERGIES[:1], K[:1])
+        got = ctx.run(angles)
+    assert_image_close(got, ref, 64, mask=_center_mask(ny, nx, 0.5))
 
 
 def test_unvalidated_context_accepts_out_of_range_v_sum(rsx):
@@ -505,6 +692,48 @@ def test_full_size_sampled_pixels_match_oracle(rsx, algorithm):
             assert (np.abs(got - ref)[big] / ref[big]).max() < 2e-3
     del dev
     torch.cuda.empty_cache()
+
+
+def test_full_size_run_sampled_pixels_match_oracle(rsx):
+    """rsx_run at the benchmark's size and launch configuration (1024 x
+    1024 x 128, c = 4, FP32, device output: the multi-angle x pass with its
+    default batch, the fused y+z pass, the Ewald image, the rotation into
+    the average), six angles (a full batch and a partial one), against the
+    oracle's average at sampled output pixels (each angle's unrotated image
+    at the corners the rotation reads, exact by linearity of the DFT)."""
+    if torch.cuda.get_device_properties(0).total_memory < 60e9:
+        pytest.skip("needs ~30 GB of device memory")
+    shape, c, E = (128, 1024, 1024), 4, 285.0
+    nz, ny, nx = shape
+    angles = (0.0, 2.0, 10.0)
+    sp = synth.sparse_voxels(shape, c, 6000, seed=26)
+    K = synth.optical_constants([E], c, seed=27)
+    dev = synth.morphology_sparse_torch(shape, c, sp)
+    g = np.random.default_rng(28)
+    oy = np.concatenate([[ny // 2, ny // 2 + 1, 3, ny - 2], g.integers(0, ny, 50)])
+    ox = np.concatenate([[nx // 2, nx // 2 - 2, 5, nx - 1], g.integers(0, nx, 50)])
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=32) as ctx:
+        assert ctx.angle_batch == 4
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants([E], K)
+        out = torch.empty((1, ny, nx), dtype=torch.float32, device="cuda")
+        ctx.run(angles, out=out)
+        ctx.check()
+        full = out[0].cpu().numpy().astype(np.float64)
+    del dev
+    torch.cuda.empty_cache()
+    got = full[oy, ox]
+    ref = O.run_alg1_sparse_pixels(sp, shape, K[0], E, VOXEL, angles, oy, ox)
+    # pixels whose rotated samples reach q = 0 carry its large value
+    center = np.hypot(oy - ny // 2, ox - nx // 2) < 2.5
+    assert center[:2].all()
+    np.testing.assert_allclose(got[center], ref[center], rtol=1e-5)
+    rest = ~center
+    rel = np.linalg.norm(got[rest] - ref[rest]) / np.linalg.norm(ref[rest])
+    assert rel < 1e-4, rel
+    big = rest & (ref > 1e-4 * ref[rest].max())
+    assert big.sum() > 30
+    assert (np.abs(got - ref)[big] / ref[big]).max() < 2e-3
 
 
 @pytest.mark.parametrize("shape,c", [((1024, 1024, 16), 2), ((64, 512, 512), 4)])

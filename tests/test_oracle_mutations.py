@@ -46,6 +46,11 @@ MUTANTS = {
                                 "return math.pi / wavelength_nm(E_eV)"),
     "average not divided": ("out[o] = acc / len(alphas)", "out[o] = acc"),  # Algorithm 1's
     "image not fftshifted": ("return np.fft.fftshift(img, axes=(0, 1))", "return img"),
+    "sampled rotation reads corners in the wrong order": (
+        "contrib[ok] = vals[pos:pos + n]", "contrib[ok] = vals[pos:pos + n][::-1]"),
+    "sampled average not divided": ("    return acc / len(alphas)", "    return acc"),
+    "sampled pixels not shifted back to FFT order": (
+        "np.mod(sy - Ny // 2, Ny), np.mod(sx - Nx // 2, Nx)", "sy, sx"),
 }
 
 

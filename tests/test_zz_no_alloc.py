@@ -5,9 +5,10 @@ framework's memory pool, or on hosts that forbid cudaMalloc after start-up)
 and so cannot create a context.  For them the library offers one entry point
 whose working memory is a fixed array inside the library.  This file checks,
 through the C ABI, that it gives the same image as the context path
-(rsx_scatter_angle) within the FP32 tolerance of the parity tests, on two
-calls in a row (the second call must not be disturbed by what the first left
-in the shared array), and that grids beyond the fixed size are refused.
+(rsx_scatter_angle) and as the FP64 CPU oracle within the FP32 tolerance of
+the parity tests, on two calls in a row (the second call must not be
+disturbed by what the first left in the shared array), and that grids beyond
+the fixed size are refused.
 
 It is collected last on purpose, so that a run stopping at the first failure
 has already run every other test; it also passes on its own in a fresh
@@ -65,6 +66,23 @@ def test_noalloc_matches_context_path_on_two_calls(rsx, frame):
             ctx.scatter_angle(ie, alpha, ref)
             torch.cuda.synchronize()
             _close(out.cpu().numpy(), ref.cpu().numpy())
+
+
+def test_noalloc_matches_the_oracle(rsx):
+    """Directly against the FP64 CPU oracle on one small grid, in both
+    frames, two calls in a row."""
+    from oracle import cyrsoxs_oracle as O
+    nz, ny, nx, c, dv = 6, 32, 64, 3, 5.0
+    M = synth.morphology_random((nz, ny, nx), c, seed=31)
+    K = synth.optical_constants([275.0, 300.0], c, seed=32)
+    Md = torch.from_numpy(M).cuda()
+    for frame, mode in ((0, "literal"), (1, "lab")):
+        for ie, alpha in ((0, 0.5), (1, 1.9)):
+            out = torch.full((ny, nx), float("nan"), device="cuda")
+            rsx.scatter_angle_noalloc(Md, [275.0, 300.0][ie], K[ie], alpha, out, dv, frame=frame)
+            torch.cuda.synchronize()
+            ref = O.scatter_one_angle(M, K[ie], [275.0, 300.0][ie], dv, alpha, uT_mode=mode)
+            _close(out.cpu().numpy(), ref)
 
 
 def test_noalloc_second_grid_after_a_larger_one(rsx):
