@@ -55,6 +55,8 @@ WORKLOADS = {
     # small enough for full ncu captures
     "p1-1024-z32": dict(shape=(32, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0),
                         energies=(150, 270.0, 320.0)),
+    "p1-1024-z16": dict(shape=(16, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0),
+                        energies=(150, 270.0, 320.0)),
 }
 VOXEL_NM = 5.0
 METRIC = "P-RSoXS voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s')"
@@ -134,6 +136,61 @@ def _dist():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def gpu_local_cpus(index):
+    """Host CPUs nearest to GPU `index` (the "CPU Affinity" column of
+    nvidia-smi topo -m), or None when it cannot be read."""
+    try:
+        out = subprocess.run(["nvidia-smi", "topo", "-m"], capture_output=True, text=True,
+                             timeout=20).stdout
+    except Exception:
+        return None
+    lines = [ln.rstrip() for ln in out.splitlines() if ln.strip()]
+    header = next((ln for ln in lines if "CPU Affinity" in ln), None)
+    row = next((ln for ln in lines if ln.split() and ln.split()[0] == f"GPU{index}"), None)
+    if not header or not row:
+        return None
+    # columns are tab-separated; the header's first cell is empty
+    hcols = [c.strip() for c in header.split("\t")]
+    rcols = [c.strip() for c in row.split("\t")]
+    try:
+        spec = rcols[hcols.index("CPU Affinity")]
+    except (ValueError, IndexError):
+        return None
+    cpus = set()
+    for part in spec.split(","):
+        part = part.strip()
+        if "-" in part:
+            a, b = part.split("-")
+            cpus.update(range(int(a), int(b) + 1))
+        elif part.isdigit():
+            cpus.add(int(part))
+    return cpus or None
+
+
+def pinned_near_gpu(shape, dtype, index):
+    """A page-locked host tensor whose pages come from the memory nearest to
+    GPU `index`: the allocation and first touch run with this process bound
+    to the GPU's local CPUs (the default local-allocation policy then places
+    the pages there), so host-to-device copies do not cross sockets.
+    Returns (tensor, whether the binding applied)."""
+    import torch
+    cpus = gpu_local_cpus(index)
+    old = None
+    if cpus:
+        try:
+            old = os.sched_getaffinity(0)
+            os.sched_setaffinity(0, cpus & set(range(os.cpu_count() or 1)) or old)
+        except Exception:
+            old = None
+    try:
+        t = torch.empty(shape, dtype=dtype, pin_memory=True)
+        t.zero_()
+    finally:
+        if old is not None:
+            os.sched_setaffinity(0, old)
+    return t, old is not None
 
 
 def _free_port():
@@ -325,7 +382,7 @@ def run_ours(args):
     # step still uploads its full morphology and reads its image back.
     e2e = None
     if not args.no_e2e:
-        Mh = torch.empty(M.shape, dtype=M.dtype, pin_memory=True)
+        Mh, numa_bound = pinned_near_gpu(M.shape, M.dtype, dev)
         Mh.copy_(M)
         Mh_np = Mh.numpy()
         out_t = torch.empty((1, ny, nx), dtype=M.dtype, pin_memory=True)
@@ -368,7 +425,7 @@ def run_ours(args):
         e2e_s = ranks.max(time.perf_counter() - t0)
         e2e = {"value": units / e2e_s / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(Mh_np.nbytes), "d2h_bytes_per_step": int(host_out.nbytes),
-               "h2d_gbs": round(h2d_gbs, 1)}
+               "h2d_gbs": round(h2d_gbs, 1), "pinned_near_gpu": numa_bound}
         for cx in ctxs:
             cx.close()
     else:

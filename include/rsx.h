@@ -79,8 +79,9 @@ typedef struct rsx_config {
                       /* of v over components is never checked.             */
   int angle_batch;    /* Algorithm 1: e-field angles whose p is formed from  */
                       /* one read of the morphology (1..RSX_MAX_ANGLE_BATCH; */
-                      /* 0 = RSX_DEFAULT_ANGLE_BATCH).  Each extra angle     */
-                      /* holds another 3 N complex p buffer.  Used on FP32   */
+                      /* 0 = the largest batch whose p buffers fit in 32    */
+                      /* GiB).  Each extra angle holds another 3 N complex  */
+                      /* p buffer.  Used on FP32                            */
                       /* grids with nx and ny 512 or 1024, nx a multiple of  */
                       /* 16 and nz a power of two up to 1024; elsewhere 1.   */
                       /* Each angle's arithmetic is unchanged (Algorithm 1's */
@@ -88,7 +89,6 @@ typedef struct rsx_config {
 } rsx_config;
 
 #define RSX_MAX_ANGLE_BATCH 8
-#define RSX_DEFAULT_ANGLE_BATCH 4
 
 typedef struct rsx_context rsx_context;
 
@@ -143,7 +143,12 @@ int rsx_angle_count(double start_deg, double increment_deg, double end_deg, int 
  *   Memory that is not page-locked returns RSX_ERR_INVALID.  Algorithms 2
  *   and 3 treat it as RSX_HOST (borrowed).
  * With validate set, a value outside the ranges of Sec. 3.1 returns
- * RSX_ERR_INVALID and leaves the previous morphology in place. */
+ * RSX_ERR_INVALID and leaves the previous morphology in place.
+ * FP64 Algorithm 1 contexts also evaluate every voxel's director (Eq.
+ * (rotBCD)) here, once, into a [c][3][N] double buffer the context holds, so
+ * the runs need no sine or cosine; for RSX_DEVICE the call then waits for
+ * that kernel (on `stream`), for RSX_HOST_ASYNC it is enqueued after the
+ * copy. */
 int rsx_set_morphology(rsx_context* ctx, const void* M, int where, void* stream);
 
 /* Optical constants (Sec. 3.2): energies_ev[n_energies] (> 0) and

@@ -126,6 +126,7 @@ struct rsx_context {
   long long N = 0, npix = 0;
   void* M_owned = nullptr;  // device copy of a host morphology
   const void* M = nullptr;  // morphology in use (owned or borrowed)
+  void* dir = nullptr;      // FP64 Algorithm 1: the morphology's director, [c][3][N] double
   std::vector<double> energies, constants;
   void* p = nullptr;    // kx x 3 N complex workspace (one p per angle of a batch)
   int kx = 1;           // angle batch of the Algorithm 1 x pass
@@ -164,6 +165,9 @@ struct rsx_context {
   void* part = nullptr;
   // linearity path: the images of a batch of angles ([kMaxAngleBatch][ny][nx])
   void* imgs = nullptr;
+  // page-locked staging of host output (grown on demand)
+  void* host_stage = nullptr;
+  size_t host_stage_bytes = 0;
   int n_sm = 0;
   unsigned wait_polls = rsx::kWaitPolls;  // bound of the pipelined kernels' waits
   int* flag = nullptr;
@@ -181,8 +185,8 @@ struct rsx_context {
 namespace {
 
 void free_all(rsx_context* c) {
-  void* ptrs[] = {c->M_owned, c->p,   c->img, c->acc,  c->geo,  c->twx,
-                  c->twy,     c->twz, c->tw4, c->flag, c->err, c->part, c->imgs};
+  void* ptrs[] = {c->M_owned, c->p,    c->img, c->acc,  c->geo,  c->twx, c->twy,
+                  c->twz,     c->tw4,  c->flag, c->err, c->part, c->imgs, c->dir};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -201,6 +205,7 @@ void free_all(rsx_context* c) {
   if (c->ft) cudaFree(c->ft);
   if (c->bins5) cudaFree(c->bins5);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->host_stage) cudaFreeHost(c->host_stage);
 }
 
 cudaEvent_t take_event(rsx_context* c) {
@@ -476,13 +481,14 @@ int x_pass(rsx_context* c, const PolParams<R>& pp, cudaStream_t s) {
   }
   if (g.nx == 1024) {
     RSX_CK(rsx::launch_pol_fft4s<R>(c->M, g.algorithm == 2 ? c->nt : nullptr, g.nx, g.ny, g.nz, pp,
-                                    c->p, c->tw4, s),
+                                    c->p, c->tw4, s, g.algorithm == 1 ? c->dir : nullptr),
            "polarisation + x-FFT kernel");
   } else if (g.algorithm == 2) {
     RSX_CK(rsx::launch_ntp_fftx<R>(c->nt, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
            "N_t polarisation + x-FFT kernel");
   } else {
-    RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s),
+    RSX_CK(rsx::launch_pol_fftx<R>(c->M, g.nx, g.ny, g.nz, pp, true, c->p, c->twx, s, 0, -1,
+                                   c->dir),
            "polarisation + x-FFT kernel");
   }
   return RSX_OK;
@@ -603,7 +609,12 @@ static int angle_batch_of(const rsx_config* cfg) {
   const bool ok = cfg->precision == 32 && cfg->algorithm == 1 &&
                   (cfg->nx == 1024 || cfg->nx == 512) && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
   if (!ok) return 1;
-  return cfg->angle_batch == 0 ? RSX_DEFAULT_ANGLE_BATCH : cfg->angle_batch;
+  if (cfg->angle_batch > 0) return cfg->angle_batch;
+  // default: the largest batch up to RSX_MAX_ANGLE_BATCH whose p buffers
+  // (3 N complex float each) fit in 32 GiB
+  const double p_bytes = 3.0 * cfg->nx * cfg->ny * cfg->nz * 8.0;
+  const int k = (int)((double)(32LL << 30) / p_bytes);
+  return k < 1 ? 1 : k > RSX_MAX_ANGLE_BATCH ? RSX_MAX_ANGLE_BATCH : k;
 }
 
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
@@ -617,6 +628,8 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
                  : 5 * (size_t)N * Cs + 2 * (size_t)stage_vox * 4 * R;  // N_t + staging (Table 2)
   if (cfg->algorithm == 3) b += 5 * (size_t)N * Cs + 10 * (size_t)npix * Cs;  // FFT'd N_t, bins
   b += 3 * (size_t)N * Cs * angle_batch_of(cfg);     // p_x, p_y, p_z (Table 1: 6 N) per angle
+  if (cfg->precision == 64 && cfg->algorithm == 1)
+    b += 3 * (size_t)cfg->n_components * N * R;      // the cached director
   b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
   b += (size_t)npix * geo_size(cfg->precision);
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
@@ -691,6 +704,13 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
       delete c;
       return rc;
     }
+  }
+  if (cfg->precision == 64 && cfg->algorithm == 1 &&
+      (e = cudaMalloc(&c->dir, 3 * (size_t)cfg->n_components * c->N * R)) != cudaSuccess) {
+    rc = cuda_fail(e, "director cache");
+    free_all(c);
+    delete c;
+    return rc;
   }
   e = cudaMemset(c->err, 0, sizeof(int));
   if (e != cudaSuccess) {
@@ -788,6 +808,9 @@ int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
     }
     if (!c->M_owned) RSX_CK(cudaMalloc(&c->M_owned, bytes), "morphology copy");
     RSX_CK(cudaMemcpyAsync(c->M_owned, M, bytes, cudaMemcpyHostToDevice, s), "morphology upload");
+    if (c->dir)
+      RSX_CK(rsx::launch_director<double>(c->M_owned, n_entries, c->N, c->dir, s),
+             "director kernel");
     if (where == RSX_HOST) RSX_CK(cudaStreamSynchronize(s), "morphology upload");
     c->M = c->M_owned;
     c->nt_energy = -1;
@@ -807,6 +830,10 @@ int rsx_set_morphology(rsx_context* c, const void* M, int where, void* stream) {
     RSX_CK(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, s), "validation");
     RSX_CK(cudaStreamSynchronize(s), "validation");
     if (h) return fail(RSX_ERR_INVALID, "morphology value outside 0<=v<=1, 0<=s<=1 or non-finite angle");
+  }
+  if (c->dir) {
+    RSX_CK(rsx::launch_director<double>(M, n_entries, c->N, c->dir, s), "director kernel");
+    RSX_CK(cudaStreamSynchronize(s), "director kernel");
   }
   c->M = M;
   c->M_host = nullptr;
@@ -1063,14 +1090,23 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
              const std::vector<int>& sel, void* out, int where, cudaStream_t s) {
   const size_t img_bytes = (size_t)c->npix * sizeof(R);
   // host output lands in `out` only once every energy has succeeded and no
-  // pipelined kernel reported a timeout: until then it is staged here
-  std::vector<unsigned char> staged;
+  // pipelined kernel reported a timeout: until then it is staged in the
+  // context's page-locked buffer (asynchronous downloads, no pageable copy)
+  unsigned char* staged = nullptr;
   if (where == RSX_HOST) {
-    try {
-      staged.resize(sel.size() * img_bytes);
-    } catch (const std::bad_alloc&) {
-      return fail(RSX_ERR_OOM, "no host memory to stage %zu result bytes", sel.size() * img_bytes);
+    const size_t need = sel.size() * img_bytes;
+    if (need > c->host_stage_bytes) {
+      if (c->host_stage) cudaFreeHost(c->host_stage);
+      c->host_stage = nullptr;
+      c->host_stage_bytes = 0;
+      if (cudaHostAlloc(&c->host_stage, need, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        c->host_stage = nullptr;
+        return fail(RSX_ERR_OOM, "no page-locked host memory to stage %zu result bytes", need);
+      }
+      c->host_stage_bytes = need;
     }
+    staged = (unsigned char*)c->host_stage;
   }
   for (size_t o = 0; o < sel.size(); ++o) {
     const int ie = sel[o];
@@ -1086,8 +1122,7 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
              "average kernel");
     } else {
       RSX_CK(rsx::launch_scale<R>(c->acc, c->acc, c->npix, inv, s), "average kernel");
-      RSX_CK(cudaMemcpyAsync(staged.data() + o * img_bytes, c->acc, img_bytes,
-                             cudaMemcpyDeviceToHost, s),
+      RSX_CK(cudaMemcpyAsync(staged + o * img_bytes, c->acc, img_bytes, cudaMemcpyDeviceToHost, s),
              "result download");
     }
   }
@@ -1095,7 +1130,7 @@ int run_impl(rsx_context* c, double start, double inc, int nang, int rotation,
     RSX_CK(cudaStreamSynchronize(s), "result download");
     const int rc = take_kernel_error(c);
     if (rc) return rc;
-    memcpy(out, staged.data(), staged.size());
+    memcpy(out, staged, sel.size() * img_bytes);
   }
   return RSX_OK;
 }

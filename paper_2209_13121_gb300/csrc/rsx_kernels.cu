@@ -74,6 +74,23 @@ __device__ __forceinline__ void sincos_r(float x, float* s, float* c) {
 }
 __device__ __forceinline__ void sincos_r(double x, double* s, double* c) { sincos(x, s, c); }
 
+// The same with the director d = (dx, dy, dz) of component j given.
+template <typename R>
+__device__ __forceinline__ void pol_add_d(PolAcc<R>& acc, R v, R s, R dx, R dy, R dz,
+                                          const PolParams<R>& pp, int j) {
+  const R v2 = v * v, v2s = v2 * s, v2s2 = v2s * s;
+  acc.aw += v2;
+  acc.as[0] += v2 * pp.q[j][0][0] + v2s * pp.q[j][1][0] + v2s2 * pp.q[j][2][0];
+  acc.as[1] += v2 * pp.q[j][0][1] + v2s * pp.q[j][1][1] + v2s2 * pp.q[j][2][1];
+  const R gr = v2s * pp.q[j][3][0] + v2s2 * pp.q[j][4][0];
+  const R gi = v2s * pp.q[j][3][1] + v2s2 * pp.q[j][4][1];
+  const R de = dx * pp.ce + dy * pp.se;
+  const R hr = gr * de, hi = gi * de;
+  acc.b[0][0] += hr * dx; acc.b[0][1] += hi * dx;
+  acc.b[1][0] += hr * dy; acc.b[1][1] += hi * dy;
+  acc.b[2][0] += hr * dz; acc.b[2][1] += hi * dz;
+}
+
 template <typename R>
 __device__ __forceinline__ void pol_add(PolAcc<R>& acc, R v, R s, R phi, R theta,
                                         const PolParams<R>& pp, int j) {
@@ -154,7 +171,8 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
                                                 typename RT<R>::C* __restrict__ p,
                                                 const typename RT<R>::C* __restrict__ twx,
                                                 int tw_in_smem,
-                                                const typename RT<R>::C* __restrict__ nt) {
+                                                const typename RT<R>::C* __restrict__ nt,
+                                                const R* __restrict__ dir) {
   using C = typename RT<R>::C;
   using V4 = typename RT<R>::V4;
   constexpr int SLOTS = EC / T;
@@ -227,10 +245,21 @@ __global__ void __launch_bounds__(T, (sizeof(R) == 4 && EC <= 1024) ? 3 : 1) k_p
         if (e < nel) nxt[sl] = ld_stream(Mj + e);
       }
     }
+    if (dir) {  // the cached director of component j ([c][3][N])
+      const R* dj = dir + (size_t)j * 3 * N + vox0;
 #pragma unroll
-    for (int sl = 0; sl < SLOTS; ++sl) {
-      const int e = threadIdx.x + sl * T;
-      if (e < nel) pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
+      for (int sl = 0; sl < SLOTS; ++sl) {
+        const int e = threadIdx.x + sl * T;
+        if (e < nel)
+          pol_add_d(acc[sl], (R)cur[sl].x, (R)cur[sl].y, dj[e], dj[N + e], dj[2 * N + e], pp, j);
+      }
+    } else {
+#pragma unroll
+      for (int sl = 0; sl < SLOTS; ++sl) {
+        const int e = threadIdx.x + sl * T;
+        if (e < nel)
+          pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
+      }
     }
 #pragma unroll
     for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = nxt[sl];
@@ -283,7 +312,8 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
                                                       long long N, long long nrows, PolParams<R> pp,
                                                       typename RT<R>::C* __restrict__ p,
                                                       const typename RT<R>::C* __restrict__ tw4_g,
-                                                      const typename RT<R>::C* __restrict__ nt) {
+                                                      const typename RT<R>::C* __restrict__ nt,
+                                                      const R* __restrict__ dir) {
   using C = typename RT<R>::C;
   using V4 = typename RT<R>::V4;
   constexpr int T = 128, NX = 1024, SLOTS = NX / T, FS = 32 * 33;  // field stride in smem
@@ -327,9 +357,17 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
       V4 cur[SLOTS];
 #pragma unroll
       for (int sl = 0; sl < SLOTS; ++sl) cur[sl] = ld_stream(Mj + threadIdx.x + sl * T);
+      if (dir) {  // the cached director of component j ([c][3][N])
+        const R* dj = dir + (size_t)j * 3 * N + vox0 + threadIdx.x;
 #pragma unroll
-      for (int sl = 0; sl < SLOTS; ++sl)
-        pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
+        for (int sl = 0; sl < SLOTS; ++sl)
+          pol_add_d(acc[sl], (R)cur[sl].x, (R)cur[sl].y, dj[sl * T], dj[N + sl * T],
+                    dj[2 * N + sl * T], pp, j);
+      } else {
+#pragma unroll
+        for (int sl = 0; sl < SLOTS; ++sl)
+          pol_add(acc[sl], (R)cur[sl].x, (R)cur[sl].y, (R)cur[sl].z, (R)cur[sl].w, pp, j);
+      }
     }
 #pragma unroll
     for (int sl = 0; sl < SLOTS; ++sl) {
@@ -723,9 +761,12 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
   for (int i = t; i < (NX == 1024 ? 1024 : 512); i += blockDim.x) tw4[i] = tw4_g[i];
   __syncthreads();
   __shared__ float ang_ce[KMAX], ang_se[KMAX];  // indexed by a run-time angle
-  if (t < KMAX) {
-    ang_ce[t] = ang.ce[t];
-    ang_se[t] = ang.se[t];
+  if (t == 0) {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {  // constant indices: the parameters stay in place
+      ang_ce[i] = ang.ce[i];
+      ang_se[i] = ang.se[i];
+    }
   }
   __syncthreads();
   const int nk = ang.n;
@@ -2223,6 +2264,26 @@ __global__ void k_validate(const R* __restrict__ M, long long n_entries, int* __
   if (!ok) atomicOr(flag, 1);
 }
 
+// The director d = (cos phi sin theta, sin phi sin theta, cos theta) of
+// every component and voxel (Eq. (rotBCD)), dir[j][3][N]: it depends on the
+// morphology alone, so FP64 runs evaluate its sines and cosines once per
+// morphology rather than once per voxel, component, energy and angle.
+template <typename R>
+__global__ void k_director(const typename RT<R>::V4* __restrict__ M, long long n_entries,
+                           long long N, R* __restrict__ dir) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n_entries) return;
+  const typename RT<R>::V4 m = M[i];
+  R sp, cp, st, ct;
+  sincos_r((R)m.z, &sp, &cp);
+  sincos_r((R)m.w, &st, &ct);
+  const long long j = i / N, v = i - j * N;
+  R* d = dir + (size_t)j * 3 * N + v;
+  d[0] = cp * st;
+  d[N] = sp * st;
+  d[2 * N] = ct;
+}
+
 // ================================================================ launchers
 static inline int ilog2(long long n) {
   int l = 0;
@@ -2234,7 +2295,7 @@ static inline unsigned grid1(long long n, int t) { return (unsigned)((n + t - 1)
 template <typename R, int T, int EC, bool DO_FFT, int LOGNX, bool FROM_NT>
 static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                                  void* p, const void* twx, const void* nt, long long row_begin,
-                                 long long row_count, cudaStream_t s) {
+                                 long long row_count, cudaStream_t s, const void* dir) {
   using C = typename RT<R>::C;
   const long long N = (long long)nx * ny * nz;
   // Without the FFT the voxels are independent: treat them as N rows of one.
@@ -2255,36 +2316,41 @@ static cudaError_t pol_fftx_impl(const void* M, int nx, int ny, int nz, const Po
   if (nrows <= 0) return cudaSuccess;
   kern<<<grid1(nrows, rows), T, smem, s>>>((const typename RT<R>::V4*)M, N, lognx, row_begin,
                                            row_begin + nrows, pp, (C*)p, (const C*)twx,
-                                           tw_in_smem, (const C*)nt);
+                                           tw_in_smem, (const C*)nt, (const R*)dir);
   return cudaGetLastError();
 }
 
 template <typename R, bool FROM_NT>
 static cudaError_t pol_fftx_dispatch(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                                      bool do_fft, void* p, const void* twx, const void* nt,
-                                     long long rb, long long rc, cudaStream_t s) {
+                                     long long rb, long long rc, cudaStream_t s, const void* dir) {
   if (!do_fft)
-    return pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+    return pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s,
+                                                           dir);
   if (nx & (nx - 1)) {
     // other lengths: polarisation alone, then the mixed-radix x-FFT of the
     // 3 ny nz rows in place
     if (rc >= 0) return cudaErrorInvalidValue;
-    cudaError_t e =
-        pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, 0, -1, s);
+    cudaError_t e = pol_fftx_impl<R, 256, 1024, false, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt,
+                                                                    0, -1, s, dir);
     if (e != cudaSuccess) return e;
     return launch_row_fft<R>(p, nx, 3LL * ny * nz, twx, s);
   }
-#define RSX_POL(L)                                                                                \
-  case L:                                                                                         \
-    return pol_fftx_impl<R, 256, 1024, true, L, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+#define RSX_POL(L)                                                                          \
+  case L:                                                                                   \
+    return pol_fftx_impl<R, 256, 1024, true, L, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, \
+                                                         s, dir);
   switch (ilog2(nx)) {
     RSX_POL(6) RSX_POL(7) RSX_POL(8) RSX_POL(9) RSX_POL(10)
     case 11:
-      return pol_fftx_impl<R, 256, 2048, true, 11, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+      return pol_fftx_impl<R, 256, 2048, true, 11, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc,
+                                                            s, dir);
     case 12:
-      return pol_fftx_impl<R, 512, 4096, true, 12, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+      return pol_fftx_impl<R, 512, 4096, true, 12, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc,
+                                                            s, dir);
     default:
-      return pol_fftx_impl<R, 256, 1024, true, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc, s);
+      return pol_fftx_impl<R, 256, 1024, true, -1, FROM_NT>(M, nx, ny, nz, pp, p, twx, nt, rb, rc,
+                                                            s, dir);
   }
 #undef RSX_POL
 }
@@ -2292,9 +2358,9 @@ static cudaError_t pol_fftx_dispatch(const void* M, int nx, int ny, int nz, cons
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                             bool do_fft, void* p, const void* twx, cudaStream_t s,
-                            long long row_begin, long long row_count) {
+                            long long row_begin, long long row_count, const void* dir) {
   return pol_fftx_dispatch<R, false>(M, nx, ny, nz, pp, do_fft, p, twx, nullptr, row_begin,
-                                     row_count, s);
+                                     row_count, s, dir);
 }
 
 template <typename R>
@@ -2302,12 +2368,22 @@ cudaError_t launch_ntp_fftx(const void* nt, int nx, int ny, int nz, const PolPar
                             bool do_fft, void* p, const void* twx, cudaStream_t s,
                             long long row_begin, long long row_count) {
   return pol_fftx_dispatch<R, true>(nullptr, nx, ny, nz, pp, do_fft, p, twx, nt, row_begin,
-                                    row_count, s);
+                                    row_count, s, nullptr);
+}
+
+template <typename R>
+cudaError_t launch_director(const void* M, long long n_entries, long long N, void* dir,
+                            cudaStream_t s) {
+  if (n_entries == 0) return cudaSuccess;
+  k_director<R><<<grid1(n_entries, 256), 256, 0, s>>>((const typename RT<R>::V4*)M, n_entries, N,
+                                                      (R*)dir);
+  return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int nz,
-                             const PolParams<R>& pp, void* p, const void* tw4, cudaStream_t s) {
+                             const PolParams<R>& pp, void* p, const void* tw4, cudaStream_t s,
+                             const void* dir) {
   using C = typename RT<R>::C;
   if (nx != 1024) return cudaErrorInvalidValue;
   const long long N = (long long)nx * ny * nz, nrows = (long long)ny * nz;
@@ -2317,13 +2393,13 @@ cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int 
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nrows, 128, smem, s>>>(nullptr, N, nrows, pp, (C*)p, (const C*)tw4,
-                                            (const C*)nt);
+                                            (const C*)nt, nullptr);
   } else {
     auto kern = k_pol_fft4s<R, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)nrows, 128, smem, s>>>((const typename RT<R>::V4*)M, N, nrows, pp, (C*)p,
-                                            (const C*)tw4, nullptr);
+                                            (const C*)tw4, nullptr, (const R*)dir);
   }
   return cudaGetLastError();
 }
@@ -2374,10 +2450,11 @@ static cudaError_t pol_fft4s_tma_multi_impl(const void* M, int ny, int nz,
                                             const PolParams<float>& pp, const XAngles& ang,
                                             void* p, long long pstride, const void* tw,
                                             int* err, int n_sm, unsigned poll, cudaStream_t s) {
-  // 4 stages of one (row, component) slice, 4 row buffers, 8 polarisation
-  // warps (NX / 256 voxels per thread), two transform groups and a producer
-  // warp: one block per SM, ~171 KB of shared memory for 1024-point rows
-  constexpr int S = 4, NPB = 4, PW = 8, FG = 2;
+  // 3 stages of one (row, component) slice, 6 row buffers, 8 polarisation
+  // warps (NX / 256 voxels per thread), three transform groups and a
+  // producer warp: one block per SM, ~205 KB of shared memory for
+  // 1024-point rows
+  constexpr int S = 3, NPB = 6, PW = 8, FG = 3;
   if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > kMaxXAngles)
     return cudaErrorInvalidValue;
   const long long N = (long long)NX * ny * nz, nrows = (long long)ny * nz;
@@ -2604,7 +2681,10 @@ template <typename R>
 cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBatches& bt,
                            const void* tw, cudaStream_t s) {
   if (L == 1) return cudaSuccess;
-  if (L & (L - 1)) {  // any other length: the mixed-radix passes
+  // the Stockham column kernels take power-of-two lengths and row widths
+  // (their tiles are power-of-two column groups); anything else takes the
+  // mixed-radix passes
+  if ((L & (L - 1)) || (W & (W - 1))) {
     const AnyLines ln = {bt.nbatch * W, W, bt.bdiv, bt.stride_hi, bt.stride_lo, bt.base, 1, S};
     return launch_fft_any<R>(p, p, L, ln, tw, s);
   }
@@ -2809,7 +2889,9 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
 
 #define RSX_INSTANTIATE(R)                                                                        \
   template cudaError_t launch_pol_fftx<R>(const void*, int, int, int, const PolParams<R>&, bool,  \
-                                          void*, const void*, cudaStream_t, long long, long long);\
+                                          void*, const void*, cudaStream_t, long long, long long, \
+                                          const void*);                                          \
+  template cudaError_t launch_director<R>(const void*, long long, long long, void*, cudaStream_t);\
   template cudaError_t launch_row_fft<R>(void*, int, long long, const void*, cudaStream_t,         \
                                          const void*);                                           \
   template cudaError_t launch_row_fft4s<R>(void*, long long, const void*, cudaStream_t,           \
@@ -2840,7 +2922,8 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                          const PolParams<R>&, void*, cudaStream_t);               \
   template cudaError_t launch_nt_restore<R>(const void*, void*, long long, double, cudaStream_t); \
   template cudaError_t launch_pol_fft4s<R>(const void*, const void*, int, int, int,               \
-                                           const PolParams<R>&, void*, const void*, cudaStream_t); \
+                                           const PolParams<R>&, void*, const void*, cudaStream_t, \
+                                           const void*);                                         \
   template cudaError_t launch_col_fft4s<R>(void*, long long, long long, const ColBatches&,         \
                                            const void*, cudaStream_t);                            \
   template cudaError_t launch_zbins5<R>(const void*, int, int, int, const Geo<R>*, const void*,    \

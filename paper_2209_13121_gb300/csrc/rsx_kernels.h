@@ -116,10 +116,18 @@ int check_device_pointer(const void* p, int dev, const char* what);
 
 // Rows are (z, y) pairs; row_begin / row_count restrict the launch to a
 // range of rows (a group of z-slices); row_count < 0 means all rows.
+// dir: the morphology's cached director ([c][3][N] Real, launch_director)
+// or nullptr (computed from phi and theta).
 template <typename R>
 cudaError_t launch_pol_fftx(const void* M, int nx, int ny, int nz, const PolParams<R>& pp,
                             bool do_fft, void* p, const void* twx, cudaStream_t s,
-                            long long row_begin = 0, long long row_count = -1);
+                            long long row_begin = 0, long long row_count = -1,
+                            const void* dir = nullptr);
+// The director of every component and voxel, dir[c][3][N], from M
+// (n_entries = c N).
+template <typename R>
+cudaError_t launch_director(const void* M, long long n_entries, long long N, void* dir,
+                            cudaStream_t s);
 // Algorithm 2: p = N_t . e from nt[5][N] (xx, xy, yy, xz, yz), fused with
 // the x-FFT like launch_pol_fftx.
 template <typename R>
@@ -149,7 +157,8 @@ cudaError_t launch_ewald_linear(const void* bins, int nx, int ny, const Geo<R>* 
 // tw4[k2 * 32 + n1] = exp(-2 pi i n1 k2 / 1024).
 template <typename R>
 cudaError_t launch_pol_fft4s(const void* M, const void* nt, int nx, int ny, int nz,
-                             const PolParams<R>& pp, void* p, const void* tw4, cudaStream_t s);
+                             const PolParams<R>& pp, void* p, const void* tw4, cudaStream_t s,
+                             const void* dir = nullptr);
 template <typename R>
 cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches& bt,
                              const void* tw4, cudaStream_t s);

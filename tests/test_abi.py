@@ -64,7 +64,7 @@ def test_workspace_bytes_follows_table1(lib):
         assert rsx.workspace_bytes(rsx.make_config(nx, ny, nz, c, 5.0, angle_batch=k)) == \
             b + (k - 1) * 3 * N * 8
     # the default batch, and no batch where the multi-angle pass does not apply
-    assert rsx.workspace_bytes(rsx.make_config(nx, ny, nz, c, 5.0)) == b + 3 * 3 * N * 8
+    assert rsx.workspace_bytes(rsx.make_config(nx, ny, nz, c, 5.0)) == b + 7 * 3 * N * 8
     for shape in ((2048, 2048, 64), (1024, 1024, 100)):
         one = rsx.make_config(*shape, c, 5.0, angle_batch=1)
         assert rsx.workspace_bytes(rsx.make_config(*shape, c, 5.0, angle_batch=4)) == \
