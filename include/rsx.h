@@ -81,10 +81,10 @@ typedef struct rsx_config {
                       /* one read of the morphology (1..RSX_MAX_ANGLE_BATCH; */
                       /* 0 = the largest batch whose p buffers fit in 32    */
                       /* GiB).  Each extra angle holds another 3 N complex  */
-                      /* p buffer.  Used on FP32                            */
-                      /* grids with nx and ny 512 or 1024, nx a multiple of  */
-                      /* 16 and nz a power of two up to 1024; elsewhere 1.   */
-                      /* Each angle's arithmetic is unchanged (Algorithm 1's */
+                      /* p buffer.  Used by FP32 Algorithm 1 with nx = 512   */
+                      /* or 1024 (up to 8) and nx = 2048 (up to 2; larger    */
+                      /* values are lowered to that); elsewhere 1.  Each     */
+                      /* angle's arithmetic is unchanged (Algorithm 1's      */
                       /* angle loop, the morphology sums shared).            */
 } rsx_config;
 

@@ -153,6 +153,7 @@ struct rsx_context {
   void* twy = nullptr;
   void* twz = nullptr;
   void* tw4 = nullptr;  // four-step twiddles [k2][n1] for 1024-point axes
+  void* tw2k = nullptr; // 2048-point rows: the four-step table, then W2048^n (n < 1024)
   // tensor maps of the p (3 fields) and, for algorithm 3, ft (5 fields)
   // buffers for the TMA y pass (FP32, ny = 1024); valid when the flag is set
   CUtensorMap tmap_p;
@@ -186,7 +187,7 @@ namespace {
 
 void free_all(rsx_context* c) {
   void* ptrs[] = {c->M_owned, c->p,    c->img, c->acc,  c->geo,  c->twx, c->twy,
-                  c->twz,     c->tw4,  c->flag, c->err, c->part, c->imgs, c->dir};
+                  c->twz,     c->tw4,  c->flag, c->err, c->part, c->imgs, c->dir, c->tw2k};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -257,6 +258,26 @@ int upload_tw4(rsx_context* c) {
     std::vector<float> f(tw.begin(), tw.end());
     RSX_CK(cudaMemcpy(c->tw4, f.data(), 8 * 1024, cudaMemcpyHostToDevice), "twiddle upload");
   }
+  return RSX_OK;
+}
+
+// Twiddles of the 2048-point row transform (FP32): the four-step table
+// W1024^(n1 k2) at [k2 * 32 + n1], then W2048^n for n < 1024.
+int upload_tw2k(rsx_context* c) {
+  std::vector<float> tw(2 * 2048);
+  for (int k2 = 0; k2 < 32; ++k2)
+    for (int n1 = 0; n1 < 32; ++n1) {
+      const double a = -2.0 * kPi * (double)(n1 * k2) / 1024.0;
+      tw[2 * (k2 * 32 + n1)] = (float)cos(a);
+      tw[2 * (k2 * 32 + n1) + 1] = (float)sin(a);
+    }
+  for (int n = 0; n < 1024; ++n) {
+    const double a = -2.0 * kPi * (double)n / 2048.0;
+    tw[2 * (1024 + n)] = (float)cos(a);
+    tw[2 * (1024 + n) + 1] = (float)sin(a);
+  }
+  RSX_CK(cudaMalloc(&c->tw2k, 8 * 2048), "twiddle table");
+  RSX_CK(cudaMemcpy(c->tw2k, tw.data(), 8 * 2048, cudaMemcpyHostToDevice), "twiddle upload");
   return RSX_OK;
 }
 
@@ -605,16 +626,23 @@ static size_t part_bytes(const rsx_config* cfg) {
 
 // The angle batch a config gets: the multi-angle x pass serves FP32
 // Algorithm 1 on the shapes of the bulk-copy x pass and the fused y+z pass.
+// The multi-angle x pass serves FP32 Algorithm 1 with nx = 512, 1024 or
+// 2048 (2048-point rows: at most 2 angles per pass).
+static int angle_batch_cap(const rsx_config* cfg) {
+  if (cfg->precision != 32 || cfg->algorithm != 1) return 0;
+  if (cfg->nx == 512 || cfg->nx == 1024) return RSX_MAX_ANGLE_BATCH;
+  return cfg->nx == 2048 ? 2 : 0;
+}
+
 static int angle_batch_of(const rsx_config* cfg) {
-  const bool ok = cfg->precision == 32 && cfg->algorithm == 1 &&
-                  (cfg->nx == 1024 || cfg->nx == 512) && rsx::yz_fusable(cfg->nx, cfg->ny, cfg->nz);
-  if (!ok) return 1;
-  if (cfg->angle_batch > 0) return cfg->angle_batch;
-  // default: the largest batch up to RSX_MAX_ANGLE_BATCH whose p buffers
-  // (3 N complex float each) fit in 32 GiB
+  const int cap = angle_batch_cap(cfg);
+  if (cap == 0) return 1;
+  if (cfg->angle_batch > 0) return cfg->angle_batch < cap ? cfg->angle_batch : cap;
+  // default: the largest batch up to the cap whose p buffers (3 N complex
+  // float each) fit in 32 GiB
   const double p_bytes = 3.0 * cfg->nx * cfg->ny * cfg->nz * 8.0;
   const int k = (int)((double)(32LL << 30) / p_bytes);
-  return k < 1 ? 1 : k > RSX_MAX_ANGLE_BATCH ? RSX_MAX_ANGLE_BATCH : k;
+  return k < 1 ? 1 : k > cap ? cap : k;
 }
 
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
@@ -720,6 +748,11 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     return rc;
   }
   if ((cfg->nx == 1024 || cfg->ny == 1024) && (rc = upload_tw4(c))) {
+    free_all(c);
+    delete c;
+    return rc;
+  }
+  if (cfg->nx == 2048 && angle_batch_cap(cfg) && (rc = upload_tw2k(c))) {
     free_all(c);
     delete c;
     return rc;
@@ -994,7 +1027,8 @@ int run_energy_angles_batched(rsx_context* c, int ie, double start, double inc, 
   if (rc) return rc;
   const PolParams<float> pp = make_params<float>(c, ie, 0.0, 0);
   const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
-  const void* tw = g.nx == 1024 ? c->tw4 : c->twx;
+  const void* tw = g.nx == 1024 ? c->tw4 : g.nx == 2048 ? c->tw2k : c->twx;
+  const bool fused = c->part && c->has_tmap_pz;
   for (int a0 = 0; a0 < nang; a0 += c->kx) {
     const int nk = nang - a0 < c->kx ? nang - a0 : c->kx;
     rsx::XAngles ang;
@@ -1018,15 +1052,25 @@ int run_energy_angles_batched(rsx_context* c, int ie, double start, double inc, 
         dc[0] = (float)(ref * cos(alpha[k]));
         dc[1] = (float)(ref * sin(alpha[k]));
       }
-      long long L = 0;
-      {
-        PhaseTimer pt(c, RSX_PHASE_FFTY, s);
-        RSX_CK(fused_yz(c, &c->tmap_pz[k], 3, &L, s), "y-FFT + z-bins kernel");
-      }
-      {
+      if (fused) {  // y-FFT and the pruned z transform in one pass
+        long long L = 0;
+        {
+          PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+          RSX_CK(fused_yz(c, &c->tmap_pz[k], 3, &L, s), "y-FFT + z-bins kernel");
+        }
         PhaseTimer pt(c, RSX_PHASE_EWALD, s);
         RSX_CK(rsx::launch_ewald_bins(c->part, g.nx, g.ny, g.nz, L, (const Geo<float>*)c->geo,
                                       dc[0], dc[1], dc[2], (float*)c->img, s),
+               "Ewald kernel");
+      } else {  // y-FFT of angle k's p in place, then the pruned z transform
+        void* pk = (char*)c->p + (size_t)k * 3 * c->N * sizeof(float2);
+        if (g.ny > 1) {
+          PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+          RSX_CK(launch_y_fft<float>(c, pk, 3, s), "y-FFT kernel");
+        }
+        PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+        RSX_CK(rsx::launch_ewald<float>(pk, g.nx, g.ny, g.nz, (const Geo<float>*)c->geo, c->twz,
+                                        true, dc, c->img, s, c->err, c->wait_polls),
                "Ewald kernel");
       }
       PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
@@ -1041,7 +1085,7 @@ template <typename R>
 int run_energy_angles(rsx_context* c, int ie, double start, double inc, int nang, int rotation,
                       cudaStream_t s) {
   if constexpr (sizeof(R) == 4) {
-    if (c->kx > 1 && c->cfg.algorithm == 1 && c->part && c->has_tmap_pz && c->n_sm > 0 &&
+    if ((c->kx > 1 || c->cfg.nx == 2048) && angle_batch_cap(&c->cfg) && c->n_sm > 0 &&
         ((uintptr_t)c->M & 15) == 0)
       return run_energy_angles_batched(c, ie, start, inc, nang, rotation, s);
   }

@@ -411,29 +411,54 @@ __global__ void __launch_bounds__(128, sizeof(R) == 4 ? 4 : 1) k_pol_fft4s(const
 //  the transpose, lanes k2 and k2 + 16 share the 32-point DFT over n1 (even
 //  n1 on the lower lane, odd on the upper), which leaves k1 = k and
 //  k1 = 16 + k on the two lanes.
+// One warp's 1024-point four-step FFT of F (dense elements 0..1023, then
+// transposed in place as [32][33]); output k goes to out[OS * k].
+template <int OS, typename Release>
+__device__ __forceinline__ void fft1024_warp(float2* F, const float2* tw4, float2* out, int lane,
+                                             Release release) {
+  using C = float2;
+  C v[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
+  dft32(v);
+#pragma unroll
+  for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+  __syncwarp();
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
+  __syncwarp();
+#pragma unroll
+  for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
+  __syncwarp();
+  release();
+  dft32(v);
+  C* o = out + OS * lane;
+#pragma unroll
+  for (int k1 = 0; k1 < 32; ++k1) o[OS * 32 * k1] = v[k1];
+}
+
 template <int NX, typename Release>
 __device__ __forceinline__ void xfft_row(float2* F, const float2* tw4, float2* out_row, int lane,
                                          Release release) {
   using C = float2;
   C v[32];
   if constexpr (NX == 1024) {
-#pragma unroll
-    for (int n2 = 0; n2 < 32; ++n2) v[n2] = F[lane + 32 * n2];
-    dft32(v);
-#pragma unroll
-    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw4[k2 * 32 + lane]);
+    fft1024_warp<1>(F, tw4, out_row, lane, release);
+  } else if constexpr (NX == 2048) {
+    // decimation in frequency: X[2k] and X[2k + 1] are the 1024-point
+    // transforms of a[n] = x[n] + x[n + 1024] and b[n] = (x[n] - x[n + 1024])
+    // W2048^n; F holds x[0..1024) at 0.. and x[1024..2048) at 1056..,
+    // tw4[1024 + n] = W2048^n
+#pragma unroll 8
+    for (int j = 0; j < 32; ++j) {
+      const int n = lane + 32 * j;
+      const C a = F[n], b = F[1056 + n];
+      F[n] = cadd(a, b);
+      F[1056 + n] = cmul(csub(a, b), tw4[1024 + n]);
+    }
     __syncwarp();
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) F[k2 * 33 + lane] = v[k2];
-    __syncwarp();
-#pragma unroll
-    for (int n1 = 0; n1 < 32; ++n1) v[n1] = F[lane * 33 + n1];
-    __syncwarp();
-    release();
-    dft32(v);
-    C* out = out_row + lane;
-#pragma unroll
-    for (int k1 = 0; k1 < 32; ++k1) out[32 * k1] = v[k1];
+    fft1024_warp<2>(F, tw4, out_row, lane, [] {});
+    fft1024_warp<2>(F + 1056, tw4, out_row + 1, lane, release);
   } else {
 #pragma unroll
     for (int n2 = 0; n2 < 16; ++n2) v[n2] = F[lane + 32 * n2];
@@ -693,30 +718,27 @@ __device__ __forceinline__ void tacc_add(TAcc& acc, float v, float s, float phi,
   acc.t[4][0] += hyr * dz; acc.t[4][1] += hyi * dz;
 }
 
-// p for e = (ce, se, 0) from the sums (ar + i ai = (sum v^2 - 1) +
-// sum v^2 tau'(2 + tau'), the reference constant left out), in the frame of
-// `literal`, as pol_final forms it from T e.
-__device__ __forceinline__ void p_from_tacc(float ar, float ai, const float (&t)[5][2], float ce,
-                                            float se, bool literal, float2 out[3]) {
-  const float inv = float(1.0 / kFourPi);
-  const float b0r = ce * t[0][0] + se * t[1][0], b0i = ce * t[0][1] + se * t[1][1];
-  const float b1r = ce * t[1][0] + se * t[2][0], b1i = ce * t[1][1] + se * t[2][1];
-  const float b2r = ce * t[3][0] + se * t[4][0], b2i = ce * t[3][1] + se * t[4][1];
-  float p0r, p0i, p1r, p1i;
+// p for e = (c, s, 0) = (cos a, sin a, 0) from the sums, already divided by
+// 4 pi (ar + i ai = [(sum v^2 - 1) + sum v^2 tau'(2 + tau')] / (4 pi), the
+// reference constant left out; t = T / (4 pi)), in the frame of `literal`:
+// with b = T e,
+//   literal (p <- U^T p):  p0 = ar + c b_x + s b_y = ar + c^2 Txx + 2cs Txy + s^2 Tyy
+//                          p1 = -s b_x + c b_y    = cs (Tyy - Txx) + (c^2 - s^2) Txy
+//   lab:                   p0 = c ar + b_x,  p1 = s ar + b_y,
+//   both:                  p2 = b_z = c Txz + s Tyz.
+__device__ __forceinline__ void p_from_tacc(float ar, float ai, const float (&t)[5][2], float c,
+                                            float s, bool literal, float2 out[3]) {
   if (literal) {
-    p0r = ar + ce * b0r + se * b1r;
-    p0i = ai + ce * b0i + se * b1i;
-    p1r = -se * b0r + ce * b1r;
-    p1i = -se * b0i + ce * b1i;
+    const float c2 = c * c, s2 = s * s, cs2 = 2.f * c * s, cs = c * s, d2 = c2 - s2;
+    out[0] = make_float2(fmaf(s2, t[2][0], fmaf(cs2, t[1][0], fmaf(c2, t[0][0], ar))),
+                         fmaf(s2, t[2][1], fmaf(cs2, t[1][1], fmaf(c2, t[0][1], ai))));
+    out[1] = make_float2(fmaf(d2, t[1][0], cs * (t[2][0] - t[0][0])),
+                         fmaf(d2, t[1][1], cs * (t[2][1] - t[0][1])));
   } else {
-    p0r = ar * ce + b0r;
-    p0i = ai * ce + b0i;
-    p1r = ar * se + b1r;
-    p1i = ai * se + b1i;
+    out[0] = make_float2(fmaf(c, ar + t[0][0], s * t[1][0]), fmaf(c, ai + t[0][1], s * t[1][1]));
+    out[1] = make_float2(fmaf(s, ar + t[2][0], c * t[1][0]), fmaf(s, ai + t[2][1], c * t[1][1]));
   }
-  out[0] = make_float2(p0r * inv, p0i * inv);
-  out[1] = make_float2(p1r * inv, p1i * inv);
-  out[2] = make_float2(b2r * inv, b2i * inv);
+  out[2] = make_float2(fmaf(c, t[3][0], s * t[4][0]), fmaf(c, t[3][1], s * t[4][1]));
 }
 
 // The Algorithm 1 x pass for up to KMAX e-field angles per read of the
@@ -737,16 +759,22 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
     XAngles ang, float2* __restrict__ p, long long pstride, const float2* __restrict__ tw4_g,
     int* __restrict__ err, unsigned poll) {
   using C = float2;
-  static_assert(NX == 1024 || NX == 512, "row length");
+  static_assert(NX == 1024 || NX == 512 || NX == 2048, "row length");
   static_assert(KMAX <= kMaxXAngles, "angle set");
-  constexpr int TP = 32 * PW, SL = NX / TP, FS = (NX / 32) * 33, NB = TP + 96;
-  static_assert(NX % TP == 0 && 1 + 2 * NPB <= 16 && NPB % FG == 0, "layout");
-  constexpr unsigned kPoll = 1u << 22, kStageBytes = NX * sizeof(float4);
+  // a stage is one component of a row segment of SV voxels; 2048-point rows
+  // come in H = 2 segments, whose fields sit at 0 and 1056 of a row buffer
+  constexpr int SV = NX > 1024 ? 1024 : NX, H = NX / SV;
+  constexpr int TP = 32 * PW, SL = SV / TP, NB = TP + 96;
+  constexpr int FS = NX == 2048 ? 2 * 1056 : (NX / 32) * 33;
+  constexpr int NTW = NX == 2048 ? 2048 : NX;  // twiddle table entries
+  static_assert(SV % TP == 0 && 1 + 2 * NPB <= 16 && NPB % FG == 0, "layout");
+  constexpr unsigned kPoll = 1u << 22, kStageBytes = SV * sizeof(float4);
   extern __shared__ __align__(128) unsigned char smem_a128[];
-  float4* stage = reinterpret_cast<float4*>(smem_a128);  // [S][NX]
-  C* P = reinterpret_cast<C*>(stage + S * NX);            // [NPB][3][FS]
-  C* tw4 = P + NPB * 3 * FS;                               // [32][32] or [512]
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(tw4 + 1024);
+  float4* stage = reinterpret_cast<float4*>(smem_a128);  // [S][SV]
+  C* P = reinterpret_cast<C*>(stage + S * SV);            // [NPB][3][FS]
+  C* tw4 = P + NPB * 3 * FS;                               // [max(NTW, 1024)]
+  unsigned long long* full =
+      reinterpret_cast<unsigned long long*>(tw4 + (NTW > 1024 ? NTW : 1024));
   unsigned long long* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
@@ -758,8 +786,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
     *abort_flag = 0;
     fence_proxy_async();
   }
-  for (int i = t; i < (NX == 1024 ? 1024 : 512); i += blockDim.x) tw4[i] = tw4_g[i];
-  __syncthreads();
+  for (int i = t; i < NTW; i += blockDim.x) tw4[i] = tw4_g[i];
   __shared__ float ang_ce[KMAX], ang_se[KMAX];  // indexed by a run-time angle
   if (t == 0) {
 #pragma unroll
@@ -776,8 +803,9 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
 
   if (w == PW + 3 * FG) {  // producer warp, one lane (as in k_pol_fft4s_tma)
     if (lane != 0) return;
-    const int G = (int)nmine * per_row;
-    int g = 0, slot = 0, k = 0, j = 0;
+    // stage g = (row rr, segment h, component j), j fastest
+    const int G = (int)nmine * H * per_row;
+    int g = 0, slot = 0, k = 0, j = 0, h = 0;
     long long row = blockIdx.x;
     for (; g < G; ++g) {
       if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), poll)) {
@@ -786,9 +814,13 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
         break;
       }
       mbar_expect_tx(&full[slot], kStageBytes);
-      bulk_g2s(stage + slot * NX, M + (size_t)j * N + (size_t)row * NX, kStageBytes, &full[slot]);
+      bulk_g2s(stage + slot * SV, M + (size_t)j * N + (size_t)row * NX + h * SV, kStageBytes,
+               &full[slot]);
       if (++slot == S) slot = 0, ++k;
-      if (++j == per_row) j = 0, row += gridDim.x;
+      if (++j == per_row) {
+        j = 0;
+        if (++h == H) h = 0, row += gridDim.x;
+      }
     }
     for (int d = g - 1; d >= 0 && d >= g - S; --d)
       mbar_wait_bounded(&full[d % S], (unsigned)((d / S) & 1), kPoll);
@@ -798,52 +830,65 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
   if (w < PW) {  // polarisation warps
     bool failed = false;
     int slot = 0, ph = 0;
-    int u = 0;  // row buffers handed on so far
     for (int rr = 0; rr < (int)nmine; ++rr) {
-      TAcc acc[SL];
+      for (int h = 0; h < H; ++h) {
+        TAcc acc[SL];
 #pragma unroll
-      for (int sl = 0; sl < SL; ++sl) tacc_zero(acc[sl]);
-      for (int j = 0; j < per_row; ++j) {
-        const int cs = slot, cph = ph;
-        if (++slot == S) slot = 0, ph ^= 1;
-        failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
-        if (failed) break;
-        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, poll))) {
-          failed = true;
-          atomicOr(err, 1);
-          *abort_flag = 1;
-          break;
+        for (int sl = 0; sl < SL; ++sl) tacc_zero(acc[sl]);
+        for (int j = 0; j < per_row; ++j) {
+          const int cs = slot, cph = ph;
+          if (++slot == S) slot = 0, ph ^= 1;
+          failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
+          if (failed) break;
+          if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, poll))) {
+            failed = true;
+            atomicOr(err, 1);
+            *abort_flag = 1;
+            break;
+          }
+          const float4* st = stage + cs * SV;
+          float4 cur[SL];
+#pragma unroll
+          for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&empty[cs]);
+#pragma unroll
+          for (int sl = 0; sl < SL; ++sl)
+            tacc_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
         }
-        const float4* st = stage + cs * NX;
-        float4 cur[SL];
+        // (sum v^2 - 1) first, then the small optical part (FP32 accuracy);
+        // everything divided by 4 pi once per voxel
+        const float inv = float(1.0 / kFourPi);
 #pragma unroll
-        for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[cs]);
+        for (int sl = 0; sl < SL; ++sl) {
+          acc[sl].aw = ((acc[sl].aw - 1.f) + acc[sl].as[0]) * inv;
+          acc[sl].as[1] *= inv;
 #pragma unroll
-        for (int sl = 0; sl < SL; ++sl)
-          tacc_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
-      }
-      // (sum v^2 - 1) first, then the small optical part (FP32 accuracy)
-#pragma unroll
-      for (int sl = 0; sl < SL; ++sl) acc[sl].aw = (acc[sl].aw - 1.f) + acc[sl].as[0];
-      for (int k = 0; k < nk; ++k, ++u) {
-        const int i = u % NPB;
-        if (u >= NPB) named_bar_sync(1 + NPB + i, NB);  // slot's previous transforms done
-        if (!failed) {
-          C* Pi = P + i * 3 * FS;
-          const float ce = ang_ce[k], se = ang_se[k];
-#pragma unroll
-          for (int sl = 0; sl < SL; ++sl) {
-            const int e = t + sl * TP;
-            C out[3];
-            p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, out);
-            Pi[e] = out[0];
-            Pi[FS + e] = out[1];
-            Pi[2 * FS + e] = out[2];
+          for (int q = 0; q < 5; ++q) {
+            acc[sl].t[q][0] *= inv;
+            acc[sl].t[q][1] *= inv;
           }
         }
-        named_bar_arrive(1 + i, NB);
+        // row buffer u = rr * nk + k holds angle k of row rr; with H > 1 all
+        // nk buffers of the row stay open across its segments (nk <= NPB)
+        for (int k = 0; k < nk; ++k) {
+          const int u = rr * nk + k, i = u % NPB;
+          if (h == 0 && u >= NPB) named_bar_sync(1 + NPB + i, NB);  // previous use done
+          if (!failed) {
+            C* Pi = P + i * 3 * FS + h * 1056;
+            const float ce = ang_ce[k], se = ang_se[k];
+#pragma unroll
+            for (int sl = 0; sl < SL; ++sl) {
+              const int e = t + sl * TP;
+              C out[3];
+              p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, out);
+              Pi[e] = out[0];
+              Pi[FS + e] = out[1];
+              Pi[2 * FS + e] = out[2];
+            }
+          }
+          if (h == H - 1) named_bar_arrive(1 + i, NB);
+        }
       }
     }
     return;
@@ -1061,8 +1106,8 @@ __global__ void __launch_bounds__(T) k_row_fft(const typename RT<R>::C* src,
 // transforms TX = 2^logTX adjacent columns (coalesced rows of TX complex
 // values) of one batch; the tile arrives by cp.async, NLD copies per thread
 // in flight, without passing registers.
-template <typename R, int T, int EC, int LOGL>
-__global__ void __launch_bounds__(T, 3) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
+template <typename R, int T, int EC, int LOGL, int MINB = 3>
+__global__ void __launch_bounds__(T, MINB) k_col_fft(typename RT<R>::C* __restrict__ data, int logL_rt,
                                                long long S, int logTX_rt, long long ntiles,
                                                long long bdiv, long long stride_hi,
                                                long long stride_lo, long long base_off,
@@ -1100,6 +1145,64 @@ __global__ void __launch_bounds__(T, 3) k_col_fft(typename RT<R>::C* __restrict_
   for (int it = 0; it < NLD; ++it) {
     const int e = threadIdx.x + it * T;
     if (e < nel) base[(size_t)(e >> logTX) * S + (e & (TX - 1))] = buf[padi(e)];
+  }
+}
+
+// 2048-point column FFTs (FP32): one CTA of 512 threads per tile of 8
+// adjacent columns of one batch.  2048 = 64 x 32 with n = n1 + 64 n2 and
+// k = k2 + 32 k1:
+//   X[k2 + 32 k1] = sum_n1 W64^(n1 k1) W2048^(n1 k2) sum_n2 x[n1 + 64 n2] W32^(n2 k2).
+// Stage 1: thread (n1, col) loads its 32 samples straight from global memory
+// (32 loads in flight), does the 32-point DFT over n2 in registers, applies
+// W2048^(n1 k2) and writes T[k2][n1][col] (k2 rows padded by 8 elements, so
+// the stage-2 reads of both k2 halves of a warp fall in different banks).
+// Stage 2: threads (k2, col, h) and (k2, col, 1 - h), lanes 16 apart, take
+// the even (h = 0) and odd (h = 1) n1 of row k2: a 32-point DFT each, the odd
+// half times W64^k, and one shuffle exchange leaves X[k2 + 32 k] on the h = 0
+// lane and X[k2 + 32 (k + 32)] on the h = 1 lane.  tw[j] = W2048^j.
+__global__ void __launch_bounds__(512, 1) k_col_fft2k(float2* __restrict__ data, long long S,
+                                                      long long ntiles, long long bdiv,
+                                                      long long stride_hi, long long stride_lo,
+                                                      long long base_off,
+                                                      const float2* __restrict__ tw_g) {
+  using C = float2;
+  constexpr int TX = 8, KS = 64 * TX + 8;  // row stride of T (k2)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* T = reinterpret_cast<C*>(smem_raw);  // [32][KS]
+  C* tw = T + 32 * KS;                    // [2048]
+  const long long tile = (long long)blockIdx.x % ntiles;
+  const long long b = (long long)blockIdx.x / ntiles;
+  C* base = data + base_off + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo + tile * TX;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  // stage 1: col = lane & 7, n1 = 4 w + lane / 8
+  {
+    const int col = lane & 7, n1 = 4 * w + (lane >> 3);
+    C v[32];
+#pragma unroll
+    for (int n2 = 0; n2 < 32; ++n2) v[n2] = __ldcs(base + (size_t)(n1 + 64 * n2) * S + col);
+    for (int i = t; i < 2048; i += 512) tw[i] = tw_g[i];
+    dft32(v);
+    __syncthreads();  // twiddle table in place
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw[n1 * k2]);
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) T[k2 * KS + n1 * TX + col] = v[k2];
+  }
+  __syncthreads();
+  // stage 2: col = lane & 7, k2 = 2 w + (lane >> 3 & 1), h = lane >> 4
+  const int col = lane & 7, k2 = 2 * w + ((lane >> 3) & 1), h = lane >> 4;
+  C v[32];
+#pragma unroll
+  for (int m = 0; m < 32; ++m) v[m] = T[k2 * KS + (2 * m + h) * TX + col];
+  dft32(v);
+  C* out = base + (size_t)(k2 + 1024 * h) * S + col;
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const C mine = h ? cmul(v[k], tw[32 * k]) : v[k];  // E[k], or W64^k O[k]
+    C other;
+    other.x = __shfl_xor_sync(0xffffffffu, mine.x, 16);
+    other.y = __shfl_xor_sync(0xffffffffu, mine.y, 16);
+    out[(size_t)(32 * k) * S] = h ? csub(other, mine) : cadd(mine, other);
   }
 }
 
@@ -2450,17 +2553,24 @@ static cudaError_t pol_fft4s_tma_multi_impl(const void* M, int ny, int nz,
                                             const PolParams<float>& pp, const XAngles& ang,
                                             void* p, long long pstride, const void* tw,
                                             int* err, int n_sm, unsigned poll, cudaStream_t s) {
-  // 3 stages of one (row, component) slice, 6 row buffers, 8 polarisation
-  // warps (NX / 256 voxels per thread), three transform groups and a
-  // producer warp: one block per SM, ~205 KB of shared memory for
-  // 1024-point rows
-  constexpr int S = 3, NPB = 6, PW = 8, FG = 3;
-  if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > kMaxXAngles)
+  // 512- and 1024-point rows: 3 stages of one (row, component) slice, 6 row
+  // buffers, 8 polarisation warps (NX / 256 voxels per thread), three
+  // transform groups (the transforms are the larger share of the work; a
+  // fourth would cut the registers below what a transform needs) and a
+  // producer warp: one 576-thread block per SM, ~205 KB of shared memory
+  // for 1024-point rows.  2048-point rows: 1024-voxel segments, 2 row
+  // buffers of 50 KB (so at most 2 angles per launch), two transform
+  // groups, ~163 KB.
+  constexpr int S = 3, NPB = NX == 2048 ? 2 : 6, PW = 8, FG = NX == 2048 ? 2 : 3;
+  constexpr int FS = NX == 2048 ? 2 * 1056 : (NX / 32) * 33;
+  constexpr int SV = NX > 1024 ? 1024 : NX, NTW = NX == 2048 ? 2048 : 1024;
+  if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > kMaxXAngles ||
+      (NX == 2048 && ang.n > NPB))
     return cudaErrorInvalidValue;
   const long long N = (long long)NX * ny * nz, nrows = (long long)ny * nz;
   if (nrows <= 0) return cudaSuccess;
-  const size_t smem = (size_t)S * NX * sizeof(float4) +
-                      (NPB * 3 * (NX / 32) * 33 + 1024) * sizeof(float2) + 2 * S * 8 + 16;
+  const size_t smem = (size_t)S * SV * sizeof(float4) + ((size_t)NPB * 3 * FS + NTW) * sizeof(float2) +
+                      2 * S * 8 + 16;
   auto kern = k_pol_fft4s_tma_multi<S, NPB, PW, FG, NX, kMaxXAngles>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
@@ -2481,6 +2591,8 @@ cudaError_t launch_pol_fft4s_tma_multi(const void* M, int nx, int ny, int nz,
     return pol_fft4s_tma_multi_impl<1024>(M, ny, nz, pp, ang, p, pstride, tw, err, n_sm, poll, s);
   if (nx == 512)
     return pol_fft4s_tma_multi_impl<512>(M, ny, nz, pp, ang, p, pstride, tw, err, n_sm, poll, s);
+  if (nx == 2048)
+    return pol_fft4s_tma_multi_impl<2048>(M, ny, nz, pp, ang, p, pstride, tw, err, n_sm, poll, s);
   return cudaErrorInvalidValue;
 }
 
@@ -2634,7 +2746,7 @@ cudaError_t launch_row_fft(void* p, int nx, long long nrows, const void* twx, cu
   return row_fft_impl<R, 256, 4096>(p, nx, nrows, twx, s, src);
 }
 
-template <typename R, int T, int EC, int LOGL>
+template <typename R, int T, int EC, int LOGL, int MINB = 3>
 static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, const ColBatches& bt,
                                 const void* tw, cudaStream_t s) {
   using C = typename RT<R>::C;
@@ -2653,7 +2765,7 @@ static cudaError_t col_fft_impl(void* p, int L, long long S, long long W, const 
     smem += L * sizeof(C);
     tw_in_smem = 1;
   }
-  auto kern = k_col_fft<R, T, EC, LOGL>;
+  auto kern = k_col_fft<R, T, EC, LOGL, MINB>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)total, T, smem, s>>>((C*)p, ilog2(L), S, logTX, ntiles, bt.bdiv, bt.stride_hi,
@@ -2688,6 +2800,22 @@ cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBa
     const AnyLines ln = {bt.nbatch * W, W, bt.bdiv, bt.stride_hi, bt.stride_lo, bt.base, 1, S};
     return launch_fft_any<R>(p, p, L, ln, tw, s);
   }
+  // FP32 2048-point columns: the four-step kernel on 8-column tiles (64-byte
+  // row segments), tw the 2048-entry table; other widths take 4-column
+  // Stockham tiles (8192 elements, one 512-thread CTA per SM)
+  if (sizeof(R) == 4 && L == 2048 && W % 8 == 0) {
+    const long long ntiles = W / 8, total = ntiles * bt.nbatch;
+    if (total <= 0) return cudaSuccess;
+    const size_t smem = (32 * (64 * 8 + 8) + 2048) * sizeof(float2);
+    cudaError_t e = cudaFuncSetAttribute(k_col_fft2k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_col_fft2k<<<(unsigned)total, 512, smem, s>>>((float2*)p, S, ntiles, bt.bdiv, bt.stride_hi,
+                                                   bt.stride_lo, bt.base, (const float2*)tw);
+    return cudaGetLastError();
+  }
+  if (sizeof(R) == 4 && L == 2048 && W % 4 == 0)
+    return col_fft_impl<R, 512, 8192, 11, 1>(p, L, S, W, bt, tw, s);
   // 4096 elements per CTA: 34 KB (FP32) or 70 KB (FP64) of padded tile
   return col_fft_dispatch<R, 4096>(p, L, S, W, bt, tw, s);
 }

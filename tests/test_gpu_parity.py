@@ -194,7 +194,8 @@ def test_polarization_lab_frame(rsx, prec):
 
 
 # ------------------------------------------------------------------ row a4
-FFT_SHAPES = [(4, 6, 8), (3, 12, 10), (5, 9, 15), (2, 11, 13), (7, 5, 3), (6, 100, 36),
+FFT_SHAPES = [(2, 2048, 16), (2048, 2, 8), (3, 2048, 4),
+              (4, 6, 8), (3, 12, 10), (5, 9, 15), (2, 11, 13), (7, 5, 3), (6, 100, 36),
               (3, 1, 17), (2, 3, 1031), (2, 1031, 2), (1, 4095, 3),
               (4, 8, 8), (5, 16, 32), (1, 64, 64), (3, 128, 16), (2, 1, 8), (1, 1, 1),
               (7, 4, 2048), (16, 32, 32), (6, 2, 4), (3, 4, 1024), (2, 1024, 8)]
@@ -381,7 +382,8 @@ def test_run_non_power_of_two_grids(rsx, shape, c, prec, algorithm):
 
 
 BATCHED = [((2, 512, 512), 3, 4), ((1, 1024, 1024), 2, 3), ((2, 512, 1024), 2, 8),
-           ((2, 1024, 512), 2, 2)]
+           ((2, 1024, 512), 2, 2), ((3, 64, 1024), 3, 4), ((2, 32, 2048), 2, 2),
+           ((3, 16, 2048), 4, 1)]
 
 
 @pytest.mark.parametrize("frame", [0, 1])
@@ -416,8 +418,9 @@ def test_run_batched_angles_match_oracle(rsx, shape, c, kx, frame):
 def test_angle_batch_applies_only_where_the_multi_angle_pass_runs(rsx):
     for shape, prec, alg, want in (((4, 1024, 1024), 32, 1, 8), ((4, 1024, 1024), 64, 1, 1),
                                    ((1024, 1024, 1024), 32, 1, 1), ((512, 1024, 1024), 32, 1, 2),
-                                   ((4, 1024, 1024), 32, 2, 1), ((3, 1024, 1024), 32, 1, 1),
-                                   ((4, 256, 1024), 32, 1, 1)):
+                                   ((4, 1024, 1024), 32, 2, 1), ((3, 1024, 1024), 32, 1, 8),
+                                   ((4, 256, 1024), 32, 1, 8), ((4, 64, 2048), 32, 1, 2),
+                                   ((2, 64, 1000), 32, 1, 1), ((4, 64, 2048), 64, 1, 1)):
         nz, ny, nx = shape
         cfg = rsx.make_config(nx, ny, nz, 2, VOXEL, precision=prec, algorithm=alg)
         # the batch of a context, without allocating the large ones
@@ -742,6 +745,46 @@ def test_full_size_run_sampled_pixels_match_oracle(rsx):
     big = rest & (ref > 1e-4 * ref[rest].max())
     assert big.sum() > 30
     assert (np.abs(got - ref)[big] / ref[big]).max() < 2e-3
+
+
+@pytest.mark.parametrize("shape,c,prec", [((1, 2048, 2048), 2, 32), ((1, 2048, 2048), 2, 64),
+                                          ((64, 2048, 2048), 4, 32)],
+                         ids=["2048x2048x1-f32", "2048x2048x1-f64", "2048x2048x64-f32"])
+def test_run_2048_grids_sampled_pixels_match_oracle(rsx, shape, c, prec):
+    """rsx_run on the 2048-wide grids of Sec. 5.1 (the 2-D film) and Sec. 6.2
+    (2048 x 2048 x 64, c = 4): FP32 through the 2048-point multi-angle x
+    pass, FP64 through the general kernels; five angles, sampled output
+    pixels against the oracle's average (exact by linearity of the DFT)."""
+    nz, ny, nx = shape
+    E = 280.0
+    angles = (0.0, 40.0, 160.0)
+    sp = synth.sparse_voxels(shape, c, 4000, seed=29)
+    K = synth.optical_constants([E], c, seed=30)
+    dev = synth.morphology_sparse_torch(shape, c, sp, dtype=_tdtype(prec))
+    g = np.random.default_rng(31)
+    oy = np.concatenate([[ny // 2, 7, ny - 3], g.integers(0, ny, 40)])
+    ox = np.concatenate([[nx // 2, nx - 1, 11], g.integers(0, nx, 40)])
+    with rsx.Context(nx, ny, nz, c, VOXEL, precision=prec) as ctx:
+        assert ctx.angle_batch == (2 if prec == 32 else 1)
+        ctx.set_morphology(dev)
+        ctx.set_optical_constants([E], K)
+        out = torch.empty((1, ny, nx), dtype=_tdtype(prec), device="cuda")
+        ctx.run(angles, out=out)
+        ctx.check()
+        full = out[0].cpu().numpy().astype(np.float64)
+    del dev
+    torch.cuda.empty_cache()
+    got = full[oy, ox]
+    ref = O.run_alg1_sparse_pixels(sp, shape, K[0], E, VOXEL, angles, oy, ox)
+    center = np.hypot(oy - ny // 2, ox - nx // 2) < 2.5
+    t = TOL[prec]
+    np.testing.assert_allclose(got[center], ref[center], rtol=1e-5 if prec == 32 else 1e-10)
+    rest = ~center
+    rel = np.linalg.norm(got[rest] - ref[rest]) / np.linalg.norm(ref[rest])
+    assert rel < t["norm"], rel
+    big = rest & (ref > t["floor"] * ref[rest].max())
+    assert big.sum() > 20
+    assert (np.abs(got - ref)[big] / ref[big]).max() < t["pix"]
 
 
 @pytest.mark.parametrize("shape,c", [((1024, 1024, 16), 2), ((64, 512, 512), 4)])
