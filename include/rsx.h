@@ -82,7 +82,7 @@ typedef struct rsx_config {
                       /* 0 = the largest batch whose p buffers fit in 32    */
                       /* GiB).  Each extra angle holds another 3 N complex  */
                       /* p buffer.  Used by FP32 Algorithm 1 with nx = 512   */
-                      /* or 1024 (up to 8) and nx = 2048 (up to 2; larger    */
+                      /* or 1024 (up to 8) and nx = 2048 (up to 3; larger    */
                       /* values are lowered to that); elsewhere 1.  Each     */
                       /* angle's arithmetic is unchanged (Algorithm 1's      */
                       /* angle loop, the morphology sums shared).            */

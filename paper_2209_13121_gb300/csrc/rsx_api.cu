@@ -627,11 +627,11 @@ static size_t part_bytes(const rsx_config* cfg) {
 // The angle batch a config gets: the multi-angle x pass serves FP32
 // Algorithm 1 on the shapes of the bulk-copy x pass and the fused y+z pass.
 // The multi-angle x pass serves FP32 Algorithm 1 with nx = 512, 1024 or
-// 2048 (2048-point rows: at most 2 angles per pass).
+// 2048 (2048-point rows: at most 3 angles per pass).
 static int angle_batch_cap(const rsx_config* cfg) {
   if (cfg->precision != 32 || cfg->algorithm != 1) return 0;
   if (cfg->nx == 512 || cfg->nx == 1024) return RSX_MAX_ANGLE_BATCH;
-  return cfg->nx == 2048 ? 2 : 0;
+  return cfg->nx == 2048 ? 3 : 0;
 }
 
 static int angle_batch_of(const rsx_config* cfg) {

@@ -1148,52 +1148,58 @@ __global__ void __launch_bounds__(T, MINB) k_col_fft(typename RT<R>::C* __restri
   }
 }
 
-// 2048-point column FFTs (FP32): one CTA of 512 threads per tile of 8
+// 2048-point column FFTs (FP32): one CTA of 64 TX threads per tile of TX
 // adjacent columns of one batch.  2048 = 64 x 32 with n = n1 + 64 n2 and
 // k = k2 + 32 k1:
 //   X[k2 + 32 k1] = sum_n1 W64^(n1 k1) W2048^(n1 k2) sum_n2 x[n1 + 64 n2] W32^(n2 k2).
 // Stage 1: thread (n1, col) loads its 32 samples straight from global memory
 // (32 loads in flight), does the 32-point DFT over n2 in registers, applies
-// W2048^(n1 k2) and writes T[k2][n1][col] (k2 rows padded by 8 elements, so
-// the stage-2 reads of both k2 halves of a warp fall in different banks).
-// Stage 2: threads (k2, col, h) and (k2, col, 1 - h), lanes 16 apart, take
-// the even (h = 0) and odd (h = 1) n1 of row k2: a 32-point DFT each, the odd
-// half times W64^k, and one shuffle exchange leaves X[k2 + 32 k] on the h = 0
-// lane and X[k2 + 32 (k + 32)] on the h = 1 lane.  tw[j] = W2048^j.
-__global__ void __launch_bounds__(512, 1) k_col_fft2k(float2* __restrict__ data, long long S,
-                                                      long long ntiles, long long bdiv,
-                                                      long long stride_hi, long long stride_lo,
-                                                      long long base_off,
-                                                      const float2* __restrict__ tw_g) {
+// W2048^(n1 k2) and writes T[k2][n1][col] (k2 rows padded by TX elements, so
+// the stage-2 reads of the k2 rows a half-warp covers fall in different
+// banks).  Stage 2: threads (k2, col, h) and (k2, col, 1 - h), lanes 16
+// apart, take the even (h = 0) and odd (h = 1) n1 of row k2: a 32-point DFT
+// each, the odd half times W64^k, and one shuffle exchange leaves
+// X[k2 + 32 k] on the h = 0 lane and X[k2 + 32 (k + 32)] on the h = 1 lane.
+// tw[j] = W2048^j.
+template <int TX>
+__global__ void __launch_bounds__(64 * TX, 8 / TX) k_col_fft2k(float2* __restrict__ data,
+                                                                long long S, long long ntiles,
+                                                                long long bdiv, long long stride_hi,
+                                                                long long stride_lo,
+                                                                long long base_off,
+                                                                const float2* __restrict__ tw_g) {
   using C = float2;
-  constexpr int TX = 8, KS = 64 * TX + 8;  // row stride of T (k2)
+  static_assert(TX == 4 || TX == 8, "tile width");
+  constexpr int T = 64 * TX, KS = 64 * TX + TX;  // threads; row stride of T (k2)
+  constexpr int LT = 5 - (TX == 8 ? 3 : 2);      // log2(32 / TX)
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* T = reinterpret_cast<C*>(smem_raw);  // [32][KS]
-  C* tw = T + 32 * KS;                    // [2048]
+  C* Tm = reinterpret_cast<C*>(smem_raw);  // [32][KS]
+  C* tw = Tm + 32 * KS;                    // [2048]
   const long long tile = (long long)blockIdx.x % ntiles;
   const long long b = (long long)blockIdx.x / ntiles;
   C* base = data + base_off + (b / bdiv) * stride_hi + (b % bdiv) * stride_lo + tile * TX;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  // stage 1: col = lane & 7, n1 = 4 w + lane / 8
+  // stage 1: col = lane mod TX, n1 = (32 / TX) w + lane / TX
   {
-    const int col = lane & 7, n1 = 4 * w + (lane >> 3);
+    const int col = lane & (TX - 1), n1 = (w << LT) + lane / TX;
     C v[32];
 #pragma unroll
     for (int n2 = 0; n2 < 32; ++n2) v[n2] = __ldcs(base + (size_t)(n1 + 64 * n2) * S + col);
-    for (int i = t; i < 2048; i += 512) tw[i] = tw_g[i];
+    for (int i = t; i < 2048; i += T) tw[i] = tw_g[i];
     dft32(v);
     __syncthreads();  // twiddle table in place
 #pragma unroll
     for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], tw[n1 * k2]);
 #pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) T[k2 * KS + n1 * TX + col] = v[k2];
+    for (int k2 = 0; k2 < 32; ++k2) Tm[k2 * KS + n1 * TX + col] = v[k2];
   }
   __syncthreads();
-  // stage 2: col = lane & 7, k2 = 2 w + (lane >> 3 & 1), h = lane >> 4
-  const int col = lane & 7, k2 = 2 * w + ((lane >> 3) & 1), h = lane >> 4;
+  // stage 2: col = lane mod TX, k2 = (16 / TX) w + (lane / TX mod 16 / TX), h = lane / 16
+  const int col = lane & (TX - 1), k2 = w * (16 / TX) + ((lane / TX) & (16 / TX - 1)),
+            h = lane >> 4;
   C v[32];
 #pragma unroll
-  for (int m = 0; m < 32; ++m) v[m] = T[k2 * KS + (2 * m + h) * TX + col];
+  for (int m = 0; m < 32; ++m) v[m] = Tm[k2 * KS + (2 * m + h) * TX + col];
   dft32(v);
   C* out = base + (size_t)(k2 + 1024 * h) * S + col;
 #pragma unroll
@@ -2558,10 +2564,9 @@ static cudaError_t pol_fft4s_tma_multi_impl(const void* M, int ny, int nz,
   // transform groups (the transforms are the larger share of the work; a
   // fourth would cut the registers below what a transform needs) and a
   // producer warp: one 576-thread block per SM, ~205 KB of shared memory
-  // for 1024-point rows.  2048-point rows: 1024-voxel segments, 2 row
-  // buffers of 50 KB (so at most 2 angles per launch), two transform
-  // groups, ~163 KB.
-  constexpr int S = 3, NPB = NX == 2048 ? 2 : 6, PW = 8, FG = NX == 2048 ? 2 : 3;
+  // for 1024-point rows.  2048-point rows: 1024-voxel segments, 3 row
+  // buffers of 50 KB (so at most 3 angles per launch), ~213 KB.
+  constexpr int S = 3, NPB = NX == 2048 ? 3 : 6, PW = 8, FG = 3;
   constexpr int FS = NX == 2048 ? 2 * 1056 : (NX / 32) * 33;
   constexpr int SV = NX > 1024 ? 1024 : NX, NTW = NX == 2048 ? 2048 : 1024;
   if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > kMaxXAngles ||
@@ -2800,22 +2805,22 @@ cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBa
     const AnyLines ln = {bt.nbatch * W, W, bt.bdiv, bt.stride_hi, bt.stride_lo, bt.base, 1, S};
     return launch_fft_any<R>(p, p, L, ln, tw, s);
   }
-  // FP32 2048-point columns: the four-step kernel on 8-column tiles (64-byte
-  // row segments), tw the 2048-entry table; other widths take 4-column
-  // Stockham tiles (8192 elements, one 512-thread CTA per SM)
-  if (sizeof(R) == 4 && L == 2048 && W % 8 == 0) {
-    const long long ntiles = W / 8, total = ntiles * bt.nbatch;
+  // FP32 2048-point columns: the four-step kernel on 4-column tiles (32-byte
+  // row segments, ~83 KB of shared memory: two 256-thread CTAs per SM), tw
+  // the 2048-entry table
+  if (sizeof(R) == 4 && L == 2048 && W % 4 == 0) {
+    constexpr int TX = 4;
+    const long long ntiles = W / TX, total = ntiles * bt.nbatch;
     if (total <= 0) return cudaSuccess;
-    const size_t smem = (32 * (64 * 8 + 8) + 2048) * sizeof(float2);
-    cudaError_t e = cudaFuncSetAttribute(k_col_fft2k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = (32 * (64 * TX + TX) + 2048) * sizeof(float2);
+    auto kern = k_col_fft2k<TX>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_col_fft2k<<<(unsigned)total, 512, smem, s>>>((float2*)p, S, ntiles, bt.bdiv, bt.stride_hi,
-                                                   bt.stride_lo, bt.base, (const float2*)tw);
+    kern<<<(unsigned)total, 64 * TX, smem, s>>>((float2*)p, S, ntiles, bt.bdiv, bt.stride_hi,
+                                                bt.stride_lo, bt.base, (const float2*)tw);
     return cudaGetLastError();
   }
-  if (sizeof(R) == 4 && L == 2048 && W % 4 == 0)
-    return col_fft_impl<R, 512, 8192, 11, 1>(p, L, S, W, bt, tw, s);
   // 4096 elements per CTA: 34 KB (FP32) or 70 KB (FP64) of padded tile
   return col_fft_dispatch<R, 4096>(p, L, S, W, bt, tw, s);
 }
