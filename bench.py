@@ -57,6 +57,12 @@ WORKLOADS = {
                         energies=(150, 270.0, 320.0)),
     "p1-1024-z16": dict(shape=(16, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0),
                         energies=(150, 270.0, 320.0)),
+    # Sec. 5.2.2 grating geometry (E5): 1 nm voxels, 17 keV, the e-field at 0
+    # only (no rotation), FP64 in the paper's comparison (--precision 64)
+    "p5-1024x63": dict(shape=(63, 1024, 1024), c=2, angles=(0.0, 1.0, 0.0),
+                       energies=(1, 17000.0, 17000.0), voxel_nm=1.0),
+    "p5-1024x1": dict(shape=(1, 1024, 1024), c=2, angles=(0.0, 1.0, 0.0),
+                      energies=(1, 17000.0, 17000.0), voxel_nm=1.0),
 }
 VOXEL_NM = 5.0
 METRIC = "P-RSoXS voxel-angle throughput (restated from 'filtered H*X GDoF-vec/s')"
@@ -274,7 +280,8 @@ def run_ours(args):
     K = synth.optical_constants(mine, c, seed=2)
     M = synth.morphology_random_torch((nz, ny, nx), c, seed=1, device="cuda",
                                       dtype=torch.float32 if prec == 32 else torch.float64)
-    ctx = rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm,
+    voxel_nm = W.get("voxel_nm", VOXEL_NM)
+    ctx = rsx.Context(nx, ny, nz, c, voxel_nm, precision=prec, algorithm=args.algorithm,
                       angle_batch=args.angle_batch)
     angle_batch = ctx.angle_batch
     ctx.set_morphology(M)
@@ -390,7 +397,7 @@ def run_ours(args):
         del M
         ctx.close()
         torch.cuda.empty_cache()
-        ctxs = [rsx.Context(nx, ny, nz, c, VOXEL_NM, precision=prec, algorithm=args.algorithm,
+        ctxs = [rsx.Context(nx, ny, nz, c, voxel_nm, precision=prec, algorithm=args.algorithm,
                             angle_batch=args.angle_batch) for _ in range(2)]
         for cx in ctxs:
             cx.set_optical_constants(mine, K)
@@ -438,7 +445,8 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if prec == 32 else "f64", "data": "synthetic",
             "config": {"workload": f"{args.workload}: Algorithm {args.algorithm}, {nx}x{ny}x{nz} voxels, "
-                                   f"c={c}, {n_ang} e-field angles 0:2:180 per energy, one energy "
+                                   f"c={c}, {n_ang} e-field angle(s) {'%g:%g:%g' % W['angles']} "
+                                   f"per energy, {voxel_nm:g} nm voxels, one energy "
                                    f"per step (of {n_e} over {e_lo:g}-{e_hi:g} eV)",
                        "voxels": N, "components": c, "angles_per_energy": n_ang,
                        "angle_batch": angle_batch,

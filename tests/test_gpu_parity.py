@@ -383,7 +383,7 @@ def test_run_non_power_of_two_grids(rsx, shape, c, prec, algorithm):
 
 BATCHED = [((2, 512, 512), 3, 4), ((1, 1024, 1024), 2, 3), ((2, 512, 1024), 2, 8),
            ((2, 1024, 512), 2, 2), ((3, 64, 1024), 3, 4), ((2, 32, 2048), 2, 2),
-           ((3, 16, 2048), 4, 1), ((2, 8, 2048), 3, 3), ((3, 1024, 64), 2, 4)]
+           ((3, 16, 2048), 4, 1), ((2, 8, 2048), 3, 3), ((3, 1024, 512), 2, 4)]
 
 
 @pytest.mark.parametrize("frame", [0, 1])
