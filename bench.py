@@ -326,10 +326,11 @@ def run_ours(args):
     peak, peak_kind = _peaks()
     cplx = 2 * real
     # the library fuses the y-FFT with the q_z bins for FP32 grids with
-    # ny = 1024, nx a multiple of 16 and nz a power of two up to 1024: the
-    # y-transformed fields are then read once and never written
-    fused = (prec == 32 and ny == 1024 and nx % 16 == 0 and nz <= 1024
-             and nz & (nz - 1) == 0)
+    # ny = 512, 1024 or 2048, nx a power of two >= 16 and nz a power of two up
+    # to 1024 (at least 4 for 2048 rows): the y-transformed fields are then
+    # read once and never written
+    fused = (prec == 32 and ny in (512, 1024, 2048) and nx >= 16 and nx & (nx - 1) == 0
+             and nz <= 1024 and nz & (nz - 1) == 0 and (ny != 2048 or nz >= 4))
     nf = 5 if args.algorithm == 3 else 3
     y_bytes = nf * cplx if fused else 2 * nf * cplx
     z_bytes = 0 if fused else nf * cplx  # the bins kernel then reads per-pixel data only

@@ -96,9 +96,11 @@ typedef struct rsx_context rsx_context;
  * workspace: 3 N complex for p (times the angle batch), two nx*ny Real
  * images, per-pixel Ewald
  * geometry, FFT twiddle tables, for Algorithms 2 and 3 the stored N_t entries
- * (Table 2) and, for FP32 grids with ny = 1024, nx a multiple of 16 and nz a
- * power of two up to 1024, the two q_z bins per pixel of the fused y-FFT +
- * z pass (2 x 3 x 16 bytes per pixel; 2 x 5 x 16 for Algorithm 3).  *out
+ * (Table 2) and, for FP32 grids with ny = 512, 1024 or 2048, nx a power of
+ * two of at least 16 and nz a power of two up to 1024 (at least 4 for
+ * ny = 2048), the two q_z bins per
+ * pixel of the fused y-FFT + z pass (up to 4 partial slots of 3 x 2 x 16
+ * bytes per pixel; 5 x 2 x 16 for Algorithm 3).  *out
  * receives the handle.  Errors: RSX_ERR_INVALID (sizes, precision,
  * algorithm), RSX_ERR_OOM. */
 int rsx_create(const rsx_config* cfg, rsx_context** out);

@@ -429,7 +429,8 @@ cudaError_t fused_yz(rsx_context* c, const CUtensorMap* map, int nf, long long* 
     return rsx::launch_yz512_tma(map, g.nx, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->twy,
                                  c->part, c->err, c->n_sm, c->wait_polls, L, s);
   return rsx::launch_yz_tma(map, g.nx, g.ny, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->tw4,
-                            c->part, c->err, c->n_sm, c->wait_polls, L, s);
+                            g.ny == 2048 ? c->twy : nullptr, c->part, c->err, c->n_sm,
+                            c->wait_polls, L, s);
 }
 
 // Linearity fast path, once per energy: FFT (x and y) of N_t's five
@@ -747,7 +748,8 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     delete c;
     return rc;
   }
-  if ((cfg->nx == 1024 || cfg->ny == 1024) && (rc = upload_tw4(c))) {
+  if ((cfg->nx == 1024 || cfg->ny == 1024 || (cfg->ny == 2048 && uses_yz(cfg))) &&
+      (rc = upload_tw4(c))) {
     free_all(c);
     delete c;
     return rc;
@@ -766,9 +768,10 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
   }
   if (uses_yz(cfg) && c->n_sm > 0) {
     // the fused y+z pass: 1024-row tiles are 8 columns wide and two blocks
-    // read the halves of each 128-byte line at once, 512-row tiles are 16
-    // columns (whole lines); promote to 128 bytes, not 256
-    const unsigned box = cfg->ny == 512 ? 32 : 16;
+    // read the halves of each 128-byte line at once, 2048-row tiles 4
+    // columns (four blocks), 512-row tiles are 16 columns (whole lines);
+    // promote to 128 bytes, not 256
+    const unsigned box = cfg->ny == 512 ? 32 : cfg->ny == 2048 ? 8 : 16;
     c->has_tmap_pz = true;
     for (int k = 0; k < c->kx; ++k)
       c->has_tmap_pz = c->has_tmap_pz &&

@@ -1513,6 +1513,25 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
   }
 }
 
+// Stage-1 samples of the 2048-row fused pass: virtual column col of the
+// 1024-point transforms is, for col < 4, a[r] = x[r] + x[r + 1024] and, for
+// col >= 4, b[r] = (x[r] - x[r + 1024]) W2048^r of real column col mod 4
+// (radix-2 decimation in frequency: X[2k] and X[2k + 1] are the 1024-point
+// transforms of a and b).  With r = r0 + 64 m, W2048^r = W2048^r0 W32^m; the
+// W32^m factor is applied here (a compile-time constant, selected per lane),
+// W2048^r0 after the 16-point DFT.  xb holds the tile as [2048][4].
+template <int M>
+__device__ __forceinline__ void yz2k_load(const float2* xb, int r0, int c4, bool odd, float2* v) {
+  if constexpr (M < 16) {
+    const float2 x1 = xb[(r0 + 64 * M) * 4 + c4], x2 = xb[(r0 + 64 * M + 1024) * 4 + c4];
+    const float2 a = cadd(x1, x2), d = csub(x1, x2);
+    const float2 b = w32<M>(d);
+    v[M].x = odd ? b.x : a.x;
+    v[M].y = odd ? b.y : a.y;
+    yz2k_load<M + 1>(xb, r0, c4, odd, v);
+  }
+}
+
 // y-FFT fused with the pruned z transform (FP32, ny = 1024, nz a power of
 // two up to 1024, nx a multiple of 16).  Work items are (field, pair of
 // adjacent 8-column tiles); each has nz steps (its z-slices).  The items'
@@ -1543,15 +1562,27 @@ __global__ void __launch_bounds__(256) k_ewald_pruned(const typename RT<R>::C* _
 // sphere, which k_ewald_bins zeroes).  The y-transformed slices are never
 // written.  The input buffer is refilled (step + 2) once the swap has been
 // read.  Waits are bounded as in k_col_fft4s_tma.
+//
+// Y2K: the same for ny = 2048.  A work item is (field, quad of adjacent
+// 4-column tiles), blocks 4j .. 4j + 3 take the four tiles of the same
+// steps (32-byte row segments, a 128-byte line per quad); each step's
+// 4 x 2048 tile arrives in eight 256-row boxes and is read by stage 1 as the
+// 8 virtual columns of two 1024-point transforms (yz2k_load: even outputs
+// from columns 0-3, odd from 4-7), so the rest of the pass is unchanged;
+// virtual pixel (row, col) is the real pixel (2 row + col / 4, 4 ti + col mod 4).
+// tw2k: W2048^j (j < 64 used).
+template <bool Y2K>
 __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUtensorMap tmap, int nx,
                                                    int nz, int nf, int ntiles, int L, int T,
                                                    const Geo<float>* __restrict__ geo,
                                                    const float2* __restrict__ twz_g,
                                                    const float2* __restrict__ tw4_g,
+                                                   const float2* __restrict__ tw2k,
                                                    float4* __restrict__ part, int* __restrict__ err,
                                                    unsigned poll) {
   using C = float2;
   constexpr int TX = 8, TILE = 1024 * TX, STR = 33 * TX;
+  constexpr int GRP = Y2K ? 4 : 2, LGRP = Y2K ? 2 : 1;  // blocks reading one line in lockstep
   constexpr unsigned kPoll = 1u << 22;
   extern __shared__ __align__(128) unsigned char smem_a128[];
   C* in = reinterpret_cast<C*>(smem_a128);  // [2][1024][TX], dense (TMA boxes)
@@ -1563,13 +1594,16 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int col = lane & 7, hw = w >> 3;
   const int q = (w & 7) * 4 + (lane >> 3);  // n1 in stage 1, k2 in stage 2
-  // 32-bit step arithmetic (T < 2^31); nz and ntiles / 2 are powers of two
-  const int s0 = (int)(blockIdx.x >> 1) * L;
+  // 32-bit step arithmetic (T < 2^31); nz and ntiles / GRP are powers of two
+  const int s0 = (int)(blockIdx.x >> LGRP) * L;
   const int s1 = s0 + L < T ? s0 + L : T;
   if (s0 >= s1) return;
-  const long long npix = 1024LL * nx;
-  const int half = ntiles >> 1, lognz = __ffs(nz) - 1, loghalf = __ffs(half) - 1;
-  const int mem = blockIdx.x & 1;
+  const long long npix = (Y2K ? 2048LL : 1024LL) * nx;
+  const int half = ntiles >> LGRP, lognz = __ffs(nz) - 1, loghalf = __ffs(half) - 1;
+  const int mem = blockIdx.x & (GRP - 1);
+  // Y2K: this lane's W2048^r0 (r0 = q + 32 hw) for the odd virtual columns
+  const bool odd = Y2K && col >= 4;
+  const C base2k = odd ? tw2k[q + 32 * hw] : make_float2(1.f, 0.f);
   if (t == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -1580,11 +1614,17 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   __syncthreads();
   auto issue = [&](int st, int b) {
     const int item = st >> lognz;
-    const int z = st & (nz - 1), f = item >> loghalf, ti = 2 * (item & (half - 1)) + mem;
+    const int z = st & (nz - 1), f = item >> loghalf, ti = GRP * (item & (half - 1)) + mem;
     mbar_expect_tx(&bar[b], TILE * sizeof(C));
+    if constexpr (Y2K) {  // 4 columns (8 floats) x 2048 rows
 #pragma unroll
-    for (int k = 0; k < 4; ++k)
-      tma_load_3d(in + b * TILE + k * 256 * TX, &tmap, ti * 2 * TX, k * 256, f * nz + z, &bar[b]);
+      for (int k = 0; k < 8; ++k)
+        tma_load_3d(in + b * TILE + k * 256 * 4, &tmap, ti * 8, k * 256, f * nz + z, &bar[b]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        tma_load_3d(in + b * TILE + k * 256 * TX, &tmap, ti * 2 * TX, k * 256, f * nz + z, &bar[b]);
+    }
   };
   if (t == 0) {
     issue(s0, 0);
@@ -1595,11 +1635,13 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     const int b = i & 1;
     const int item = st >> lognz;
     const int z = st & (nz - 1);
-    const int ti = 2 * (item & (half - 1)) + mem;
+    const int ti = GRP * (item & (half - 1)) + mem;
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
       __syncthreads();  // the previous step's reads of the bins are done
       for (int e = t; e < TILE; e += 512) {
-        const int b0 = geo[(size_t)(e >> 3) * nx + ti * TX + (e & 7)].b0;
+        const size_t pixel = Y2K ? (size_t)(2 * (e >> 3) + ((e & 7) >> 2)) * nx + ti * 4 + (e & 3)
+                                 : (size_t)(e >> 3) * nx + ti * TX + (e & 7);
+        const int b0 = geo[pixel].b0;
         btab[e] = (unsigned short)(b0 < 0 ? 0 : b0);
       }
 #pragma unroll
@@ -1618,9 +1660,17 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     // stage 1: 16-point DFT of the samples n2 = 2m + hw of row n1 = q
     {
       C v[16];
+      if constexpr (Y2K) {
+        yz2k_load<0>(xb, q + 32 * hw, col & 3, odd, v);
+      } else {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = xb[(q + 32 * hw + 64 * m) * TX + col];
+        for (int m = 0; m < 16; ++m) v[m] = xb[(q + 32 * hw + 64 * m) * TX + col];
+      }
       dft_reg<16>(v);
+      if constexpr (Y2K) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) v[k] = cmul(v[k], base2k);
+      }
       if (hw) w32_outputs<0>(v);
 #pragma unroll
       for (int k = 0; k < 16; ++k) tr[(16 * hw + k) * STR + q * TX + col] = v[out_pos<16>(k)];
@@ -1669,11 +1719,13 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         const int item_start = st - z;
         const int slot = item_start >= s0 ? 0 : s0 / L - item_start / L;
         const int f = item >> loghalf;
-        float4* dst = part + ((size_t)slot * nf + f) * npix + (size_t)ti * TX + col;
+        float4* dst = part + ((size_t)slot * nf + f) * npix +
+                      (Y2K ? (size_t)(col >> 2) * nx + ti * 4 + (col & 3) : (size_t)ti * TX + col);
 #pragma unroll
         for (int k = 0; k < 16; ++k) {
           const int row = q + 512 * hw + 32 * k;
-          dst[(size_t)row * nx] = make_float4(acc0[k].x, acc0[k].y, acc1[k].x, acc1[k].y);
+          dst[(size_t)row * (Y2K ? 2 * nx : nx)] =
+              make_float4(acc0[k].x, acc0[k].y, acc1[k].x, acc1[k].y);
         }
       }
     }
@@ -2602,8 +2654,12 @@ cudaError_t launch_pol_fft4s_tma_multi(const void* M, int nx, int ny, int nz,
 }
 
 bool yz_fusable(int nx, int ny, int nz) {
-  return (ny == 1024 || ny == 512) && nx >= 16 && (nx & (nx - 1)) == 0 && nz >= 1 &&
-         nz <= 1024 && (nz & (nz - 1)) == 0;
+  // 2048 rows: from 4 slices up (a work item re-reads its bin indices from
+  // the per-pixel geometry, 4x the bytes of one slice of its tile, which the
+  // separate y and z passes beat on thinner stacks: 2048^2 x 1 film 21 ms
+  // against 31 ms per energy)
+  return (ny == 2048 || ny == 1024 || ny == 512) && nx >= 16 && (nx & (nx - 1)) == 0 &&
+         nz >= (ny == 2048 ? 4 : 1) && nz <= 1024 && (nz & (nz - 1)) == 0;
 }
 
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
@@ -2629,27 +2685,32 @@ cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo
 }
 
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
-                          const void* twz, const void* tw4, void* part, int* err, int n_sm,
-                          unsigned poll, long long* L_out, cudaStream_t s) {
-  if (!yz_fusable(nx, ny, nz) || n_sm <= 0) return cudaErrorInvalidValue;
+                          const void* twz, const void* tw4, const void* tw2k, void* part, int* err,
+                          int n_sm, unsigned poll, long long* L_out, cudaStream_t s) {
+  if (!yz_fusable(nx, ny, nz) || ny == 512 || n_sm <= 0) return cudaErrorInvalidValue;
   if (nf != 3 && nf != 5) return cudaErrorInvalidValue;
-  const long long ntiles = nx / 8, items = nf * (ntiles / 2), T = items * nz;
-  if (n_sm < 2) return cudaErrorInvalidValue;
-  // equal step ranges over as many block pairs as SMs allow, but at least
-  // nz / 3 steps each, so an item meets at most kYzSlots pairs
-  const long long P0 = n_sm / 2;
+  // 1024 rows: pairs of 8-column tiles; 2048 rows: quads of 4-column tiles
+  const bool y2k = ny == 2048;
+  if (y2k && !tw2k) return cudaErrorInvalidValue;
+  const int grp = y2k ? 4 : 2;
+  const long long ntiles = y2k ? nx / 4 : nx / 8, items = nf * (ntiles / grp), T = items * nz;
+  if (n_sm < grp) return cudaErrorInvalidValue;
+  // equal step ranges over as many block groups as SMs allow, but at least
+  // nz / 3 steps each, so an item meets at most kYzSlots groups
+  const long long P0 = n_sm / grp;
   const long long L0 = (T + P0 - 1) / P0, Lmin = (nz + kYzSlots - 2) / (kYzSlots - 1);
   const long long L = L0 > Lmin ? L0 : Lmin;
-  const long long pairs = (T + L - 1) / L;
+  const long long groups = (T + L - 1) / L;
   *L_out = L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 1024 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_yz_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = y2k ? k_yz_tma<true> : k_yz_tma<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_yz_tma<<<(unsigned)(2 * pairs), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles,
-                                                     (int)L, (int)T, geo,
-                                             (const float2*)twz, (const float2*)tw4, (float4*)part,
-                                             err, poll);
+  kern<<<(unsigned)(grp * groups), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf,
+                                                    (int)ntiles, (int)L, (int)T, geo,
+                                                    (const float2*)twz, (const float2*)tw4,
+                                                    (const float2*)tw2k, (float4*)part, err, poll);
   return cudaGetLastError();
 }
 

@@ -193,19 +193,20 @@ cudaError_t launch_ntp_fft4s_tma(const void* nt, int nx, int ny, int nz,
                                  const PolParams<float>& pp, void* p, const void* tw4, int* err,
                                  int n_sm, unsigned poll, cudaStream_t s);
 // The y-FFT fused with the pruned z transform (FP32): yz_fusable says
-// whether the shape qualifies (ny = 1024 or 512, nx a multiple of 16, nz a
-// power of two up to 1024).
-// launch_yz_tma writes the two q_z bins of every pixel and of each of the nf
-// fields (3: p; 5: the linearity path's N_t entries) into part ([kYzSlots]
-// [nf][ny][nx] float4 = bin b0, bin b0 + 1) and returns in *L_out
-// the step count per block that launch_ewald_bins needs to add the slots.
+// whether the shape qualifies (ny = 2048, 1024 or 512, nx a power of two of
+// at least 16, nz a power of two up to 1024, and at least 4 for 2048 rows).
+// launch_yz_tma (ny = 1024 or 2048) writes the two q_z bins of every pixel
+// and of each of the nf fields (3: p; 5: the linearity path's N_t entries)
+// into part ([kYzSlots][nf][ny][nx] float4 = bin b0, bin b0 + 1) and returns
+// in *L_out the step count per block that launch_ewald_bins needs to add the
+// slots.  tw2k: exp(-2 pi i j / 2048) (ny = 2048 only).
 bool yz_fusable(int nx, int ny, int nz);
 // Partial-bin slots of the fused pass: a work item's z-slices meet at most
 // this many blocks (their step ranges hold at least nz / (kYzSlots - 1)).
 constexpr int kYzSlots = 4;
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
-                          const void* twz, const void* tw4, void* part, int* err, int n_sm,
-                          unsigned poll, long long* L_out, cudaStream_t s);
+                          const void* twz, const void* tw4, const void* tw2k, void* part, int* err,
+                          int n_sm, unsigned poll, long long* L_out, cudaStream_t s);
 // The same for ny = 512 (16-column tiles, tensor map boxes of 32 floats x
 // 256 rows; twy the 512-point twiddle table).
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,

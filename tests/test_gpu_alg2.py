@@ -162,7 +162,7 @@ def test_nt_refused_in_algorithm1_context(rsx):
 @pytest.mark.parametrize("frame", [0, 1])
 @pytest.mark.parametrize("shape,c", [((4, 16, 16), 3), ((6, 32, 128), 4), ((1, 64, 64), 2),
                                      ((5, 8, 32), 2), ((2, 1024, 8), 2), ((4, 1024, 64), 2),
-                                     ((2, 512, 32), 2)])
+                                     ((2, 512, 32), 2), ((4, 2048, 16), 2)])
 def test_linear_path_matches_oracle_and_alg1(rsx, shape, c, prec, frame):
     M = synth.morphology_random(shape, c, seed=61, dtype=_real(prec))
     K = synth.optical_constants(ENERGIES, c, seed=62)

@@ -295,7 +295,8 @@ def test_scatter_angle_matches_oracle(rsx, shape, c, prec):
 # fused pass, with items split between blocks); 512-wide rows (the 32 x 16
 # transform of the bulk-copy x pass) with one and three components, alone
 # and feeding the 512-row fused pass.
-MULTI = [((3, 256, 1024), 2), ((8, 1024, 256), 2), ((1, 1024, 64), 3), ((4, 1024, 16), 2),
+MULTI = [((2, 2048, 16), 2), ((1, 2048, 64), 3), ((4, 2048, 32), 2), ((8, 2048, 128), 2),
+         ((3, 256, 1024), 2), ((8, 1024, 256), 2), ((1, 1024, 64), 3), ((4, 1024, 16), 2),
          ((2, 1024, 512), 2), ((1, 1024, 2048), 2), ((3, 8, 1024), 1), ((4, 512, 64), 2),
          ((2, 512, 1024), 2), ((5, 64, 512), 3), ((3, 8, 512), 1), ((4, 512, 512), 2)]
 
@@ -313,11 +314,12 @@ def test_scatter_angle_persistent_passes(rsx, shape, c):
             assert_image_close(img.cpu().numpy(), ref, 32)
 
 
+@pytest.mark.parametrize("ny", [1024, 2048])
 @pytest.mark.parametrize("frame", [0, 1])
-def test_fused_yz_pass_off_sphere_pixels_and_frames(rsx, frame):
-    """ny = 1024 with 2 nm voxels at 270 eV: the detector corners lie
-    outside the Ewald sphere (zero in both paths), in either frame."""
-    shape, c, vox = (4, 1024, 32), 2, 2.0
+def test_fused_yz_pass_off_sphere_pixels_and_frames(rsx, frame, ny):
+    """ny = 1024 and 2048 with 2 nm voxels at 270 eV: the detector corners
+    lie outside the Ewald sphere (zero in both paths), in either frame."""
+    shape, c, vox = (4, ny, 32), 2, 2.0
     M, K = _inputs(shape, c, 32, seed=18)
     nz, ny, nx = shape
     with rsx.Context(nx, ny, nz, c, vox, precision=32, frame=frame) as ctx:
@@ -383,7 +385,8 @@ def test_run_non_power_of_two_grids(rsx, shape, c, prec, algorithm):
 
 BATCHED = [((2, 512, 512), 3, 4), ((1, 1024, 1024), 2, 3), ((2, 512, 1024), 2, 8),
            ((2, 1024, 512), 2, 2), ((3, 64, 1024), 3, 4), ((2, 32, 2048), 2, 2),
-           ((3, 16, 2048), 4, 1), ((2, 8, 2048), 3, 3), ((3, 1024, 512), 2, 4)]
+           ((3, 16, 2048), 4, 1), ((2, 8, 2048), 3, 3), ((3, 1024, 512), 2, 4),
+           ((2, 2048, 512), 2, 4)]
 
 
 @pytest.mark.parametrize("frame", [0, 1])
