@@ -133,6 +133,7 @@ struct rsx_context {
   void* img = nullptr;  // one detector image
   void* acc = nullptr;  // running sum of rotated images
   void* geo = nullptr;  // per-pixel Ewald geometry of energy geo_energy
+  unsigned short* b0idx = nullptr;  // its lower q_z bins, packed (fused y+z passes)
   // Algorithm 2: N_t of energy nt_energy (5 complex per voxel); a host
   // morphology stays on the host and is streamed per component in chunks
   // through two staging buffers on a copy stream.
@@ -187,7 +188,8 @@ namespace {
 
 void free_all(rsx_context* c) {
   void* ptrs[] = {c->M_owned, c->p,    c->img, c->acc,  c->geo,  c->twx, c->twy,
-                  c->twz,     c->tw4,  c->flag, c->err, c->part, c->imgs, c->dir, c->tw2k};
+                  c->twz,     c->tw4,  c->flag, c->err, c->part, c->imgs, c->dir, c->tw2k,
+                  c->b0idx};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : c->recs) {
@@ -373,7 +375,7 @@ int ensure_geo(rsx_context* c, int ie, cudaStream_t s) {
   if (c->geo_energy == ie) return RSX_OK;
   PhaseTimer pt(c, RSX_PHASE_OTHER, s);
   RSX_CK(rsx::launch_geometry<R>((Geo<R>*)c->geo, c->cfg.nx, c->cfg.ny, c->cfg.nz,
-                                 c->cfg.voxel_nm, wavenumber(c->energies[ie]), s),
+                                 c->cfg.voxel_nm, wavenumber(c->energies[ie]), s, c->b0idx),
          "geometry kernel");
   c->geo_energy = ie;
   return RSX_OK;
@@ -427,9 +429,9 @@ cudaError_t fused_yz(rsx_context* c, const CUtensorMap* map, int nf, long long* 
   const rsx_config& g = c->cfg;
   if (g.ny == 512)
     return rsx::launch_yz512_tma(map, g.nx, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->twy,
-                                 c->part, c->err, c->n_sm, c->wait_polls, L, s);
+                                 c->b0idx, c->part, c->err, c->n_sm, c->wait_polls, L, s);
   return rsx::launch_yz_tma(map, g.nx, g.ny, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->tw4,
-                            g.ny == 2048 ? c->twy : nullptr, c->part, c->err, c->n_sm,
+                            g.ny == 2048 ? c->twy : nullptr, c->b0idx, c->part, c->err, c->n_sm,
                             c->wait_polls, L, s);
 }
 
@@ -662,7 +664,7 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
   b += 2 * (size_t)npix * R;                         // Ewald, Ewald_Avg (Table 1: 2 nx ny)
   b += (size_t)npix * geo_size(cfg->precision);
   b += (size_t)(cfg->nx + cfg->ny + cfg->nz) * Cs + sizeof(int);
-  if (uses_yz(cfg)) b += part_bytes(cfg);  // bins of the fused y + z pass
+  if (uses_yz(cfg)) b += part_bytes(cfg) + 2 * (size_t)npix;  // fused y + z pass: bins, bin indices
   if (cfg->algorithm == 3) b += (size_t)rsx::kMaxAngleBatch * npix * R;  // a batch of images
   return b;
 }
@@ -788,7 +790,8 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     delete c;
     return rc;
   }
-  if (uses_yz(cfg) && (e = cudaMalloc(&c->part, part_bytes(cfg))) != cudaSuccess) {
+  if (uses_yz(cfg) && ((e = cudaMalloc(&c->part, part_bytes(cfg))) != cudaSuccess ||
+                       (e = cudaMalloc((void**)&c->b0idx, (size_t)c->npix * 2)) != cudaSuccess)) {
     rc = cuda_fail(e, "y + z pass bins");
     free_all(c);
     delete c;

@@ -1320,9 +1320,11 @@ __device__ __forceinline__ size_t shifted_pixel(long long pix, int nx, int ny) {
 // Eq. (Ewald) per pixel, in double: q from the FFT index (FFT order),
 // q_z = -k + sqrt(k^2 - q_x^2 - q_y^2), t = q_z / dq_z, bins floor(t) and
 // floor(t) + 1 (periodic), weight w = t - floor(t) on the upper bin.
+// b0idx (optional): the lower bin alone, 0 off the sphere, for the fused
+// y+z passes' per-tile tables (2 bytes per pixel instead of a 32-byte record).
 template <typename R>
 __global__ void k_geometry(Geo<R>* __restrict__ geo, int nx, int ny, int nz, double voxel_nm,
-                           double k) {
+                           double k, unsigned short* __restrict__ b0idx) {
   const long long pix = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (pix >= (long long)nx * ny) return;
   const int my = (int)(pix / nx), mx = (int)(pix - (long long)my * nx);
@@ -1337,6 +1339,7 @@ __global__ void k_geometry(Geo<R>* __restrict__ geo, int nx, int ny, int nz, dou
     g.b0 = g.b1 = -1;
     g.w = g.rx = g.ry = g.rz = g.k4 = R(0);
     geo[pix] = g;
+    if (b0idx) b0idx[pix] = 0;
     return;
   }
   const double qz = -k + sqrt(rad);
@@ -1359,6 +1362,7 @@ __global__ void k_geometry(Geo<R>* __restrict__ geo, int nx, int ny, int nz, dou
   g.rz = (R)(kz / kmag);
   g.k4 = (R)(kmag2 * kmag2);
   geo[pix] = g;
+  if (b0idx) b0idx[pix] = (unsigned short)i0;
 }
 
 // ------------------------------------------------------------------- Ewald
@@ -1578,6 +1582,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
                                                    const float2* __restrict__ twz_g,
                                                    const float2* __restrict__ tw4_g,
                                                    const float2* __restrict__ tw2k,
+                                                   const unsigned short* __restrict__ b0idx,
                                                    float4* __restrict__ part, int* __restrict__ err,
                                                    unsigned poll) {
   using C = float2;
@@ -1641,8 +1646,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
       for (int e = t; e < TILE; e += 512) {
         const size_t pixel = Y2K ? (size_t)(2 * (e >> 3) + ((e & 7) >> 2)) * nx + ti * 4 + (e & 3)
                                  : (size_t)(e >> 3) * nx + ti * TX + (e & 7);
-        const int b0 = geo[pixel].b0;
-        btab[e] = (unsigned short)(b0 < 0 ? 0 : b0);
+        btab[e] = b0idx[pixel];
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
@@ -1752,6 +1756,7 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
                                                       int T, const Geo<float>* __restrict__ geo,
                                                       const float2* __restrict__ twz_g,
                                                       const float2* __restrict__ twy_g,
+                                                      const unsigned short* __restrict__ b0idx,
                                                       float4* __restrict__ part,
                                                       int* __restrict__ err, unsigned poll) {
   using C = float2;
@@ -1801,8 +1806,7 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
       __syncthreads();  // the previous step's reads of the bins are done
       for (int e = t; e < TILE; e += 512) {
-        const int b0 = geo[(size_t)(e >> 4) * nx + ti * TX + (e & 15)].b0;
-        btab[e] = (unsigned short)(b0 < 0 ? 0 : b0);
+        btab[e] = b0idx[(size_t)(e >> 4) * nx + ti * TX + (e & 15)];
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
@@ -2663,8 +2667,9 @@ bool yz_fusable(int nx, int ny, int nz) {
 }
 
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
-                             const void* twz, const void* twy, void* part, int* err, int n_sm,
-                             unsigned poll, long long* L_out, cudaStream_t s) {
+                             const void* twz, const void* twy, const unsigned short* b0idx,
+                             void* part, int* err, int n_sm, unsigned poll, long long* L_out,
+                             cudaStream_t s) {
   if (!yz_fusable(nx, 512, nz) || n_sm <= 0 || (nf != 3 && nf != 5)) return cudaErrorInvalidValue;
   const long long ntiles = nx / 16, items = nf * ntiles, T = items * nz;
   // equal step ranges over as many blocks as SMs, but at least nz / 3 steps
@@ -2680,13 +2685,15 @@ cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo
   if (e != cudaSuccess) return e;
   k_yz512_tma<<<(unsigned)grid, 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles,
                                                 (int)L, (int)T, geo, (const float2*)twz,
-                                                (const float2*)twy, (float4*)part, err, poll);
+                                                (const float2*)twy, b0idx, (float4*)part, err,
+                                                poll);
   return cudaGetLastError();
 }
 
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
-                          const void* twz, const void* tw4, const void* tw2k, void* part, int* err,
-                          int n_sm, unsigned poll, long long* L_out, cudaStream_t s) {
+                          const void* twz, const void* tw4, const void* tw2k,
+                          const unsigned short* b0idx, void* part, int* err, int n_sm,
+                          unsigned poll, long long* L_out, cudaStream_t s) {
   if (!yz_fusable(nx, ny, nz) || ny == 512 || n_sm <= 0) return cudaErrorInvalidValue;
   if (nf != 3 && nf != 5) return cudaErrorInvalidValue;
   // 1024 rows: pairs of 8-column tiles; 2048 rows: quads of 4-column tiles
@@ -2710,7 +2717,8 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, cons
   kern<<<(unsigned)(grp * groups), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf,
                                                     (int)ntiles, (int)L, (int)T, geo,
                                                     (const float2*)twz, (const float2*)tw4,
-                                                    (const float2*)tw2k, (float4*)part, err, poll);
+                                                    (const float2*)tw2k, b0idx, (float4*)part,
+                                                    err, poll);
   return cudaGetLastError();
 }
 
@@ -2939,8 +2947,9 @@ cudaError_t launch_dft_z(const void* in, void* out, int nx, int ny, int nz, cons
 
 template <typename R>
 cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm, double k,
-                            cudaStream_t s) {
-  k_geometry<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>(geo, nx, ny, nz, voxel_nm, k);
+                            cudaStream_t s, unsigned short* b0idx) {
+  k_geometry<R><<<grid1((long long)nx * ny, 256), 256, 0, s>>>(geo, nx, ny, nz, voxel_nm, k,
+                                                               b0idx);
   return cudaGetLastError();
 }
 
@@ -3097,7 +3106,8 @@ cudaError_t launch_validate(const void* M, long long n_entries, int* flag, cudaS
                                        cudaStream_t);                                             \
   template cudaError_t launch_fft_any<R>(const void*, void*, int, const AnyLines&, const void*,   \
                                          cudaStream_t);                                           \
-  template cudaError_t launch_geometry<R>(Geo<R>*, int, int, int, double, double, cudaStream_t);  \
+  template cudaError_t launch_geometry<R>(Geo<R>*, int, int, int, double, double, cudaStream_t,  \
+                                          unsigned short*);                                      \
   template cudaError_t launch_ewald<R>(const void*, int, int, int, const Geo<R>*, const void*,     \
                                        bool, const R*, void*, cudaStream_t, int*, unsigned);      \
   template cudaError_t launch_rotate_acc<R>(const void*, void*, int, int, double, bool,           \

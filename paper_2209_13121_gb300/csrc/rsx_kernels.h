@@ -204,14 +204,17 @@ bool yz_fusable(int nx, int ny, int nz);
 // Partial-bin slots of the fused pass: a work item's z-slices meet at most
 // this many blocks (their step ranges hold at least nz / (kYzSlots - 1)).
 constexpr int kYzSlots = 4;
+// b0idx: each pixel's lower q_z bin (launch_geometry's packed output).
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
-                          const void* twz, const void* tw4, const void* tw2k, void* part, int* err,
-                          int n_sm, unsigned poll, long long* L_out, cudaStream_t s);
+                          const void* twz, const void* tw4, const void* tw2k,
+                          const unsigned short* b0idx, void* part, int* err, int n_sm,
+                          unsigned poll, long long* L_out, cudaStream_t s);
 // The same for ny = 512 (16-column tiles, tensor map boxes of 32 floats x
 // 256 rows; twy the 512-point twiddle table).
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
-                             const void* twz, const void* twy, void* part, int* err, int n_sm,
-                             unsigned poll, long long* L_out, cudaStream_t s);
+                             const void* twz, const void* twy, const unsigned short* b0idx,
+                             void* part, int* err, int n_sm, unsigned poll, long long* L_out,
+                             cudaStream_t s);
 // The linearity path's per-energy bins (k_zbins5 layout) from launch_yz_tma
 // run over the five FFT'd N_t entries (nf = 5); dc = -(c-1)/(4 pi) N.
 cudaError_t launch_bins5_from_part(const void* part, int nx, int ny, int nz, long long L,
@@ -252,9 +255,11 @@ cudaError_t launch_col_fft(void* p, int L, long long S, long long W, const ColBa
 template <typename R>
 cudaError_t launch_dft_z(const void* in, void* out, int nx, int ny, int nz, const void* twz,
                          cudaStream_t s);
+// b0idx (optional): also each pixel's lower q_z bin as unsigned short (0
+// off the sphere), for the fused y+z passes.
 template <typename R>
 cudaError_t launch_geometry(Geo<R>* geo, int nx, int ny, int nz, double voxel_nm, double k,
-                            cudaStream_t s);
+                            cudaStream_t s, unsigned short* b0idx = nullptr);
 // err: device int that records a pipeline timeout (the bulk-copy pipeline
 // of the pruned path is used only when err is given and npix is a multiple
 // of 512).

@@ -57,8 +57,8 @@ def test_workspace_bytes_follows_table1(lib):
     table1 = (4 * c + 6) * N * 4 + 2 * npix * 4   # (4c+6) N + 2 nx ny Real
     # beyond Table 1: per-pixel geometry (32 B) and, for FP32 grids the fused
     # y+z pass takes, the two q_z bins of three fields in up to four partial
-    # slots (192 B)
-    assert table1 <= b <= table1 + 224 * npix + 64 * (nx + ny + nz) + 64
+    # slots (192 B) and each pixel's lower bin index (2 B)
+    assert table1 <= b <= table1 + 226 * npix + 64 * (nx + ny + nz) + 64
     # each further angle of a batch holds one more p (3 N complex float)
     for k in (2, 4, 8):
         assert rsx.workspace_bytes(rsx.make_config(nx, ny, nz, c, 5.0, angle_batch=k)) == \

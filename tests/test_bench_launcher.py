@@ -36,3 +36,13 @@ def test_gpus_must_agree_with_a_torchrun_environment():
                         "--check-launcher"], cwd=ROOT, env=env, capture_output=True, text=True,
                        timeout=120)
     assert r.returncode != 0 and "disagrees" in (r.stderr + r.stdout)
+
+
+def test_reference_arm_prints_its_line():
+    """bench.py --impl reference times the oracle on the host cores and
+    prints the reference line (no GPU needed)."""
+    out = _run("--impl", "reference", "--steps", "1", "--warmup", "0")
+    assert out["impl"] == "reference" and out["value"] > 0
+    assert out["unit"] == "Gvoxel-angle/s" and out["higher_is_better"] is True
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
+    assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
