@@ -550,10 +550,10 @@ def cpu_baseline(W, args, c):
 
 
 def cpu_report(args):
-    """The oracle's CPU baselines of the survey's plan: 128^2 x 16 and
-    256^2 x 32 (c = 4) and the 2048^2 x 1 film (c = 2), one energy and the 91
-    angles of 0:2:180, on one core and on every host core; seconds per
-    energy extrapolate linearly to the workloads' energy counts."""
+    """The oracle's CPU baselines: 128^2 x 16 and 256^2 x 32 (c = 4) and the
+    2048^2 x 1 film (c = 2), one energy and the 91 angles of 0:2:180, on one
+    core and on every host core; seconds per energy extrapolate linearly to
+    the workloads' energy counts."""
     cores = _host_cores()
     rows = []
     for shape, c, n_one in (((16, 128, 128), 4, 91), ((32, 256, 256), 4, 23),

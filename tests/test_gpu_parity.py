@@ -357,7 +357,7 @@ def test_run_matches_oracle(rsx, shape, c, prec):
 
 
 ODD = [((4, 6, 8), 2), ((3, 12, 10), 3), ((2, 9, 15), 2), ((3, 25, 48), 2), ((1, 45, 35), 2),
-       ((2, 16, 12), 2)]
+       ((2, 16, 12), 2), ((2, 3, 4093), 1), ((2, 4, 4096), 2)]   # the largest rows: prime, 2^12
 
 
 @pytest.mark.parametrize("algorithm", [1, 2, 3])
