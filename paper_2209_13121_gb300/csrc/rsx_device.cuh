@@ -546,22 +546,21 @@ __device__ __forceinline__ void any_butterfly(const C* x, C* y, int j, int n, in
   }
 }
 
-// One butterfly for any other radix (a prime above 7): each output is
-// summed straight from x, O(RAD^2) work; the combined exponent of the
-// pass twiddle and W_RAD^(r m) is reduced modulo n.
+// Output r of one butterfly for any other radix (a prime above 7), summed
+// straight from x (O(RAD) work; a pass spreads its outputs over threads);
+// the combined exponent of the pass twiddle and W_RAD^(r m) is reduced
+// modulo n.
 template <typename C>
-__device__ __forceinline__ void any_butterfly_prime(const C* x, C* y, int j, int rad, int n,
-                                                    int Ns, const C* tw) {
+__device__ __forceinline__ void any_output_prime(const C* x, C* y, int j, int r, int rad, int n,
+                                                 int Ns, const C* tw) {
   const int nb = n / rad, k = j % Ns, ts = n / (Ns * rad);
   const int o = (j - k) * rad + k;
-  for (int r = 0; r < rad; ++r) {
-    C acc = x[j];
-    for (int m = 1; m < rad; ++m) {
-      const long long e = (long long)m * k * ts + (long long)((r * m) % rad) * nb;
-      acc = cadd(acc, cmul(x[j + m * nb], tw[(int)(e % n)]));
-    }
-    y[o + r * Ns] = acc;
+  C acc = x[j];
+  for (int m = 1; m < rad; ++m) {
+    const long long e = (long long)m * k * ts + (long long)((r * m) % rad) * nb;
+    acc = cadd(acc, cmul(x[j + m * nb], tw[(int)(e % n)]));
   }
+  y[o + r * Ns] = acc;
 }
 
 }  // namespace rsx

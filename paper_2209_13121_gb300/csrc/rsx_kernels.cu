@@ -753,6 +753,30 @@ __device__ __forceinline__ void p_from_tacc(float ar, float ai, const float (&t)
 // keeps each slot with one transform group.  Per voxel and angle this
 // reads 16 c / n bytes of morphology instead of 16 c.  One persistent CTA
 // per SM.  Waits are bounded as in k_pol_fft4s_tma.
+// Roles of the 18 warps of the multi-angle x pass (8 polarisation, 9
+// transform, 1 producer).  A block's warps are dealt to the SM's four
+// schedulers by warp index mod 4, and the transform warps carry about twice
+// the per-warp work of the others, so they are spread 2, 2, 3, 2 over the
+// schedulers with the polarisation warps and the producer filling the rest:
+// kind 0 = polarisation (index 0..7), 1 = transform (index 0..8, group
+// index / 3, field index mod 3), 2 = producer.
+// Warps 0-7 and 10 transform (indices 0-7, 8), 16 produces, the other eight
+// polarise (8, 9, 11, 12, 13, 14, 15, 17 -> 0..7).  (P1: x pass 85.7 -> 84.6
+// ms per energy; the 2048-point rows, whose transforms are longer, keep warp
+// order: 3 % slower with this table.)
+__device__ __forceinline__ void multi_role(int w, int& kind, int& idx) {
+  if (w < 8 || w == 10) {
+    kind = 1;
+    idx = w < 8 ? w : 8;
+  } else if (w == 16) {
+    kind = 2;
+    idx = 0;
+  } else {
+    kind = 0;
+    idx = w - 8 - (w > 10) - (w > 16);
+  }
+}
+
 template <int S, int NPB, int PW, int FG, int NX, int KMAX>
 __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_multi(
     const float4* __restrict__ M, long long N, long long nrows, PolParams<float> pp,
@@ -778,6 +802,14 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
   unsigned long long* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  static_assert(PW == 8 && FG == 3, "role table");
+  int kind, ridx;
+  if constexpr (NX == 2048) {  // measured faster in warp order for 2048-point rows
+    kind = w < PW ? 0 : w < PW + 3 * FG ? 1 : 2;
+    ridx = w < PW ? w : w - PW;
+  } else {
+    multi_role(w, kind, ridx);
+  }
   if (t == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
@@ -801,7 +833,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
       blockIdx.x < nrows ? (nrows - 1 - blockIdx.x) / gridDim.x + 1 : 0;
   const int per_row = pp.c;
 
-  if (w == PW + 3 * FG) {  // producer warp, one lane (as in k_pol_fft4s_tma)
+  if (kind == 2) {  // producer warp, one lane (as in k_pol_fft4s_tma)
     if (lane != 0) return;
     // stage g = (row rr, segment h, component j), j fastest
     const int G = (int)nmine * H * per_row;
@@ -827,7 +859,8 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
     return;
   }
 
-  if (w < PW) {  // polarisation warps
+  if (kind == 0) {  // polarisation warps; pt: this thread's index among them
+    const int pt = ridx * 32 + lane;
     bool failed = false;
     int slot = 0, ph = 0;
     for (int rr = 0; rr < (int)nmine; ++rr) {
@@ -849,7 +882,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
           const float4* st = stage + cs * SV;
           float4 cur[SL];
 #pragma unroll
-          for (int sl = 0; sl < SL; ++sl) cur[sl] = st[t + sl * TP];
+          for (int sl = 0; sl < SL; ++sl) cur[sl] = st[pt + sl * TP];
           __syncwarp();
           if (lane == 0) mbar_arrive(&empty[cs]);
 #pragma unroll
@@ -879,7 +912,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
             const float ce = ang_ce[k], se = ang_se[k];
 #pragma unroll
             for (int sl = 0; sl < SL; ++sl) {
-              const int e = t + sl * TP;
+              const int e = pt + sl * TP;
               C out[3];
               p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, out);
               Pi[e] = out[0];
@@ -895,7 +928,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
   }
 
   // transform warps: group fg, field f; buffers u = fg, fg + FG, ...
-  const int fg = (w - PW) / 3, f = (w - PW) % 3;
+  const int fg = ridx / 3, f = ridx % 3;
   const int U = (int)nmine * nk;
   for (int u = fg; u < U; u += FG) {
     const int i = u % NPB;
@@ -1254,20 +1287,32 @@ __global__ void __launch_bounds__(256) k_fft_any(const typename RT<R>::C* src,
   C* y = B;
   int Ns = 1;
   for (int ps = 0; ps < plan.np; ++ps) {
-    const int rad = plan.rad[ps], nb = n / rad, total = nl * nb;
-    for (int it = threadIdx.x; it < total; it += blockDim.x) {
-      const int t = lines_fast ? it % nl : it / nb, j = lines_fast ? it / nl : it % nb;
-      const C* xl = x + t * n;
-      C* yl = y + t * n;
-      switch (rad) {
-        case 2: any_butterfly<2>(xl, yl, j, n, Ns, tw); break;
-        case 3: any_butterfly<3>(xl, yl, j, n, Ns, tw); break;
-        case 4: any_butterfly<4>(xl, yl, j, n, Ns, tw); break;
-        case 5: any_butterfly<5>(xl, yl, j, n, Ns, tw); break;
-        case 7: any_butterfly<7>(xl, yl, j, n, Ns, tw); break;
-        case 8: any_butterfly<8>(xl, yl, j, n, Ns, tw); break;
-        case 16: any_butterfly<16>(xl, yl, j, n, Ns, tw); break;
-        default: any_butterfly_prime(xl, yl, j, rad, n, Ns, tw); break;
+    const int rad = plan.rad[ps], nb = n / rad;
+    const bool general = rad != 2 && rad != 3 && rad != 4 && rad != 5 && rad != 7 && rad != 8 &&
+                         rad != 16;
+    if (general) {
+      // other primes: one thread per output of a butterfly (O(rad) each)
+      const int total = nl * nb * rad;
+      for (int it = threadIdx.x; it < total; it += blockDim.x) {
+        const int r = it % rad, q = it / rad;
+        const int t = lines_fast ? q % nl : q / nb, j = lines_fast ? q / nl : q % nb;
+        any_output_prime(x + t * n, y + t * n, j, r, rad, n, Ns, tw);
+      }
+    } else {
+      const int total = nl * nb;
+      for (int it = threadIdx.x; it < total; it += blockDim.x) {
+        const int t = lines_fast ? it % nl : it / nb, j = lines_fast ? it / nl : it % nb;
+        const C* xl = x + t * n;
+        C* yl = y + t * n;
+        switch (rad) {
+          case 2: any_butterfly<2>(xl, yl, j, n, Ns, tw); break;
+          case 3: any_butterfly<3>(xl, yl, j, n, Ns, tw); break;
+          case 4: any_butterfly<4>(xl, yl, j, n, Ns, tw); break;
+          case 5: any_butterfly<5>(xl, yl, j, n, Ns, tw); break;
+          case 7: any_butterfly<7>(xl, yl, j, n, Ns, tw); break;
+          case 8: any_butterfly<8>(xl, yl, j, n, Ns, tw); break;
+          default: any_butterfly<16>(xl, yl, j, n, Ns, tw); break;
+        }
       }
     }
     __syncthreads();
