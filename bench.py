@@ -286,6 +286,7 @@ def run_ours(args):
     angle_batch = ctx.angle_batch
     ctx.set_morphology(M)
     ctx.set_optical_constants(mine, K)
+    zplan = [ctx.zfirst_plan(i) for i in range(n_steps)]
     out = torch.empty((1, ny, nx), device="cuda", dtype=M.dtype)
     stream = torch.cuda.current_stream()
 
@@ -349,6 +350,26 @@ def run_ours(args):
         # ceil(n_ang / kx) launches
         n_x = -(-n_ang // kx)
         per_voxel["pol_fftx"] = (src_bytes * n_x + 3 * cplx * n_ang) / n_x
+    # the z-first path (rsx_zfirst_plan): per energy, ns q_z planes of the
+    # nz slices are kept and kz angles share one read of the morphology.
+    # Per launch: the polarisation + z-FFT pass reads M and writes kz x 3 x ns
+    # planes; the x-FFT reads and writes them; the y-FFT + bin selection pass
+    # reads one angle's 3 x ns planes (bins per pixel not counted)
+    zplans = [zplan[i] for i in range(args.warmup, n_steps)]
+    zfirst = args.algorithm == 1 and all(z[0] > 0 for z in zplans)
+    if zfirst:
+        npix = nx * ny
+        tot = {"pol_fftx": 0.0, "fftx": 0.0, "ffty": 0.0}
+        for ns_i, _, kz_i in zplans:
+            n_pass = -(-n_ang // kz_i)
+            tot["pol_fftx"] += n_pass * src_bytes * N + n_ang * 3 * ns_i * npix * cplx
+            tot["fftx"] += n_ang * 2 * 3 * ns_i * npix * cplx
+            tot["ffty"] += n_ang * 3 * ns_i * npix * cplx
+        for k in tot:
+            launches = phases[k][1]
+            per_voxel[k] = tot[k] / (N * launches) if launches else 0.0
+        per_voxel["ewald"] = 0
+    per_voxel.setdefault("fftx", 0)
     bytes_per_voxel = per_voxel[top]
     t_ms, n_l = phases[top]
     if args.algorithm == 3 and top == "ewald":
@@ -364,6 +385,8 @@ def run_ours(args):
     # DRAM bytes per launch from an ncu capture of this kernel (the
     # multi-angle x pass is recorded per batch size)
     tkey = f"{top}-k{kx}" if (top == "pol_fftx" and kx > 1) else top
+    if zfirst:
+        tkey = f"zfirst-{top}"
     traffic = _traffic_from_profiles(args.workload, tkey, prec) if args.algorithm == 1 else None
     roofline = {"bound": "hbm", "kernel": top, "achieved": achieved, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s",
@@ -451,6 +474,8 @@ def run_ours(args):
                                    f"per step (of {n_e} over {e_lo:g}-{e_hi:g} eV)",
                        "voxels": N, "components": c, "angles_per_energy": n_ang,
                        "angle_batch": angle_batch,
+                       "zfirst_planes": sorted({z[0] for z in zplans}) if zfirst else None,
+                       "angles_per_pass": sorted({z[2] for z in zplans}) if zfirst else None,
                        "precision": prec, "parallelism": f"energy-sharded x{ws}",
                        "ranks_per_gpu": -(-ws // ndev),
                        "l2": f"inputs larger than L2 (morphology {N * c * 4 * real / 1e9:.1f} GB)"},

@@ -122,6 +122,26 @@ size_t rsx_workspace_bytes(const rsx_config* cfg);
  * default and the shape rules above), or -1 for a NULL context. */
 int rsx_angle_batch(const rsx_context* ctx);
 
+/* The z-first path of Algorithm 1 (FP32, nz = 32, 64 or 128, nx and ny =
+ * 512, 1024 or 2048).  The 3-D FFT of Algorithm 1 is separable, so its z
+ * transform may come first; a detector pixel reads only the two q_z bins
+ * b0 = floor(q_z / dq_z) and b0 + 1 of Eq. (Ewald), and since q_z <= 0 on
+ * the sphere all pixels of one energy read one cyclic run of bins ending at
+ * bin 1.  On this path rsx_run forms p, transforms each pixel's z column,
+ * keeps only that run's planes, and x- and y-transforms those planes
+ * instead of all nz slices (the same transform values; only the rounding
+ * order differs).  It serves an energy when the run holds at most 3/4 of the
+ * nz bins; the angles of one morphology read are then up to
+ * min(8, angle_batch * nz / n_planes).
+ * For energy_index: *n_planes receives the run length (0 when the path does
+ * not serve this context or energy), *first_bin its first bin (the run is
+ * first_bin, ..., first_bin + n_planes - 1 mod nz), *angles_per_pass the
+ * angles per morphology read; any of them may be NULL.  Errors:
+ * RSX_ERR_INVALID (NULL context, index out of range), RSX_ERR_STATE (no
+ * optical constants yet). */
+int rsx_zfirst_plan(const rsx_context* ctx, int energy_index, int* n_planes, int* first_bin,
+                    int* angles_per_pass);
+
 /* Number of e-field angles in the inclusive list start:increment:end
  * (degrees, Algorithm 1 "E_Angle [start, increment, end]"); 1 when rotation
  * is 0.  Returns -1 for increment <= 0, end < start or non-finite input. */
@@ -180,13 +200,15 @@ int rsx_run(rsx_context* ctx, double start_deg, double increment_deg, double end
 
 /* ---- per-phase device timers (the Polarization, FFT, Scatter3DEwalds and
  * Rotation timers of the breakdowns in Sec. 6) -------------------------- */
-#define RSX_PHASE_POL_FFTX 0 /* polarisation fused with the x-FFT           */
+#define RSX_PHASE_POL_FFTX 0 /* polarisation fused with the x-FFT (z-first  */
+                             /* path: with the z-FFT)                        */
 #define RSX_PHASE_FFTY 1     /* y-FFT                                         */
 #define RSX_PHASE_EWALD 2    /* pruned q_z transform + scatter + Ewald        */
 #define RSX_PHASE_ROTATE 3   /* detector rotation and accumulation            */
 #define RSX_PHASE_OTHER 4    /* geometry, averaging, validation, z/x FFTs     */
 #define RSX_PHASE_NT 5       /* N_t of Algorithm 3 (Algorithm 2 contexts)     */
-#define RSX_N_PHASES 6
+#define RSX_PHASE_FFTX 6     /* z-first path: x-FFT of the kept q_z planes    */
+#define RSX_N_PHASES 7
 
 /* enable != 0: every kernel the context launches from now on is bracketed by
  * two CUDA events on its stream (a few microseconds each); 0 stops that. */

@@ -283,11 +283,7 @@ int upload_tw2k(rsx_context* c) {
   return RSX_OK;
 }
 
-// A tensor map over `ncomp` fields of [nz][ny][nx] complex float viewed as
-// [ncomp nz][ny][2 nx] floats with box_x x 256 x 1 boxes (box_x floats: 16
-// for 8-column tiles, 32 for 16-column tiles).
-bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m, unsigned box_x,
-               CUtensorMapL2promotion promo) {
+PFN_cuTensorMapEncodeTiled_v12000 tmap_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -295,11 +291,22 @@ bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m, unsi
     if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
                                          &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
-      return false;
+      return nullptr;
     encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
   }
+  return encode;
+}
+
+// A tensor map over `nslices` [ny][nx] complex float planes (fields x
+// z-slices, or fields x kept q_z planes) viewed as [nslices][ny][2 nx]
+// floats with box_x x 256 x 1 boxes (box_x floats: 16 for 8-column tiles,
+// 32 for 16-column tiles).
+bool make_tmap(rsx_context* c, void* base, long long nslices, CUtensorMap* m, unsigned box_x,
+               CUtensorMapL2promotion promo) {
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+  if (!encode) return false;
   const rsx_config& g = c->cfg;
-  const cuuint64_t dims[3] = {2 * (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)(ncomp * g.nz)};
+  const cuuint64_t dims[3] = {2 * (cuuint64_t)g.nx, (cuuint64_t)g.ny, (cuuint64_t)nslices};
   const cuuint64_t strides[2] = {2 * (cuuint64_t)g.nx * sizeof(float),
                                  (cuuint64_t)g.ny * 2 * g.nx * sizeof(float)};
   const cuuint32_t box[3] = {box_x, 256, 1};
@@ -307,6 +314,25 @@ bool make_tmap(rsx_context* c, void* base, long long ncomp, CUtensorMap* m, unsi
   return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, promo,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+         CUDA_SUCCESS;
+}
+
+// The z-first pass's tensor map over the FP32 morphology, viewed as
+// [c nz][ny][4 nx] floats: boxes of 128 / nz adjacent voxels (4 floats each)
+// of one row y by the nz slices of one component (16 KB).
+bool make_tmap_m(rsx_context* c, CUtensorMap* m) {
+  const PFN_cuTensorMapEncodeTiled_v12000 encode = tmap_encoder();
+  if (!encode || !c->M || ((uintptr_t)c->M & 15)) return false;
+  const rsx_config& g = c->cfg;
+  const cuuint64_t dims[3] = {4 * (cuuint64_t)g.nx, (cuuint64_t)g.ny,
+                              (cuuint64_t)g.n_components * g.nz};
+  const cuuint64_t strides[2] = {4 * (cuuint64_t)g.nx * sizeof(float),
+                                 (cuuint64_t)g.ny * 4 * g.nx * sizeof(float)};
+  const cuuint32_t box[3] = {(cuuint32_t)(4 * (1024 / g.nz)), 1, (cuuint32_t)g.nz};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(c->M), dims, strides, box,
+                estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
          CUDA_SUCCESS;
 }
 
@@ -425,14 +451,18 @@ int ensure_nt(rsx_context* c, int ie, cudaStream_t s) {
 // The fused y-FFT + q_z bins pass over nf fields (3: p; 5: the linearity
 // path's N_t entries) through the tensor map `map`: the 1024-row kernel or
 // the 512-row one.
-cudaError_t fused_yz(rsx_context* c, const CUtensorMap* map, int nf, long long* L, cudaStream_t s) {
+// sel: the z-first path's ns planes per field (sel.nzfull > 0) instead of
+// the nz slices.
+cudaError_t fused_yz(rsx_context* c, const CUtensorMap* map, int nf, long long* L, cudaStream_t s,
+                     rsx::YzSel sel = rsx::YzSel(), int ns = 0) {
   const rsx_config& g = c->cfg;
+  const int nzv = sel.nzfull > 0 ? ns : g.nz;
   if (g.ny == 512)
-    return rsx::launch_yz512_tma(map, g.nx, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->twy,
-                                 c->b0idx, c->part, c->err, c->n_sm, c->wait_polls, L, s);
-  return rsx::launch_yz_tma(map, g.nx, g.ny, g.nz, nf, (const Geo<float>*)c->geo, c->twz, c->tw4,
+    return rsx::launch_yz512_tma(map, g.nx, nzv, nf, (const Geo<float>*)c->geo, c->twz, c->twy,
+                                 c->b0idx, c->part, c->err, c->n_sm, c->wait_polls, L, s, sel);
+  return rsx::launch_yz_tma(map, g.nx, g.ny, nzv, nf, (const Geo<float>*)c->geo, c->twz, c->tw4,
                             g.ny == 2048 ? c->twy : nullptr, c->b0idx, c->part, c->err, c->n_sm,
-                            c->wait_polls, L, s);
+                            c->wait_polls, L, s, sel);
 }
 
 // Linearity fast path, once per energy: FFT (x and y) of N_t's five
@@ -627,14 +657,25 @@ static size_t part_bytes(const rsx_config* cfg) {
   return rsx::kYzSlots * (size_t)(cfg->algorithm == 3 ? 5 : 3) * cfg->nx * cfg->ny * 16;
 }
 
-// The angle batch a config gets: the multi-angle x pass serves FP32
-// Algorithm 1 on the shapes of the bulk-copy x pass and the fused y+z pass.
+// The z-first path serves FP32 Algorithm 1 with nz = 32, 64 or 128 and
+// nx, ny = 512, 1024 or 2048.
+static bool zfirst_ok(const rsx_config* cfg) {
+  return cfg->precision == 32 && cfg->algorithm == 1 &&
+         rsx::zfirst_fusable(cfg->nx, cfg->ny, cfg->nz);
+}
+
 // The multi-angle x pass serves FP32 Algorithm 1 with nx = 512, 1024 or
 // 2048 (2048-point rows: at most 3 angles per pass).
-static int angle_batch_cap(const rsx_config* cfg) {
+static int x_multi_cap(const rsx_config* cfg) {
   if (cfg->precision != 32 || cfg->algorithm != 1) return 0;
   if (cfg->nx == 512 || cfg->nx == 1024) return RSX_MAX_ANGLE_BATCH;
   return cfg->nx == 2048 ? 3 : 0;
+}
+
+// The angle batch a config gets (the number of p buffers): up to 8 where
+// the z-first path or the multi-angle x pass serves it.
+static int angle_batch_cap(const rsx_config* cfg) {
+  return zfirst_ok(cfg) ? RSX_MAX_ANGLE_BATCH : x_multi_cap(cfg);
 }
 
 static int angle_batch_of(const rsx_config* cfg) {
@@ -646,6 +687,59 @@ static int angle_batch_of(const rsx_config* cfg) {
   const double p_bytes = 3.0 * cfg->nx * cfg->ny * cfg->nz * 8.0;
   const int k = (int)((double)(32LL << 30) / p_bytes);
   return k < 1 ? 1 : k > cap ? cap : k;
+}
+
+// The z-first path's plan for one energy: the cyclic run of q_z bins its
+// pixels read and the angles per pass.  The run ends at bin 1 (q_z <= 0
+// on the sphere, so b0 <= 0); it starts one bin below the lowest b0 over
+// the pixels on the sphere (Eq. (Ewald) in double as k_geometry evaluates
+// it; the extra bin covers a rounding difference between the two), which
+// per row is reached at the largest |q_x| still on the sphere.
+struct ZPlan {
+  int kb = 0, ns = 0, kz = 0;
+};
+
+static int lowest_bin(const rsx_config& g, double k) {
+  const double two_pi = 2.0 * kPi;
+  const double dqx = two_pi / (g.nx * g.voxel_nm), dqz = two_pi / (g.nz * g.voxel_nm);
+  const int fmax = g.nx / 2;  // largest |f_x| on the FFT grid (nx even)
+  double tmin = 0.0;
+  for (int my = 0; my < g.ny; ++my) {
+    const int fy = my < (g.ny + 1) / 2 ? my : my - g.ny;
+    const double qy = two_pi * fy / (g.ny * g.voxel_nm);
+    const double r2 = k * k - qy * qy;
+    if (r2 < 0.0) continue;
+    double fl = floor(sqrt(r2) / dqx);
+    int f = fl < (double)fmax ? (int)fl : fmax;
+    while (f < fmax && (dqx * (f + 1)) * (dqx * (f + 1)) <= r2) ++f;
+    while (f > 0 && (dqx * f) * (dqx * f) > r2) --f;
+    const double qx = dqx * f;
+    const double rad = k * k - qx * qx - qy * qy;
+    if (rad < 0.0) continue;
+    const double t = (-k + sqrt(rad)) / dqz;
+    if (t < tmin) tmin = t;
+  }
+  return (int)floor(tmin);
+}
+
+static bool zfirst_plan(const rsx_context* c, int ie, ZPlan* zp) {
+  const rsx_config& g = c->cfg;
+  if (!zfirst_ok(&g) || c->n_sm <= 0 || !c->part || !c->b0idx || ie < 0 ||
+      ie >= (int)c->energies.size() || (c->M && ((uintptr_t)c->M & 15)))
+    return false;
+  if ((g.nx == 1024 && !c->tw4) || (g.nx == 2048 && !c->tw2k) || (g.ny == 2048 && !c->twy))
+    return false;
+  const int blo = lowest_bin(g, wavenumber(c->energies[ie])) - 1;
+  const int ns = 2 - blo;
+  // worth it while at most 3/4 of the bins are kept (the z transform costs
+  // about what the dropped planes' x and y transforms save at ~0.8)
+  if (4 * ns > 3 * g.nz) return false;
+  zp->ns = ns;
+  zp->kb = ((blo % g.nz) + g.nz) % g.nz;
+  // the kept planes of kz angles fit in the kx p buffers of 3 nz planes each
+  const int kz = (int)((long long)c->kx * g.nz / ns);
+  zp->kz = kz < rsx::kMaxXAngles ? kz : rsx::kMaxXAngles;
+  return zp->kz >= 1;
 }
 
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
@@ -670,6 +764,20 @@ size_t rsx_workspace_bytes(const rsx_config* cfg) {
 }
 
 int rsx_angle_batch(const rsx_context* c) { return c ? c->kx : -1; }
+
+int rsx_zfirst_plan(const rsx_context* c, int ie, int* n_planes, int* first_bin,
+                    int* angles_per_pass) {
+  if (!c) return fail(RSX_ERR_INVALID, "context is NULL");
+  if (c->energies.empty()) return fail(RSX_ERR_STATE, "no optical constants set");
+  if (ie < 0 || ie >= (int)c->energies.size())
+    return fail(RSX_ERR_INVALID, "energy index %d out of range [0, %zu)", ie, c->energies.size());
+  ZPlan zp;
+  if (!zfirst_plan(c, ie, &zp)) zp = ZPlan();
+  if (n_planes) *n_planes = zp.ns;
+  if (first_bin) *first_bin = zp.kb;
+  if (angles_per_pass) *angles_per_pass = zp.kz;
+  return RSX_OK;
+}
 
 int rsx_angle_count(double start, double inc, double end, int rotation) {
   if (!rotation) return 1;
@@ -764,9 +872,11 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
   if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess)
     c->n_sm = 0;
   if (cfg->precision == 32 && cfg->ny == 1024 && cfg->nx % 8 == 0 && c->n_sm > 0) {
-    c->has_tmap_p = make_tmap(c, c->p, 3, &c->tmap_p, 16, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
+    c->has_tmap_p =
+        make_tmap(c, c->p, 3LL * cfg->nz, &c->tmap_p, 16, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
     if (c->ft)
-      c->has_tmap_ft = make_tmap(c, c->ft, 5, &c->tmap_ft, 16, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
+      c->has_tmap_ft =
+          make_tmap(c, c->ft, 5LL * cfg->nz, &c->tmap_ft, 16, CU_TENSOR_MAP_L2_PROMOTION_L2_256B);
   }
   if (uses_yz(cfg) && c->n_sm > 0) {
     // the fused y+z pass: 1024-row tiles are 8 columns wide and two blocks
@@ -777,11 +887,11 @@ int rsx_create(const rsx_config* cfg, rsx_context** out) {
     c->has_tmap_pz = true;
     for (int k = 0; k < c->kx; ++k)
       c->has_tmap_pz = c->has_tmap_pz &&
-                       make_tmap(c, (char*)c->p + (size_t)k * 3 * c->N * Cs, 3, &c->tmap_pz[k],
-                                 box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+                       make_tmap(c, (char*)c->p + (size_t)k * 3 * c->N * Cs, 3LL * cfg->nz,
+                                 &c->tmap_pz[k], box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
     if (c->ft)
-      c->has_tmap_ftz =
-          make_tmap(c, c->ft, 5, &c->tmap_ftz, box, CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
+      c->has_tmap_ftz = make_tmap(c, c->ft, 5LL * cfg->nz, &c->tmap_ftz, box,
+                                  CU_TENSOR_MAP_L2_PROMOTION_L2_128B);
   }
   if (cfg->algorithm == 3 &&
       (e = cudaMalloc(&c->imgs, (size_t)rsx::kMaxAngleBatch * c->npix * R)) != cudaSuccess) {
@@ -1035,8 +1145,9 @@ int run_energy_angles_batched(rsx_context* c, int ie, double start, double inc, 
   const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
   const void* tw = g.nx == 1024 ? c->tw4 : g.nx == 2048 ? c->tw2k : c->twx;
   const bool fused = c->part && c->has_tmap_pz;
-  for (int a0 = 0; a0 < nang; a0 += c->kx) {
-    const int nk = nang - a0 < c->kx ? nang - a0 : c->kx;
+  const int cap = x_multi_cap(&g), kx = c->kx < cap ? c->kx : cap;
+  for (int a0 = 0; a0 < nang; a0 += kx) {
+    const int nk = nang - a0 < kx ? nang - a0 : kx;
     rsx::XAngles ang;
     memset(&ang, 0, sizeof(ang));
     ang.n = nk;
@@ -1087,11 +1198,83 @@ int run_energy_angles_batched(rsx_context* c, int ie, double start, double inc, 
   return RSX_OK;
 }
 
+// All angles of one energy on the z-first path (plan from zfirst_plan):
+// per batch of up to kz angles, the polarisation + z-FFT pass keeps the ns
+// q_z planes of every angle (packed: angle k, field f, plane s at
+// ((k * 3 + f) * ns + s) * nx * ny), one launch x-transforms all their rows,
+// then per angle the fused y-FFT pass picks each pixel's two bins from the
+// planes, the image and the rotation follow as on the other paths.
+int run_energy_zfirst(rsx_context* c, int ie, double start, double inc, int nang, int rotation,
+                      const ZPlan& zp, cudaStream_t s) {
+  const rsx_config& g = c->cfg;
+  int rc = ensure_geo<float>(c, ie, s);
+  if (rc) return rc;
+  CUtensorMap tm_m;
+  if (!make_tmap_m(c, &tm_m)) return fail(RSX_ERR_CUDA, "morphology tensor map");
+  const PolParams<float> pp = make_params<float>(c, ie, 0.0, 0);
+  const double ref = -(double)(g.n_components - 1) / (4.0 * kPi) * (double)c->N;
+  const long long fstride = (long long)zp.ns * c->npix, kstride = 3 * fstride;
+  const void* twx = g.nx == 1024 ? c->tw4 : g.nx == 2048 ? c->tw2k : c->twx;
+  const unsigned box = g.ny == 512 ? 32 : g.ny == 2048 ? 8 : 16;
+  const rsx::YzSel sel = {zp.kb, g.nz};
+  for (int a0 = 0; a0 < nang; a0 += zp.kz) {
+    const int nk = nang - a0 < zp.kz ? nang - a0 : zp.kz;
+    rsx::XAngles ang;
+    memset(&ang, 0, sizeof(ang));
+    ang.n = nk;
+    double alpha[RSX_MAX_ANGLE_BATCH];
+    for (int k = 0; k < nk; ++k) {
+      alpha[k] = rotation ? (start + inc * (a0 + k)) * (kPi / 180.0) : 0.0;
+      ang.ce[k] = (float)cos(alpha[k]);
+      ang.se[k] = (float)sin(alpha[k]);
+    }
+    {
+      PhaseTimer pt(c, RSX_PHASE_POL_FFTX, s);
+      RSX_CK(rsx::launch_pol_zfft_multi(&tm_m, g.nx, g.ny, g.nz, pp, ang, c->p, kstride, fstride,
+                                        zp.kb, zp.ns, c->twz, c->err, c->n_sm, c->wait_polls, s),
+             "polarisation + z-FFT kernel");
+    }
+    {
+      PhaseTimer pt(c, RSX_PHASE_FFTX, s);
+      RSX_CK(rsx::launch_xfft_rows(c->p, g.nx, (long long)nk * 3 * zp.ns * g.ny, twx, s),
+             "x-FFT kernel");
+    }
+    for (int k = 0; k < nk; ++k) {
+      float dc[3] = {(float)ref, 0.f, 0.f};
+      if (g.frame != RSX_FRAME_LITERAL) {
+        dc[0] = (float)(ref * cos(alpha[k]));
+        dc[1] = (float)(ref * sin(alpha[k]));
+      }
+      CUtensorMap tm;
+      if (!make_tmap(c, (char*)c->p + (size_t)k * kstride * sizeof(float2), 3LL * zp.ns, &tm, box,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B))
+        return fail(RSX_ERR_CUDA, "q_z plane tensor map");
+      long long L = 0;
+      {
+        PhaseTimer pt(c, RSX_PHASE_FFTY, s);
+        RSX_CK(fused_yz(c, &tm, 3, &L, s, sel, zp.ns), "y-FFT + bin selection kernel");
+      }
+      {
+        PhaseTimer pt(c, RSX_PHASE_EWALD, s);
+        RSX_CK(rsx::launch_ewald_bins(c->part, g.nx, g.ny, zp.ns, L, (const Geo<float>*)c->geo,
+                                      dc[0], dc[1], dc[2], (float*)c->img, s),
+               "Ewald kernel");
+      }
+      PhaseTimer pt(c, RSX_PHASE_ROTATE, s);
+      RSX_CK(rsx::launch_rotate_acc<float>(c->img, c->acc, g.nx, g.ny, alpha[k], rotation != 0, s),
+             "rotation kernel");
+    }
+  }
+  return RSX_OK;
+}
+
 template <typename R>
 int run_energy_angles(rsx_context* c, int ie, double start, double inc, int nang, int rotation,
                       cudaStream_t s) {
   if constexpr (sizeof(R) == 4) {
-    if ((c->kx > 1 || c->cfg.nx == 2048) && angle_batch_cap(&c->cfg) && c->n_sm > 0 &&
+    ZPlan zp;
+    if (zfirst_plan(c, ie, &zp)) return run_energy_zfirst(c, ie, start, inc, nang, rotation, zp, s);
+    if ((c->kx > 1 || c->cfg.nx == 2048) && x_multi_cap(&c->cfg) && c->n_sm > 0 &&
         ((uintptr_t)c->M & 15) == 0)
       return run_energy_angles_batched(c, ie, start, inc, nang, rotation, s);
   }

@@ -946,6 +946,266 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
   }
 }
 
+// ------------------------------------------------------ z-first x pass
+// Algorithm 1's 3-D FFT of p, z axis first.  Each detector pixel reads two
+// q_z bins of the transform, b0 = floor(t) and b0 + 1 with t = q_z / dq_z
+// (Eq. (Ewald)); q_z <= 0 on the sphere and falls as the in-plane |q|
+// grows, so over all pixels of one energy the bins read are the cyclic run
+// kb, kb + 1, ..., kb + ns - 1 (mod nz) that ends at bin 1.  The 3-D DFT is
+// separable, so its z transform may come first; the nz - ns bins no pixel
+// reads are then dropped before the x and y transforms, which run on ns
+// planes instead of nz slices (P1 geometry: ns ~ 37 of 128).
+//
+// This pass forms p as k_pol_fft4s_tma_multi does (same roles, ring and
+// arithmetic: the morphology sums once per voxel, then each angle's p) but
+// over tiles of XW = 32 / R adjacent pixels of one row y by the whole stack
+// nz = 32 R (1024 voxels, one 3-D tensor copy per component), transforms
+// every pixel's z column and stores planes s < ns (bin kb + s mod nz) of
+// angle k at out + k * kstride + f * fstride + s * nx * ny (+ y nx + x).
+//
+// Row buffers hold a field as XW lines of LS complex (line px, sample z at
+// px * LS + z).  A transform warp takes one field of one buffer:
+//   nz = 32 R, n = n1 + R n2, k = k2 + 32 k1, lane = n1 XW + px:
+//   stage 1: the 32-point DFT over n2 of samples n1 + R n2 of line px,
+//            times W_nz^(n1 k2), written back as Y[n1][k2] (pitch P2);
+//   stage 2: lane (px, n1) takes k2 = n1 + R m: the R-point DFT over n1
+//            gives X[k2 + 32 k1], written back to px * LS + k;
+// then the warp copies the ns kept bins of its XW lines out (XW adjacent
+// pixels per plane row).  LS and P2 keep the polarisation stores, both
+// stages and the copy free of shared-memory bank conflicts (checked per
+// half-warp for R = 1, 2, 4).
+template <int R> struct ZfLayout {
+  static constexpr int NZ = 32 * R, XW = 32 / R, LXW = R == 1 ? 5 : R == 2 ? 4 : 3;
+  static constexpr int LS = R == 4 ? 146 : NZ + 1, P2 = R == 4 ? 33 : 32, FS = XW * LS;
+};
+
+template <int R>
+__device__ __forceinline__ void zfft_lines(float2* F, const float2* twt, int lane) {
+  using C = float2;
+  using Lay = ZfLayout<R>;
+  constexpr int XW = Lay::XW, LS = Lay::LS, P2 = Lay::P2;
+  const int px = lane & (XW - 1), n1 = lane >> Lay::LXW;
+  C* Ln = F + px * LS;
+  C v[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) v[n2] = Ln[n1 + R * n2];
+  dft32(v);
+  if constexpr (R == 1) {  // the lane's own line: X[k] = v[k]
+#pragma unroll
+    for (int k = 0; k < 32; ++k) Ln[k] = v[k];
+  } else {
+#pragma unroll
+    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], twt[k2 * R + n1]);
+    __syncwarp();
+#pragma unroll
+    for (int k2 = 0; k2 < 32; ++k2) Ln[n1 * P2 + k2] = v[k2];
+    __syncwarp();
+    C y[32];  // [m][n1'] for k2 = n1 + R m
+#pragma unroll
+    for (int m = 0; m < 32 / R; ++m)
+#pragma unroll
+      for (int q = 0; q < R; ++q) y[m * R + q] = Ln[q * P2 + n1 + R * m];
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < 32 / R; ++m) {
+      if constexpr (R == 4)
+        dft4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
+      else
+        dft2(y[2 * m], y[2 * m + 1]);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) Ln[n1 + R * m + 32 * k1] = y[m * R + k1];
+    }
+  }
+  __syncwarp();
+}
+
+template <int R, int S, int NPB, int PW, int FG, int KMAX>
+__global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
+    const __grid_constant__ CUtensorMap tmap, int nx, long long npix, long long ntiles,
+    PolParams<float> pp, XAngles ang, float2* __restrict__ out, long long kstride,
+    long long fstride, int kb, int ns, const float2* __restrict__ twz_g,
+    int* __restrict__ err, unsigned poll) {
+  using C = float2;
+  using Lay = ZfLayout<R>;
+  constexpr int NZ = Lay::NZ, XW = Lay::XW, LXW = Lay::LXW, LS = Lay::LS, FS = Lay::FS;
+  constexpr int SV = 1024, TP = 32 * PW, SL = SV / TP, NB = TP + 96;
+  static_assert(KMAX <= kMaxXAngles && SV % TP == 0 && 1 + 2 * NPB <= 16 && NPB % FG == 0,
+                "layout");
+  static_assert(PW == 8 && FG == 3, "role table");
+  constexpr unsigned kPoll = 1u << 22, kStageBytes = SV * sizeof(float4);
+  extern __shared__ __align__(128) unsigned char smem_a128[];
+  float4* stage = reinterpret_cast<float4*>(smem_a128);  // [S][NZ][XW] voxels
+  C* P = reinterpret_cast<C*>(stage + S * SV);            // [NPB][3][FS]
+  C* twt = P + NPB * 3 * FS;                              // [32][R]: W_nz^(n1 k2)
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(twt + 32 * R);
+  unsigned long long* empty = full + S;
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
+  const int t = threadIdx.x, w = t >> 5, lane = t & 31;
+  int kind, ridx;
+  multi_role(w, kind, ridx);
+  if (t == 0) {
+    for (int i = 0; i < S; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], PW);
+    }
+    *abort_flag = 0;
+    fence_proxy_async();
+  }
+  for (int i = t; i < 32 * R; i += blockDim.x) twt[i] = twz_g[(i / R) * (i % R)];
+  __shared__ float ang_ce[KMAX], ang_se[KMAX];  // indexed by a run-time angle
+  if (t == 0) {
+#pragma unroll
+    for (int i = 0; i < KMAX; ++i) {  // constant indices: the parameters stay in place
+      ang_ce[i] = ang.ce[i];
+      ang_se[i] = ang.se[i];
+    }
+  }
+  __syncthreads();
+  const int nk = ang.n;
+  const long long nmine =
+      blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int per_row = pp.c;
+  const int nxt = nx >> LXW;  // tiles per row y
+
+  if (kind == 2) {  // producer lane: stage g = (tile rr, component j), j fastest
+    if (lane != 0) return;
+    const int G = (int)nmine * per_row;
+    int g = 0, slot = 0, k = 0, j = 0;
+    long long tile = blockIdx.x;
+    for (; g < G; ++g) {
+      if (k > 0 && !mbar_wait_bounded(&empty[slot], (unsigned)((k - 1) & 1), poll)) {
+        atomicOr(err, 1);
+        *abort_flag = 1;
+        break;
+      }
+      const int y = (int)(tile / nxt), xb = (int)(tile - (long long)y * nxt);
+      mbar_expect_tx(&full[slot], kStageBytes);
+      tma_load_3d(stage + slot * SV, &tmap, xb * XW * 4, y, j * NZ, &full[slot]);
+      if (++slot == S) slot = 0, ++k;
+      if (++j == per_row) j = 0, tile += gridDim.x;
+    }
+    for (int d = g - 1; d >= 0 && d >= g - S; --d)
+      mbar_wait_bounded(&full[d % S], (unsigned)((d / S) & 1), kPoll);
+    return;
+  }
+
+  if (kind == 0) {  // polarisation warps; pt: this thread's index among them
+    const int pt = ridx * 32 + lane;
+    bool failed = false;
+    int slot = 0, ph = 0;
+    for (int rr = 0; rr < (int)nmine; ++rr) {
+      TAcc acc[SL];
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) tacc_zero(acc[sl]);
+      for (int j = 0; j < per_row; ++j) {
+        const int cs = slot, cph = ph;
+        if (++slot == S) slot = 0, ph ^= 1;
+        failed = failed || __any_sync(0xffffffffu, *abort_flag != 0);
+        if (failed) break;
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[cs], (unsigned)cph, poll))) {
+          failed = true;
+          atomicOr(err, 1);
+          *abort_flag = 1;
+          break;
+        }
+        const float4* st = stage + cs * SV;
+        float4 cur[SL];
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl) cur[sl] = st[pt + sl * TP];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[cs]);
+#pragma unroll
+        for (int sl = 0; sl < SL; ++sl)
+          tacc_add(acc[sl], cur[sl].x, cur[sl].y, cur[sl].z, cur[sl].w, pp, j);
+      }
+      const float inv = float(1.0 / kFourPi);
+#pragma unroll
+      for (int sl = 0; sl < SL; ++sl) {
+        acc[sl].aw = ((acc[sl].aw - 1.f) + acc[sl].as[0]) * inv;
+        acc[sl].as[1] *= inv;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          acc[sl].t[q][0] *= inv;
+          acc[sl].t[q][1] *= inv;
+        }
+      }
+      for (int k = 0; k < nk; ++k) {
+        const int u = rr * nk + k, i = u % NPB;
+        if (u >= NPB) named_bar_sync(1 + NPB + i, NB);  // previous use done
+        if (!failed) {
+          C* Pi = P + i * 3 * FS;
+          const float ce = ang_ce[k], se = ang_se[k];
+#pragma unroll
+          for (int sl = 0; sl < SL; ++sl) {
+            const int e = pt + sl * TP;  // voxel (z, px) of the tile
+            const int at = (e & (XW - 1)) * LS + (e >> LXW);
+            C o3[3];
+            p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, o3);
+            Pi[at] = o3[0];
+            Pi[FS + at] = o3[1];
+            Pi[2 * FS + at] = o3[2];
+          }
+        }
+        named_bar_arrive(1 + i, NB);
+      }
+    }
+    return;
+  }
+
+  // transform warps: group fg, field f; buffers u = fg, fg + FG, ...
+  const int fg = ridx / 3, f = ridx % 3;
+  const int U = (int)nmine * nk;
+  const int cnt = ns * XW;
+  for (int u = fg; u < U; u += FG) {
+    const int i = u % NPB;
+    named_bar_sync(1 + i, NB);
+    if (*abort_flag == 0) {
+      const int rr = u / nk, k = u - rr * nk;
+      const long long tile = blockIdx.x + (long long)rr * gridDim.x;
+      const int y = (int)(tile / nxt), x0 = (int)(tile - (long long)y * nxt) * XW;
+      C* F = P + i * 3 * FS + f * FS;
+      zfft_lines<R>(F, twt, lane);
+      C* o = out + (size_t)k * kstride + (size_t)f * fstride + (size_t)y * nx + x0;
+      for (int idx = lane; idx < cnt; idx += 32) {
+        const int s = idx >> LXW, px = idx & (XW - 1);
+        o[(size_t)s * npix + px] = F[px * LS + ((kb + s) & (NZ - 1))];
+      }
+      __syncwarp();
+    }
+    if (u + NPB < U) named_bar_arrive(1 + NPB + i, NB);
+  }
+}
+
+// x-FFT of contiguous rows of NX complex in place (the kept q_z planes of
+// the z-first path): one warp per row, the row staged in shared memory in
+// the layout xfft_row<NX> takes (2048 points: halves at 0 and 1056), then
+// xfft_row's four-step transform writes it back.  tw_g: the table xfft_row
+// uses (1024: W1024^(n1 k2) as [32][32]; 2048: that, then W2048^n, n < 1024;
+// 512: W512^j).
+template <int NX, int W>
+__global__ void __launch_bounds__(32 * W) k_xfft_rows(float2* __restrict__ data, long long nrows,
+                                                      const float2* __restrict__ tw_g) {
+  using C = float2;
+  constexpr int FS = NX == 2048 ? 2 * 1056 : (NX / 32) * 33;
+  constexpr int NTW = NX == 2048 ? 2048 : NX == 1024 ? 1024 : 512;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* F = tw + NTW + (threadIdx.x >> 5) * FS;
+  for (int i = threadIdx.x; i < NTW; i += 32 * W) tw[i] = tw_g[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long row = (long long)blockIdx.x * W + (threadIdx.x >> 5);
+  if (row >= nrows) return;
+  C* r = data + (size_t)row * NX;
+#pragma unroll 16
+  for (int j = 0; j < NX / 32; ++j) {
+    const int n = lane + 32 * j;
+    F[NX == 2048 && n >= 1024 ? n + 32 : n] = r[n];
+  }
+  __syncwarp();
+  xfft_row<NX>(F, tw, r, lane, [] {});
+}
+
 // y pass: a tile of TX adjacent columns of one batch.  Thread (n1, col)
 // loads rows n1 + 32 n2 straight from global memory (32 independent loads),
 // transforms over n2 in registers, applies the twiddles and writes row k2 of
@@ -1620,7 +1880,13 @@ __device__ __forceinline__ void yz2k_load(const float2* xb, int r0, int c4, bool
 // from columns 0-3, odd from 4-7), so the rest of the pass is unchanged;
 // virtual pixel (row, col) is the real pixel (2 row + col / 4, 4 ti + col mod 4).
 // tw2k: W2048^j (j < 64 used).
-template <bool Y2K>
+//
+// SEL: the z-first path's planes instead of z-slices.  A field holds nz = ns
+// planes (any count), plane s being bin (kb + s) mod (zmask + 1) of the z
+// transform, already x-transformed; each pixel's two bins are planes
+// sb = (b0 - kb) mod (zmask + 1) and sb + 1, so a step selects instead of
+// accumulating: A0 = Y(sb), A1 = Y(sb + 1) (twz unused).
+template <bool Y2K, bool SEL>
 __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUtensorMap tmap, int nx,
                                                    int nz, int nf, int ntiles, int L, int T,
                                                    const Geo<float>* __restrict__ geo,
@@ -1629,7 +1895,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
                                                    const float2* __restrict__ tw2k,
                                                    const unsigned short* __restrict__ b0idx,
                                                    float4* __restrict__ part, int* __restrict__ err,
-                                                   unsigned poll) {
+                                                   unsigned poll, int kb, int zmask) {
   using C = float2;
   constexpr int TX = 8, TILE = 1024 * TX, STR = 33 * TX;
   constexpr int GRP = Y2K ? 4 : 2, LGRP = Y2K ? 2 : 1;  // blocks reading one line in lockstep
@@ -1660,11 +1926,23 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     fence_proxy_async();
   }
   for (int i = t; i < 1024; i += 512) tw4[i] = tw4_g[i];
-  for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
+  if constexpr (!SEL)
+    for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
   __syncthreads();
+  // step st -> (work item, slice or plane z)
+  auto split = [&](int st, int& item, int& z) {
+    if constexpr (SEL) {
+      item = st / nz;
+      z = st - item * nz;
+    } else {
+      item = st >> lognz;
+      z = st & (nz - 1);
+    }
+  };
   auto issue = [&](int st, int b) {
-    const int item = st >> lognz;
-    const int z = st & (nz - 1), f = item >> loghalf, ti = GRP * (item & (half - 1)) + mem;
+    int item, z;
+    split(st, item, z);
+    const int f = item >> loghalf, ti = GRP * (item & (half - 1)) + mem;
     mbar_expect_tx(&bar[b], TILE * sizeof(C));
     if constexpr (Y2K) {  // 4 columns (8 floats) x 2048 rows
 #pragma unroll
@@ -1683,15 +1961,16 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   int i = 0;
   for (int st = s0; st < s1; ++st, ++i) {
     const int b = i & 1;
-    const int item = st >> lognz;
-    const int z = st & (nz - 1);
+    int item, z;
+    split(st, item, z);
     const int ti = GRP * (item & (half - 1)) + mem;
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
       __syncthreads();  // the previous step's reads of the bins are done
       for (int e = t; e < TILE; e += 512) {
         const size_t pixel = Y2K ? (size_t)(2 * (e >> 3) + ((e & 7) >> 2)) * nx + ti * 4 + (e & 3)
                                  : (size_t)(e >> 3) * nx + ti * TX + (e & 7);
-        btab[e] = b0idx[pixel];
+        const int bin = b0idx[pixel];
+        btab[e] = (unsigned short)(SEL ? (bin - kb) & zmask : bin);
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
@@ -1750,7 +2029,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     }
     __syncthreads();  // halves swapped; every stage-2 read of tr is done
     {
-      const C wz = twz[z];
+      const C wz = SEL ? make_float2(1.f, 0.f) : twz[z];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const C mine = v[out_pos<16>(k)];
@@ -1758,9 +2037,14 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         const C y = hw ? csub(other, mine) : cadd(mine, other);  // X[k2 + 32 (16 hw + k)]
         const int row = q + 512 * hw + 32 * k;
         const int b0 = btab[row * TX + col];
-        const C qq = cmul(y, twz[(b0 * z) & (nz - 1)]);
-        acc0[k] = cadd(acc0[k], qq);
-        acc1[k] = cadd(acc1[k], cmul(qq, wz));
+        if constexpr (SEL) {
+          if (b0 == z) acc0[k] = y;
+          if (b0 + 1 == z) acc1[k] = y;
+        } else {
+          const C qq = cmul(y, twz[(b0 * z) & (nz - 1)]);
+          acc0[k] = cadd(acc0[k], qq);
+          acc1[k] = cadd(acc1[k], cmul(qq, wz));
+        }
       }
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
         // slot: this segment's place among the item's segments (0 if it
@@ -1795,7 +2079,9 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
 //           registers, which leaves it the 16 pixels k2 + 32 k1 (no swap);
 // then the two q_z bins of those pixels are accumulated across z as in
 // k_yz_tma.  The consumed input buffer is refilled (slice + 2) right after
-// stage 1.  Waits are bounded as in k_col_fft4s_tma.
+// stage 1.  Waits are bounded as in k_col_fft4s_tma.  SEL: the z-first
+// path's planes, as in k_yz_tma.
+template <bool SEL>
 __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CUtensorMap tmap,
                                                       int nx, int nz, int nf, int ntiles, int L,
                                                       int T, const Geo<float>* __restrict__ geo,
@@ -1803,7 +2089,8 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
                                                       const float2* __restrict__ twy_g,
                                                       const unsigned short* __restrict__ b0idx,
                                                       float4* __restrict__ part,
-                                                      int* __restrict__ err, unsigned poll) {
+                                                      int* __restrict__ err, unsigned poll,
+                                                      int kb, int zmask) {
   using C = float2;
   constexpr int TX = 16, NY = 512, TILE = NY * TX, STR = 33 * 8;
   constexpr unsigned kPoll = 1u << 22;
@@ -1827,11 +2114,23 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
     fence_proxy_async();
   }
   for (int i = t; i < NY; i += 512) twy[i] = twy_g[i];
-  for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
+  if constexpr (!SEL)
+    for (int i = t; i < nz; i += 512) twz[i] = twz_g[i];
   __syncthreads();
+  // step st -> (work item, slice or plane z)
+  auto split = [&](int st, int& item, int& z) {
+    if constexpr (SEL) {
+      item = st / nz;
+      z = st - item * nz;
+    } else {
+      item = st >> lognz;
+      z = st & (nz - 1);
+    }
+  };
   auto issue = [&](int st, int b) {
-    const int item = st >> lognz;
-    const int z = st & (nz - 1), f = item / ntiles, ti = item - f * ntiles;
+    int item, z;
+    split(st, item, z);
+    const int f = item / ntiles, ti = item - f * ntiles;
     mbar_expect_tx(&bar[b], TILE * sizeof(C));
 #pragma unroll
     for (int k = 0; k < 2; ++k)
@@ -1845,13 +2144,14 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
   int i = 0;
   for (int st = s0; st < s1; ++st, ++i) {
     const int b = i & 1;
-    const int item = st >> lognz;
-    const int z = st & (nz - 1);
+    int item, z;
+    split(st, item, z);
     const int ti = item % ntiles;
     if (z == 0 || st == s0) {  // a new segment: this tile's bins, zero accumulators
       __syncthreads();  // the previous step's reads of the bins are done
       for (int e = t; e < TILE; e += 512) {
-        btab[e] = b0idx[(size_t)(e >> 4) * nx + ti * TX + (e & 15)];
+        const int bin = b0idx[(size_t)(e >> 4) * nx + ti * TX + (e & 15)];
+        btab[e] = (unsigned short)(SEL ? (bin - kb) & zmask : bin);
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
@@ -1895,14 +2195,19 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
         v[n1] = cmul(make_float2(fmaf(sg, o.x, e.x), fmaf(sg, o.y, e.y)), twy[n1 * k2]);
       }
       dft_reg<16>(v);
-      const C wz = twz[z];
+      const C wz = SEL ? make_float2(1.f, 0.f) : twz[z];
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) {
         const int row = k2 + 32 * k1;
         const int b0 = btab[row * TX + col];
-        const C qq = cmul(v[out_pos<16>(k1)], twz[(b0 * z) & (nz - 1)]);
-        acc0[k1] = cadd(acc0[k1], qq);
-        acc1[k1] = cadd(acc1[k1], cmul(qq, wz));
+        if constexpr (SEL) {
+          if (b0 == z) acc0[k1] = v[out_pos<16>(k1)];
+          if (b0 + 1 == z) acc1[k1] = v[out_pos<16>(k1)];
+        } else {
+          const C qq = cmul(v[out_pos<16>(k1)], twz[(b0 * z) & (nz - 1)]);
+          acc0[k1] = cadd(acc0[k1], qq);
+          acc1[k1] = cadd(acc1[k1], cmul(qq, wz));
+        }
       }
       if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
         // slot: this segment's place among the item's segments (0 if it
@@ -2702,6 +3007,81 @@ cudaError_t launch_pol_fft4s_tma_multi(const void* M, int nx, int ny, int nz,
   return cudaErrorInvalidValue;
 }
 
+template <int R>
+static cudaError_t pol_zfft_impl(const void* tmap, int nx, int ny, const PolParams<float>& pp,
+                                 const XAngles& ang, void* out, long long kstride,
+                                 long long fstride, int kb, int ns, const void* twz, int* err,
+                                 int n_sm, unsigned poll, cudaStream_t s) {
+  // as the multi-angle x pass: 3 stages (one component of a 1024-voxel
+  // tile each), 6 row buffers, 8 polarisation warps, three transform groups
+  // and a producer: one 576-thread block per SM, ~213 KB of shared memory
+  // for nz = 128
+  constexpr int S = 3, NPB = 6, PW = 8, FG = 3;
+  using Lay = ZfLayout<R>;
+  if (n_sm <= 0 || ang.n < 1 || ang.n > kMaxXAngles || nx % Lay::XW || ns < 1 || ns > Lay::NZ ||
+      kb < 0 || kb >= Lay::NZ)
+    return cudaErrorInvalidValue;
+  const long long npix = (long long)nx * ny, ntiles = npix / Lay::XW;
+  if (ntiles <= 0) return cudaSuccess;
+  const size_t smem = (size_t)S * 1024 * sizeof(float4) +
+                      ((size_t)NPB * 3 * Lay::FS + 32 * R) * sizeof(float2) + 2 * S * 8 + 16;
+  auto kern = k_pol_zfft_multi<R, S, NPB, PW, FG, kMaxXAngles>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  const long long grid = ntiles < (long long)n_sm ? ntiles : (long long)n_sm;
+  kern<<<(unsigned)grid, 32 * (PW + 3 * FG + 1), smem, s>>>(
+      *(const CUtensorMap*)tmap, nx, npix, ntiles, pp, ang, (float2*)out, kstride, fstride, kb, ns,
+      (const float2*)twz, err, poll);
+  return cudaGetLastError();
+}
+
+bool zfirst_fusable(int nx, int ny, int nz) {
+  return (nz == 32 || nz == 64 || nz == 128) && (nx == 512 || nx == 1024 || nx == 2048) &&
+         (ny == 512 || ny == 1024 || ny == 2048);
+}
+
+cudaError_t launch_pol_zfft_multi(const void* tmap, int nx, int ny, int nz,
+                                  const PolParams<float>& pp, const XAngles& ang, void* out,
+                                  long long kstride, long long fstride, int kb, int ns,
+                                  const void* twz, int* err, int n_sm, unsigned poll,
+                                  cudaStream_t s) {
+  if (!zfirst_fusable(nx, ny, nz)) return cudaErrorInvalidValue;
+  if (nz == 128)
+    return pol_zfft_impl<4>(tmap, nx, ny, pp, ang, out, kstride, fstride, kb, ns, twz, err, n_sm,
+                            poll, s);
+  if (nz == 64)
+    return pol_zfft_impl<2>(tmap, nx, ny, pp, ang, out, kstride, fstride, kb, ns, twz, err, n_sm,
+                            poll, s);
+  return pol_zfft_impl<1>(tmap, nx, ny, pp, ang, out, kstride, fstride, kb, ns, twz, err, n_sm,
+                          poll, s);
+}
+
+template <int NX, int W>
+static cudaError_t xfft_rows_impl(void* data, long long nrows, const void* tw, cudaStream_t s) {
+  constexpr int FS = NX == 2048 ? 2 * 1056 : (NX / 32) * 33;
+  constexpr int NTW = NX == 2048 ? 2048 : NX == 1024 ? 1024 : 512;
+  const size_t smem = ((size_t)NTW + (size_t)W * FS) * sizeof(float2);
+  auto kern = k_xfft_rows<NX, W>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid1(nrows, W), 32 * W, smem, s>>>((float2*)data, nrows, (const float2*)tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xfft_rows(void* data, int nx, long long nrows, const void* tw, cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  if (!tw || ((uintptr_t)data & 7)) return cudaErrorInvalidValue;
+  // 8 warps (2 blocks per SM) for 512- and 1024-point rows; 2048-point rows
+  // stage 17 KB per warp: 4 warps (2 blocks per SM)
+  if (nx == 1024) return xfft_rows_impl<1024, 8>(data, nrows, tw, s);
+  if (nx == 2048) return xfft_rows_impl<2048, 4>(data, nrows, tw, s);
+  if (nx == 512) return xfft_rows_impl<512, 8>(data, nrows, tw, s);
+  return cudaErrorInvalidValue;
+}
+
 bool yz_fusable(int nx, int ny, int nz) {
   // 2048 rows: from 4 slices up (a work item re-reads its bin indices from
   // the per-pixel geometry, 4x the bytes of one slice of its tile, which the
@@ -2711,11 +3091,20 @@ bool yz_fusable(int nx, int ny, int nz) {
          nz >= (ny == 2048 ? 4 : 1) && nz <= 1024 && (nz & (nz - 1)) == 0;
 }
 
+// sel.nzfull > 0: the z-first path's planes (nz = their count per field).
+static bool yz_sel_ok(int nx, int nz, const YzSel& sel) {
+  return nx >= 16 && (nx & (nx - 1)) == 0 && nz >= 1 && nz <= sel.nzfull && sel.nzfull <= 1024 &&
+         (sel.nzfull & (sel.nzfull - 1)) == 0 && sel.kb >= 0 && sel.kb < sel.nzfull;
+}
+
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
                              const void* twz, const void* twy, const unsigned short* b0idx,
                              void* part, int* err, int n_sm, unsigned poll, long long* L_out,
-                             cudaStream_t s) {
-  if (!yz_fusable(nx, 512, nz) || n_sm <= 0 || (nf != 3 && nf != 5)) return cudaErrorInvalidValue;
+                             cudaStream_t s, YzSel sel) {
+  const bool is_sel = sel.nzfull > 0;
+  if (!(is_sel ? yz_sel_ok(nx, nz, sel) : yz_fusable(nx, 512, nz)) || n_sm <= 0 ||
+      (nf != 3 && nf != 5))
+    return cudaErrorInvalidValue;
   const long long ntiles = nx / 16, items = nf * ntiles, T = items * nz;
   // equal step ranges over as many blocks as SMs, but at least nz / 3 steps
   // each, so an item meets at most kYzSlots blocks
@@ -2725,21 +3114,23 @@ cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo
   *L_out = L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 512 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_yz512_tma, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  auto kern = is_sel ? k_yz512_tma<true> : k_yz512_tma<false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_yz512_tma<<<(unsigned)grid, 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles,
-                                                (int)L, (int)T, geo, (const float2*)twz,
-                                                (const float2*)twy, b0idx, (float4*)part, err,
-                                                poll);
+  kern<<<(unsigned)grid, 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf, (int)ntiles, (int)L,
+                                         (int)T, geo, (const float2*)twz, (const float2*)twy, b0idx,
+                                         (float4*)part, err, poll, sel.kb, sel.nzfull - 1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, const void* tw2k,
                           const unsigned short* b0idx, void* part, int* err, int n_sm,
-                          unsigned poll, long long* L_out, cudaStream_t s) {
-  if (!yz_fusable(nx, ny, nz) || ny == 512 || n_sm <= 0) return cudaErrorInvalidValue;
+                          unsigned poll, long long* L_out, cudaStream_t s, YzSel sel) {
+  const bool is_sel = sel.nzfull > 0;
+  if (!(is_sel ? yz_sel_ok(nx, nz, sel) && (ny == 1024 || ny == 2048) : yz_fusable(nx, ny, nz)) ||
+      ny == 512 || n_sm <= 0)
+    return cudaErrorInvalidValue;
   if (nf != 3 && nf != 5) return cudaErrorInvalidValue;
   // 1024 rows: pairs of 8-column tiles; 2048 rows: quads of 4-column tiles
   const bool y2k = ny == 2048;
@@ -2756,14 +3147,15 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, cons
   *L_out = L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 1024 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;
-  auto kern = y2k ? k_yz_tma<true> : k_yz_tma<false>;
+  auto kern = y2k ? (is_sel ? k_yz_tma<true, true> : k_yz_tma<true, false>)
+                  : (is_sel ? k_yz_tma<false, true> : k_yz_tma<false, false>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<(unsigned)(grp * groups), 512, smem, s>>>(*(const CUtensorMap*)tmap, nx, nz, nf,
                                                     (int)ntiles, (int)L, (int)T, geo,
                                                     (const float2*)twz, (const float2*)tw4,
                                                     (const float2*)tw2k, b0idx, (float4*)part,
-                                                    err, poll);
+                                                    err, poll, sel.kb, sel.nzfull - 1);
   return cudaGetLastError();
 }
 

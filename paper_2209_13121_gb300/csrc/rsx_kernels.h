@@ -186,6 +186,24 @@ cudaError_t launch_pol_fft4s_tma_multi(const void* M, int nx, int ny, int nz,
                                        const PolParams<float>& pp, const XAngles& ang, void* p,
                                        long long pstride, const void* tw, int* err, int n_sm,
                                        unsigned poll, cudaStream_t s);
+// The z-first Algorithm 1 pass (FP32): p for ang.n angles per read of the
+// morphology, each pixel's z column transformed, and only the ns bins
+// kb .. kb + ns - 1 (mod nz) kept: angle k's plane s of field f goes to
+// out + k * kstride + f * fstride + s * nx * ny as an [ny][nx] complex plane
+// (not yet x- or y-transformed).  tmap: a CUtensorMap over the morphology
+// viewed as [c nz][ny][4 nx] floats with (128 / nz) x 1 x nz boxes (see
+// make_tmap_m); twz: exp(-2 pi i j / nz), j < nz.  zfirst_fusable says
+// whether the shape qualifies (nz = 32, 64 or 128; nx and ny = 512, 1024 or
+// 2048).  One persistent CTA per SM (n_sm).
+bool zfirst_fusable(int nx, int ny, int nz);
+cudaError_t launch_pol_zfft_multi(const void* tmap, int nx, int ny, int nz,
+                                  const PolParams<float>& pp, const XAngles& ang, void* out,
+                                  long long kstride, long long fstride, int kb, int ns,
+                                  const void* twz, int* err, int n_sm, unsigned poll,
+                                  cudaStream_t s);
+// In-place x-FFT of nrows contiguous rows of nx = 512, 1024 or 2048 complex
+// (FP32; tw: twx for 512, tw4 for 1024, the 2048-point table for 2048).
+cudaError_t launch_xfft_rows(void* data, int nx, long long nrows, const void* tw, cudaStream_t s);
 // The same pipeline for Algorithm 2: p = N_t e from the five stored entries
 // of N_t ([5][N] complex float, 16-byte aligned; the reference constant
 // left out as k_nt_all stores it).
@@ -205,16 +223,23 @@ bool yz_fusable(int nx, int ny, int nz);
 // this many blocks (their step ranges hold at least nz / (kYzSlots - 1)).
 constexpr int kYzSlots = 4;
 // b0idx: each pixel's lower q_z bin (launch_geometry's packed output).
+// sel: the z-first path's planes instead of z-slices when nzfull > 0: nz is
+// then the plane count per field (any value up to nzfull), plane s holds bin
+// (kb + s) mod nzfull, and each pixel takes its two bins from planes
+// (b0 - kb) mod nzfull and the one after.
+struct YzSel {
+  int kb = 0, nzfull = 0;
+};
 cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, const Geo<float>* geo,
                           const void* twz, const void* tw4, const void* tw2k,
                           const unsigned short* b0idx, void* part, int* err, int n_sm,
-                          unsigned poll, long long* L_out, cudaStream_t s);
+                          unsigned poll, long long* L_out, cudaStream_t s, YzSel sel = YzSel());
 // The same for ny = 512 (16-column tiles, tensor map boxes of 32 floats x
 // 256 rows; twy the 512-point twiddle table).
 cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo<float>* geo,
                              const void* twz, const void* twy, const unsigned short* b0idx,
                              void* part, int* err, int n_sm, unsigned poll, long long* L_out,
-                             cudaStream_t s);
+                             cudaStream_t s, YzSel sel = YzSel());
 // The linearity path's per-energy bins (k_zbins5 layout) from launch_yz_tma
 // run over the five FFT'd N_t entries (nf = 5); dc = -(c-1)/(4 pi) N.
 cudaError_t launch_bins5_from_part(const void* part, int nx, int ny, int nz, long long L,

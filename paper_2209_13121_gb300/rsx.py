@@ -32,12 +32,12 @@ EXPORTED = (
     "rsx_set_morphology", "rsx_set_optical_constants", "rsx_run", "rsx_polarization",
     "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
     "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc", "rsx_nt",
-    "rsx_set_wait_limit", "rsx_check", "rsx_angle_batch",
+    "rsx_set_wait_limit", "rsx_check", "rsx_angle_batch", "rsx_zfirst_plan",
 )
 MAX_ANGLE_BATCH = 8
 NOALLOC_MAX_VOXELS = 1 << 20
 NOALLOC_MAX_PIXELS = 1 << 16
-PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other", "nt")
+PHASES = ("pol_fftx", "ffty", "ewald", "rotate", "other", "nt", "fftx")
 
 
 class RsxConfig(ctypes.Structure):
@@ -87,6 +87,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "rsx_nt": (ci, [vp, ci, vp, vp]),
         "rsx_check": (ci, [vp, vp]),
         "rsx_angle_batch": (ci, [vp]),
+        "rsx_zfirst_plan": (ci, [vp, ci, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -178,6 +179,14 @@ class Context:
     def angle_batch(self):
         """e-field angles per read of the morphology in rsx_run (Algorithm 1)."""
         return lib().rsx_angle_batch(self._h)
+
+    def zfirst_plan(self, energy_index):
+        """(n_planes, first_bin, angles_per_pass) of the z-first path for this
+        energy (rsx_zfirst_plan); n_planes = 0 when the path does not serve it."""
+        ns, kb, kz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().rsx_zfirst_plan(self._h, int(energy_index), ctypes.byref(ns),
+                                     ctypes.byref(kb), ctypes.byref(kz)))
+        return ns.value, kb.value, kz.value
 
     @property
     def shape(self):

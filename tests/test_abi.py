@@ -65,10 +65,15 @@ def test_workspace_bytes_follows_table1(lib):
             b + (k - 1) * 3 * N * 8
     # the default batch, and no batch where the multi-angle pass does not apply
     assert rsx.workspace_bytes(rsx.make_config(nx, ny, nz, c, 5.0)) == b + 7 * 3 * N * 8
-    # nx = 2048 takes at most 3; other row lengths none
+    # nx = 2048 takes at most 3 on the multi-angle x pass (nz = 16), up to 8
+    # where the z-first path serves the shape (nz = 32, 64, 128); other row
+    # lengths none
+    one = rsx.make_config(2048, 2048, 16, c, 5.0, angle_batch=1)
+    assert rsx.workspace_bytes(rsx.make_config(2048, 2048, 16, c, 5.0, angle_batch=4)) == \
+        rsx.workspace_bytes(one) + 2 * 3 * 2048 * 2048 * 16 * 8
     one = rsx.make_config(2048, 2048, 64, c, 5.0, angle_batch=1)
     assert rsx.workspace_bytes(rsx.make_config(2048, 2048, 64, c, 5.0, angle_batch=4)) == \
-        rsx.workspace_bytes(one) + 2 * 3 * 2048 * 2048 * 64 * 8
+        rsx.workspace_bytes(one) + 3 * 3 * 2048 * 2048 * 64 * 8
     one = rsx.make_config(1000, 1024, 100, c, 5.0, angle_batch=1)
     assert rsx.workspace_bytes(rsx.make_config(1000, 1024, 100, c, 5.0, angle_batch=4)) == \
         rsx.workspace_bytes(one)

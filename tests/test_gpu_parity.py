@@ -710,8 +710,9 @@ def test_full_size_sampled_pixels_match_oracle(rsx, algorithm):
 
 def test_full_size_run_sampled_pixels_match_oracle(rsx):
     """rsx_run at the benchmark's size and launch configuration (1024 x
-    1024 x 128, c = 4, FP32, device output: the multi-angle x pass with its
-    default batch, the fused y+z pass, the Ewald image, the rotation into
+    1024 x 128, c = 4, FP32, device output: the z-first path with its
+    default batch (polarisation + z-FFT, x-FFT of the kept planes, the
+    y-FFT selecting each pixel's bins), the Ewald image, the rotation into
     the average), ten angles (a full batch and a partial one), against the
     oracle's average at sampled output pixels (each angle's unrotated image
     at the corners the rotation reads, exact by linearity of the DFT)."""
@@ -756,8 +757,9 @@ def test_full_size_run_sampled_pixels_match_oracle(rsx):
 def test_run_2048_grids_sampled_pixels_match_oracle(rsx, shape, c, prec):
     """rsx_run on the 2048-wide grids of Sec. 5.1 (the 2-D film) and Sec. 6.2
     (2048 x 2048 x 64, c = 4): FP32 through the 2048-point multi-angle x
-    pass, FP64 through the general kernels; five angles, sampled output
-    pixels against the oracle's average (exact by linearity of the DFT)."""
+    pass (the film) or the z-first path (64 slices), FP64 through the
+    general kernels; five angles, sampled output pixels against the
+    oracle's average (exact by linearity of the DFT)."""
     nz, ny, nx = shape
     E = 280.0
     angles = (0.0, 40.0, 160.0)
@@ -768,7 +770,9 @@ def test_run_2048_grids_sampled_pixels_match_oracle(rsx, shape, c, prec):
     oy = np.concatenate([[ny // 2, 7, ny - 3], g.integers(0, ny, 40)])
     ox = np.concatenate([[nx // 2, nx - 1, 11], g.integers(0, nx, 40)])
     with rsx.Context(nx, ny, nz, c, VOXEL, precision=prec) as ctx:
-        assert ctx.angle_batch == (3 if prec == 32 else 1)
+        # FP32: 3 angles per multi-angle pass (the film); p buffers within
+        # 32 GiB for the z-first path (5 of 6.4 GB at 64 slices)
+        assert ctx.angle_batch == (1 if prec == 64 else 3 if nz == 1 else 5)
         ctx.set_morphology(dev)
         ctx.set_optical_constants([E], K)
         out = torch.empty((1, ny, nx), dtype=_tdtype(prec), device="cuda")
