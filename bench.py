@@ -57,6 +57,14 @@ WORKLOADS = {
                         energies=(150, 270.0, 320.0)),
     "p1-1024-z16": dict(shape=(16, 1024, 1024), c=4, angles=(0.0, 2.0, 180.0),
                         energies=(150, 270.0, 320.0)),
+    # P1's stack depth (128 slices) on smaller lateral grids, for captures of
+    # the z-first kernels at their P1 instantiation in a few GB: the
+    # polarisation + z-FFT pass (any lateral size) and the 1024-row
+    # selection pass
+    "p1-512-z128": dict(shape=(128, 512, 512), c=4, angles=(0.0, 2.0, 180.0),
+                        energies=(150, 270.0, 320.0)),
+    "p1-1024x512-z128": dict(shape=(128, 1024, 512), c=2, angles=(0.0, 2.0, 180.0),
+                             energies=(150, 270.0, 320.0)),
     # Sec. 5.2.2 grating geometry (E5): 1 nm voxels, 17 keV, the e-field at 0
     # only (no rotation), FP64 in the paper's comparison (--precision 64)
     "p5-1024x63": dict(shape=(63, 1024, 1024), c=2, angles=(0.0, 1.0, 0.0),

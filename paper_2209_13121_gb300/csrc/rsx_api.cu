@@ -1151,7 +1151,7 @@ int run_energy_angles_batched(rsx_context* c, int ie, double start, double inc, 
     rsx::XAngles ang;
     memset(&ang, 0, sizeof(ang));
     ang.n = nk;
-    double alpha[RSX_MAX_ANGLE_BATCH];
+    double alpha[rsx::kMaxXAngles];
     for (int k = 0; k < nk; ++k) {
       alpha[k] = rotation ? (start + inc * (a0 + k)) * (kPi / 180.0) : 0.0;
       ang.ce[k] = (float)cos(alpha[k]);
@@ -1222,7 +1222,7 @@ int run_energy_zfirst(rsx_context* c, int ie, double start, double inc, int nang
     rsx::XAngles ang;
     memset(&ang, 0, sizeof(ang));
     ang.n = nk;
-    double alpha[RSX_MAX_ANGLE_BATCH];
+    double alpha[rsx::kMaxXAngles];
     for (int k = 0; k < nk; ++k) {
       alpha[k] = rotation ? (start + inc * (a0 + k)) * (kPi / 180.0) : 0.0;
       ang.ce[k] = (float)cos(alpha[k]);

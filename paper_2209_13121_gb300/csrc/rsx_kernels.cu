@@ -963,59 +963,71 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
 // every pixel's z column and stores planes s < ns (bin kb + s mod nz) of
 // angle k at out + k * kstride + f * fstride + s * nx * ny (+ y nx + x).
 //
-// Row buffers hold a field as XW lines of LS complex (line px, sample z at
-// px * LS + z).  A transform warp takes one field of one buffer:
-//   nz = 32 R, n = n1 + R n2, k = k2 + 32 k1, lane = n1 XW + px:
-//   stage 1: the 32-point DFT over n2 of samples n1 + R n2 of line px,
-//            times W_nz^(n1 k2), written back as Y[n1][k2] (pitch P2);
-//   stage 2: lane (px, n1) takes k2 = n1 + R m: the R-point DFT over n1
-//            gives X[k2 + 32 k1], written back to px * LS + k;
+// Row buffers hold a field as XW lines of LS complex; sample z of line px
+// sits at px * LS + zf_pos(z >> 5, z & 31).  A transform warp takes one
+// field of one buffer, decimation in frequency with nz = 32 R,
+// n = n2 + 32 n1, k = R k2 + k1 (n2, k2 < 32; n1, k1 < R):
+//   X[R k2 + k1] = sum_n2 W32^(n2 k2) W_nz^(n2 k1) sum_n1 x[n2 + 32 n1] W_R^(n1 k1);
+//   stage 1: lane (px, r) takes n2 = r + R m: the R-point DFT over n1 of
+//            x[n2 + 32 n1] gives u[k1][n2], stored in place at zf_pos(k1, n2)
+//            (the R positions a lane reads are the R it writes);
+//   stage 2: lane (px, k1) loads u[k1][0..32) times W_nz^(n2 k1) (each
+//            twiddle used as it is read), does the 32-point DFT and stores
+//            X[R k2 + k1] over the same 32 positions, zf_pos(k1, k2);
 // then the warp copies the ns kept bins of its XW lines out (XW adjacent
-// pixels per plane row).  LS and P2 keep the polarisation stores, both
-// stages and the copy free of shared-memory bank conflicts (checked per
-// half-warp for R = 1, 2, 4).
+// pixels per plane row).  zf_pos(a, b) = 32 a + b, for R = 4 with b xor a
+// (the low bits swizzled by a); with LS = 130 (R = 4) or nz + 1 that keeps
+// the polarisation stores, both stages and the copy free of shared-memory
+// bank conflicts (checked per half-warp for R = 1, 2, 4).
 template <int R> struct ZfLayout {
   static constexpr int NZ = 32 * R, XW = 32 / R, LXW = R == 1 ? 5 : R == 2 ? 4 : 3;
-  static constexpr int LS = R == 4 ? 146 : NZ + 1, P2 = R == 4 ? 33 : 32, FS = XW * LS;
+  static constexpr int LS = R == 4 ? 130 : NZ + 1, FS = XW * LS;
 };
+template <int R> __device__ __forceinline__ int zf_pos(int a, int b) {
+  return 32 * a + (R == 4 ? (b ^ a) : b);
+}
 
 template <int R>
 __device__ __forceinline__ void zfft_lines(float2* F, const float2* twt, int lane) {
   using C = float2;
   using Lay = ZfLayout<R>;
-  constexpr int XW = Lay::XW, LS = Lay::LS, P2 = Lay::P2;
-  const int px = lane & (XW - 1), n1 = lane >> Lay::LXW;
+  constexpr int XW = Lay::XW, LS = Lay::LS;
+  const int px = lane & (XW - 1), r = lane >> Lay::LXW;  // r < R
   C* Ln = F + px * LS;
-  C v[32];
+  // zf_pos(a, b) for b = 4 j + c is base[c] + 4 j with base[c] = 32 a +
+  // (c xor a): four base addresses per lane and immediate offsets
+  if constexpr (R > 1) {
+    C* b1[R];  // stage 1: a = n1, c = r (n2 = r + R m)
 #pragma unroll
-  for (int n2 = 0; n2 < 32; ++n2) v[n2] = Ln[n1 + R * n2];
-  dft32(v);
-  if constexpr (R == 1) {  // the lane's own line: X[k] = v[k]
-#pragma unroll
-    for (int k = 0; k < 32; ++k) Ln[k] = v[k];
-  } else {
-#pragma unroll
-    for (int k2 = 1; k2 < 32; ++k2) v[k2] = cmul(v[k2], twt[k2 * R + n1]);
-    __syncwarp();
-#pragma unroll
-    for (int k2 = 0; k2 < 32; ++k2) Ln[n1 * P2 + k2] = v[k2];
-    __syncwarp();
-    C y[32];  // [m][n1'] for k2 = n1 + R m
-#pragma unroll
-    for (int m = 0; m < 32 / R; ++m)
-#pragma unroll
-      for (int q = 0; q < R; ++q) y[m * R + q] = Ln[q * P2 + n1 + R * m];
-    __syncwarp();
+    for (int n1 = 0; n1 < R; ++n1) b1[n1] = Ln + zf_pos<R>(n1, r);
 #pragma unroll
     for (int m = 0; m < 32 / R; ++m) {
-      if constexpr (R == 4)
-        dft4(y[4 * m], y[4 * m + 1], y[4 * m + 2], y[4 * m + 3]);
-      else
-        dft2(y[2 * m], y[2 * m + 1]);
+      C u[R];
 #pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) Ln[n1 + R * m + 32 * k1] = y[m * R + k1];
+      for (int n1 = 0; n1 < R; ++n1) u[n1] = b1[n1][R * m];
+      if constexpr (R == 4)
+        dft4(u[0], u[1], u[2], u[3]);
+      else
+        dft2(u[0], u[1]);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) b1[k1][R * m] = u[k1];
     }
+    __syncwarp();
   }
+  // stage 2: a = k1 = r, b = n2 (or k2)
+  C* b2[R];
+#pragma unroll
+  for (int c = 0; c < R; ++c) b2[c] = Ln + zf_pos<R>(r, c);
+  const C* tw = twt + r;
+  C v[32];
+#pragma unroll
+  for (int n2 = 0; n2 < 32; ++n2) {
+    const C a = b2[n2 % R][n2 - n2 % R];
+    v[n2] = (R > 1 && n2 > 0) ? cmul(a, tw[n2 * R]) : a;
+  }
+  dft32(v);
+#pragma unroll
+  for (int k2 = 0; k2 < 32; ++k2) b2[k2 % R][k2 - k2 % R] = v[k2];
   __syncwarp();
 }
 
@@ -1036,7 +1048,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
   extern __shared__ __align__(128) unsigned char smem_a128[];
   float4* stage = reinterpret_cast<float4*>(smem_a128);  // [S][NZ][XW] voxels
   C* P = reinterpret_cast<C*>(stage + S * SV);            // [NPB][3][FS]
-  C* twt = P + NPB * 3 * FS;                              // [32][R]: W_nz^(n1 k2)
+  C* twt = P + NPB * 3 * FS;                              // [32][R]: W_nz^(n2 k1)
   unsigned long long* full = reinterpret_cast<unsigned long long*>(twt + 32 * R);
   unsigned long long* empty = full + S;
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
@@ -1137,8 +1149,8 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
           const float ce = ang_ce[k], se = ang_se[k];
 #pragma unroll
           for (int sl = 0; sl < SL; ++sl) {
-            const int e = pt + sl * TP;  // voxel (z, px) of the tile
-            const int at = (e & (XW - 1)) * LS + (e >> LXW);
+            const int e = pt + sl * TP, z = e >> LXW;  // voxel (z, px) of the tile
+            const int at = (e & (XW - 1)) * LS + zf_pos<R>(z >> 5, z & 31);
             C o3[3];
             p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, o3);
             Pi[at] = o3[0];
@@ -1167,8 +1179,8 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
       zfft_lines<R>(F, twt, lane);
       C* o = out + (size_t)k * kstride + (size_t)f * fstride + (size_t)y * nx + x0;
       for (int idx = lane; idx < cnt; idx += 32) {
-        const int s = idx >> LXW, px = idx & (XW - 1);
-        o[(size_t)s * npix + px] = F[px * LS + ((kb + s) & (NZ - 1))];
+        const int s = idx >> LXW, px = idx & (XW - 1), kz = (kb + s) & (NZ - 1);
+        o[(size_t)s * npix + px] = F[px * LS + zf_pos<R>(kz & (R - 1), kz / R)];
       }
       __syncwarp();
     }
@@ -2975,14 +2987,14 @@ static cudaError_t pol_fft4s_tma_multi_impl(const void* M, int ny, int nz,
   constexpr int S = 3, NPB = NX == 2048 ? 3 : 6, PW = 8, FG = 3;
   constexpr int FS = NX == 2048 ? 2 * 1056 : (NX / 32) * 33;
   constexpr int SV = NX > 1024 ? 1024 : NX, NTW = NX == 2048 ? 2048 : 1024;
-  if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > kMaxXAngles ||
+  if (n_sm <= 0 || ((uintptr_t)M & 15) || ang.n < 1 || ang.n > 8 ||
       (NX == 2048 && ang.n > NPB))
     return cudaErrorInvalidValue;
   const long long N = (long long)NX * ny * nz, nrows = (long long)ny * nz;
   if (nrows <= 0) return cudaSuccess;
   const size_t smem = (size_t)S * SV * sizeof(float4) + ((size_t)NPB * 3 * FS + NTW) * sizeof(float2) +
                       2 * S * 8 + 16;
-  auto kern = k_pol_fft4s_tma_multi<S, NPB, PW, FG, NX, kMaxXAngles>;
+  auto kern = k_pol_fft4s_tma_multi<S, NPB, PW, FG, NX, 8>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
@@ -3014,7 +3026,7 @@ static cudaError_t pol_zfft_impl(const void* tmap, int nx, int ny, const PolPara
                                  int n_sm, unsigned poll, cudaStream_t s) {
   // as the multi-angle x pass: 3 stages (one component of a 1024-voxel
   // tile each), 6 row buffers, 8 polarisation warps, three transform groups
-  // and a producer: one 576-thread block per SM, ~213 KB of shared memory
+  // and a producer: one 576-thread block per SM, ~200 KB of shared memory
   // for nz = 128
   constexpr int S = 3, NPB = 6, PW = 8, FG = 3;
   using Lay = ZfLayout<R>;

@@ -80,7 +80,7 @@ def test_plan_covers_the_bins_every_pixel_reads(rsx, shape):
             run = {(kb + s) % nz for s in range(ns)}
             assert need <= run, (E, sorted(need - run))
             assert (kb + ns - 1) % nz == 1   # the run ends at bin 1
-            assert kz == min(8, kx * nz // ns)
+            assert kz == min(16, kx * nz // ns)
     # shapes and precisions the path does not serve
     for (nz, ny, nx), prec, alg in (((16, 512, 512), 32, 1), ((32, 512, 512), 64, 1),
                                     ((32, 512, 512), 32, 2), ((32, 256, 512), 32, 1),
@@ -133,11 +133,11 @@ SAMPLED = [((64, 512, 512), 4, 0), ((128, 1024, 512), 3, 1), ((32, 512, 2048), 2
 def test_sampled_pixels_match_oracle(rsx, shape, c, frame):
     """Every kernel shape of the path: nz = 32, 64, 128 (1, 2 or 4 lanes per
     z line), x rows of 512, 1024, 2048 points, the 512-, 1024- and 2048-row
-    selection passes, both frames; nine angles (a full batch of 8 and a
+    selection passes, both frames; 18 angles (a full batch of 16 and a
     partial one) averaged with the rotation, at sampled output pixels."""
     nz, ny, nx = shape
     E = 280.0
-    angles = (0.0, 20.0, 160.0)
+    angles = (0.0, 10.0, 170.0)
     sp = synth.sparse_voxels(shape, c, 3000, seed=43)
     K = synth.optical_constants([E], c, seed=44)
     dev = synth.morphology_sparse_torch(shape, c, sp)
@@ -148,7 +148,7 @@ def test_sampled_pixels_match_oracle(rsx, shape, c, frame):
         ctx.set_morphology(dev)
         ctx.set_optical_constants([E], K)
         ns, kb, kz = ctx.zfirst_plan(0)
-        assert 0 < ns < nz and kz == 8, (ns, kz)
+        assert 0 < ns < nz and kz == 16, (ns, kz)
         out = torch.empty((1, ny, nx), device="cuda")
         ctx.run(angles, out=out)
         ctx.check()
@@ -190,7 +190,7 @@ def test_energy_beyond_the_plan_takes_the_other_path(rsx):
 def test_result_is_bitwise_independent_of_the_angle_batch(rsx):
     """Each angle's planes, transforms and image are the same arithmetic
     whatever batch it falls in: angle_batch 1 (2 angles per pass) and 8
-    (8 per pass) give identical images."""
+    (16 per pass) give identical images."""
     shape, c = (32, 512, 1024), 3
     nz, ny, nx = shape
     M = synth.morphology_random(shape, c, seed=49, dtype=np.float32)
@@ -202,9 +202,9 @@ def test_result_is_bitwise_independent_of_the_angle_batch(rsx):
         with rsx.Context(nx, ny, nz, c, VOXEL, precision=32, angle_batch=k) as ctx:
             ctx.set_morphology(dev)
             ctx.set_optical_constants(energies, K)
-            assert ctx.zfirst_plan(0)[2] == (8 if k == 8 else nz // ctx.zfirst_plan(0)[0])
+            assert ctx.zfirst_plan(0)[2] == (16 if k == 8 else nz // ctx.zfirst_plan(0)[0])
             out = torch.empty((2, ny, nx), device="cuda")
-            ctx.run((0.0, 15.0, 165.0), out=out)
+            ctx.run((0.0, 10.0, 170.0), out=out)
             ctx.check()
             outs.append(out.cpu().numpy())
     np.testing.assert_array_equal(outs[0], outs[1])
