@@ -132,7 +132,7 @@ int rsx_angle_batch(const rsx_context* ctx);
  * instead of all nz slices (the same transform values; only the rounding
  * order differs).  It serves an energy when the run holds at most 3/4 of the
  * nz bins; the angles of one morphology read are then up to
- * min(16, angle_batch * nz / n_planes).
+ * min(32, angle_batch * nz / n_planes), spread evenly over the passes.
  * For energy_index: *n_planes receives the run length (0 when the path does
  * not serve this context or energy), *first_bin its first bin (the run is
  * first_bin, ..., first_bin + n_planes - 1 mod nz), *angles_per_pass the

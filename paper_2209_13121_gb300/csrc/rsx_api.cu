@@ -691,10 +691,13 @@ static int angle_batch_of(const rsx_config* cfg) {
 
 // The z-first path's plan for one energy: the cyclic run of q_z bins its
 // pixels read and the angles per pass.  The run ends at bin 1 (q_z <= 0
-// on the sphere, so b0 <= 0); it starts one bin below the lowest b0 over
-// the pixels on the sphere (Eq. (Ewald) in double as k_geometry evaluates
-// it; the extra bin covers a rounding difference between the two), which
-// per row is reached at the largest |q_x| still on the sphere.
+// on the sphere, so b0 <= 0, b1 <= 1) and starts at the lowest b0 =
+// floor(t) over the pixels on the sphere (Eq. (Ewald) in double, as
+// k_geometry evaluates it), reached per row at the largest |q_x| still on
+// the sphere.  The device rounds in another order, so the bound is taken
+// wide enough for any such difference: a pixel within 1e-12 k^2 of the
+// sphere's edge counts as on it (at q_z = -k, its lowest possible value),
+// and a t within 1e-9 above an integer also takes the bin below.
 struct ZPlan {
   int kb = 0, ns = 0, kz = 0;
 };
@@ -702,24 +705,27 @@ struct ZPlan {
 static int lowest_bin(const rsx_config& g, double k) {
   const double two_pi = 2.0 * kPi;
   const double dqx = two_pi / (g.nx * g.voxel_nm), dqz = two_pi / (g.nz * g.voxel_nm);
+  const double edge = 1e-12 * k * k;
   const int fmax = g.nx / 2;  // largest |f_x| on the FFT grid (nx even)
   double tmin = 0.0;
   for (int my = 0; my < g.ny; ++my) {
     const int fy = my < (g.ny + 1) / 2 ? my : my - g.ny;
     const double qy = two_pi * fy / (g.ny * g.voxel_nm);
-    const double r2 = k * k - qy * qy;
+    const double r2 = k * k - qy * qy + edge;
     if (r2 < 0.0) continue;
-    double fl = floor(sqrt(r2) / dqx);
+    const double fl = floor(sqrt(r2) / dqx);
     int f = fl < (double)fmax ? (int)fl : fmax;
     while (f < fmax && (dqx * (f + 1)) * (dqx * (f + 1)) <= r2) ++f;
     while (f > 0 && (dqx * f) * (dqx * f) > r2) --f;
     const double qx = dqx * f;
     const double rad = k * k - qx * qx - qy * qy;
-    if (rad < 0.0) continue;
-    const double t = (-k + sqrt(rad)) / dqz;
+    if (rad < -edge) continue;
+    const double t = (-k + sqrt(rad > 0.0 ? rad : 0.0)) / dqz;
     if (t < tmin) tmin = t;
   }
-  return (int)floor(tmin);
+  double lo = floor(tmin);
+  if (tmin - lo < 1e-9 * (1.0 + fabs(tmin))) lo -= 1.0;
+  return (int)lo;
 }
 
 static bool zfirst_plan(const rsx_context* c, int ie, ZPlan* zp) {
@@ -729,7 +735,7 @@ static bool zfirst_plan(const rsx_context* c, int ie, ZPlan* zp) {
     return false;
   if ((g.nx == 1024 && !c->tw4) || (g.nx == 2048 && !c->tw2k) || (g.ny == 2048 && !c->twy))
     return false;
-  const int blo = lowest_bin(g, wavenumber(c->energies[ie])) - 1;
+  const int blo = lowest_bin(g, wavenumber(c->energies[ie]));
   const int ns = 2 - blo;
   // worth it while at most 3/4 of the bins are kept (the z transform costs
   // about what the dropped planes' x and y transforms save at ~0.8)
@@ -1217,8 +1223,10 @@ int run_energy_zfirst(rsx_context* c, int ie, double start, double inc, int nang
   const void* twx = g.nx == 1024 ? c->tw4 : g.nx == 2048 ? c->tw2k : c->twx;
   const unsigned box = g.ny == 512 ? 32 : g.ny == 2048 ? 8 : 16;
   const rsx::YzSel sel = {zp.kb, g.nz};
-  for (int a0 = 0; a0 < nang; a0 += zp.kz) {
-    const int nk = nang - a0 < zp.kz ? nang - a0 : zp.kz;
+  // the angles spread evenly over the fewest passes of at most kz
+  const int npass = (nang + zp.kz - 1) / zp.kz, per = (nang + npass - 1) / npass;
+  for (int a0 = 0; a0 < nang; a0 += per) {
+    const int nk = nang - a0 < per ? nang - a0 : per;
     rsx::XAngles ang;
     memset(&ang, 0, sizeof(ang));
     ang.n = nk;

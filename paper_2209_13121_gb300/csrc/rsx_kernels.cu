@@ -1031,6 +1031,28 @@ __device__ __forceinline__ void zfft_lines(float2* F, const float2* twt, int lan
   __syncwarp();
 }
 
+// Roles of the 18 warps of the z-first pass for nz = 128.  A transform warp
+// there does ~1.2x the per-tile work of a polarisation warp; over the four
+// schedulers (warp index mod 4) the split Prod T T T P | P P P P P | T T T P
+// | T T T P keeps every scheduler within ~7 % of the mean, and each
+// transform group (three consecutive indices) spans three schedulers: warps
+// 0, 2, 3, 4, 6, 7, 8, 10, 11 transform (0..8), 16 produces, 1, 5, 9, 13,
+// 17, 12, 14, 15 polarise (0..7).  (P1: x pass 72.8 -> 72.2 ms per energy;
+// nz = 64 measured 3 % slower with it and keeps multi_role.)
+__device__ __forceinline__ void zf_role(int w, int& kind, int& idx) {
+  const int q = w & 3;
+  if (w == 16) {
+    kind = 2;
+    idx = 0;
+  } else if (w < 12 && q != 1) {
+    kind = 1;
+    idx = (w >> 2) * 3 + (q == 0 ? 0 : q - 1);
+  } else {
+    kind = 0;
+    idx = q == 1 ? w >> 2 : w == 12 ? 5 : w - 8;
+  }
+}
+
 template <int R, int S, int NPB, int PW, int FG, int KMAX>
 __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
     const __grid_constant__ CUtensorMap tmap, int nx, long long npix, long long ntiles,
@@ -1054,7 +1076,10 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
   volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + S);
   const int t = threadIdx.x, w = t >> 5, lane = t & 31;
   int kind, ridx;
-  multi_role(w, kind, ridx);
+  if constexpr (R == 4)
+    zf_role(w, kind, ridx);
+  else
+    multi_role(w, kind, ridx);
   if (t == 0) {
     for (int i = 0; i < S; ++i) {
       mbar_init(&full[i], 1);
@@ -1919,6 +1944,9 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
   C* twz = tw4 + 1024;                       // [nz]
   unsigned short* btab = reinterpret_cast<unsigned short*>(twz + nz);  // [1024][TX]
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(btab + TILE);
+  // SEL: each thread's 16 plane indices as bytes, [512][16] over the unused
+  // twz (16-byte aligned), read as one 16-byte word per step
+  unsigned char* btab8 = reinterpret_cast<unsigned char*>(twz);
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   const int col = lane & 7, hw = w >> 3;
   const int q = (w & 7) * 4 + (lane >> 3);  // n1 in stage 1, k2 in stage 2
@@ -1982,7 +2010,15 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         const size_t pixel = Y2K ? (size_t)(2 * (e >> 3) + ((e & 7) >> 2)) * nx + ti * 4 + (e & 3)
                                  : (size_t)(e >> 3) * nx + ti * TX + (e & 7);
         const int bin = b0idx[pixel];
-        btab[e] = (unsigned short)(SEL ? (bin - kb) & zmask : bin);
+        if constexpr (SEL) {
+          // virtual pixel (row, col) belongs to the stage-3 thread
+          // (q, hw, col) with row = q + 512 hw + 32 k: byte k of its word
+          const int row = e >> 3, rem = row & 511, qq = rem & 31;
+          const int owner = ((row >> 9) * 8 + (qq >> 2)) * 32 + ((qq & 3) << 3) + (e & 7);
+          btab8[owner * 16 + (rem >> 5)] = (unsigned char)((bin - kb) & zmask);
+        } else {
+          btab[e] = (unsigned short)bin;
+        }
       }
 #pragma unroll
       for (int k = 0; k < 16; ++k) acc0[k] = acc1[k] = make_float2(0.f, 0.f);
@@ -2042,17 +2078,21 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     __syncthreads();  // halves swapped; every stage-2 read of tr is done
     {
       const C wz = SEL ? make_float2(1.f, 0.f) : twz[z];
+      uint4 sb4 = make_uint4(0u, 0u, 0u, 0u);
+      if constexpr (SEL) sb4 = reinterpret_cast<const uint4*>(btab8)[t];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const C mine = v[out_pos<16>(k)];
         const C other = xb[(16 * (1 - hw) + k) * 256 + q * TX + col];
         const C y = hw ? csub(other, mine) : cadd(mine, other);  // X[k2 + 32 (16 hw + k)]
         const int row = q + 512 * hw + 32 * k;
-        const int b0 = btab[row * TX + col];
         if constexpr (SEL) {
-          if (b0 == z) acc0[k] = y;
-          if (b0 + 1 == z) acc1[k] = y;
+          const unsigned wd = k < 4 ? sb4.x : k < 8 ? sb4.y : k < 12 ? sb4.z : sb4.w;
+          const int sb = (int)((wd >> (8 * (k & 3))) & 0xffu);
+          if (sb == z) acc0[k] = y;
+          if (sb + 1 == z) acc1[k] = y;
         } else {
+          const int b0 = btab[row * TX + col];
           const C qq = cmul(y, twz[(b0 * z) & (nz - 1)]);
           acc0[k] = cadd(acc0[k], qq);
           acc1[k] = cadd(acc1[k], cmul(qq, wz));

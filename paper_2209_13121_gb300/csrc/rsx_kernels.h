@@ -170,9 +170,9 @@ cudaError_t launch_col_fft4s(void* p, long long S, long long W, const ColBatches
 cudaError_t launch_pol_fft4s_tma(const void* M, int nx, int ny, int nz, const PolParams<float>& pp,
                                  void* p, const void* tw4, int* err, int n_sm, unsigned poll,
                                  cudaStream_t s);
-// Up to kMaxXAngles e-field angles for one multi-angle x pass or z-first
-// pass: cos and sin of each, n of them in use.
-constexpr int kMaxXAngles = 16;
+// Up to kMaxXAngles e-field angles for one multi-angle x pass (which takes
+// up to 8) or z-first pass: cos and sin of each, n of them in use.
+constexpr int kMaxXAngles = 32;
 struct XAngles {
   float ce[kMaxXAngles], se[kMaxXAngles];
   int n;
