@@ -2079,7 +2079,13 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
     {
       const C wz = SEL ? make_float2(1.f, 0.f) : twz[z];
       uint4 sb4 = make_uint4(0u, 0u, 0u, 0u);
-      if constexpr (SEL) sb4 = reinterpret_cast<const uint4*>(btab8)[t];
+      float2* sel0 = nullptr;  // SEL: slot 0 of this thread's pixel column, as float2 pairs
+      if constexpr (SEL) {
+        sb4 = reinterpret_cast<const uint4*>(btab8)[t];
+        sel0 = reinterpret_cast<float2*>(
+            part + (size_t)(item >> loghalf) * npix +
+            (Y2K ? (size_t)(col >> 2) * nx + ti * 4 + (col & 3) : (size_t)ti * TX + col));
+      }
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
         const C mine = v[out_pos<16>(k)];
@@ -2087,10 +2093,12 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
         const C y = hw ? csub(other, mine) : cadd(mine, other);  // X[k2 + 32 (16 hw + k)]
         const int row = q + 512 * hw + 32 * k;
         if constexpr (SEL) {
+          // each pixel's bins come from one plane each: stored as they pass
           const unsigned wd = k < 4 ? sb4.x : k < 8 ? sb4.y : k < 12 ? sb4.z : sb4.w;
           const int sb = (int)((wd >> (8 * (k & 3))) & 0xffu);
-          if (sb == z) acc0[k] = y;
-          if (sb + 1 == z) acc1[k] = y;
+          float2* d = sel0 + 2 * (size_t)row * (Y2K ? 2 * nx : nx);
+          if (sb == z) d[0] = y;
+          if (sb + 1 == z) d[1] = y;
         } else {
           const int b0 = btab[row * TX + col];
           const C qq = cmul(y, twz[(b0 * z) & (nz - 1)]);
@@ -2098,7 +2106,7 @@ __global__ void __launch_bounds__(512, 1) k_yz_tma(const __grid_constant__ CUten
           acc1[k] = cadd(acc1[k], cmul(qq, wz));
         }
       }
-      if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
+      if (!SEL && (z == nz - 1 || st == s1 - 1)) {  // segment end: slot 0 if it began at z = 0
         // slot: this segment's place among the item's segments (0 if it
         // began at z = 0); L >= nz / 3 keeps it below kYzSlots
         const int item_start = st - z;
@@ -2248,20 +2256,25 @@ __global__ void __launch_bounds__(512, 1) k_yz512_tma(const __grid_constant__ CU
       }
       dft_reg<16>(v);
       const C wz = SEL ? make_float2(1.f, 0.f) : twz[z];
+      float2* sel0 = nullptr;  // SEL: slot 0 of this thread's pixel column, as float2 pairs
+      if constexpr (SEL)
+        sel0 = reinterpret_cast<float2*>(part + (size_t)(item / ntiles) * npix + (size_t)ti * TX + col);
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) {
         const int row = k2 + 32 * k1;
         const int b0 = btab[row * TX + col];
         if constexpr (SEL) {
-          if (b0 == z) acc0[k1] = v[out_pos<16>(k1)];
-          if (b0 + 1 == z) acc1[k1] = v[out_pos<16>(k1)];
+          // each pixel's bins come from one plane each: stored as they pass
+          float2* d = sel0 + 2 * (size_t)row * nx;
+          if (b0 == z) d[0] = v[out_pos<16>(k1)];
+          if (b0 + 1 == z) d[1] = v[out_pos<16>(k1)];
         } else {
           const C qq = cmul(v[out_pos<16>(k1)], twz[(b0 * z) & (nz - 1)]);
           acc0[k1] = cadd(acc0[k1], qq);
           acc1[k1] = cadd(acc1[k1], cmul(qq, wz));
         }
       }
-      if (z == nz - 1 || st == s1 - 1) {  // segment end: slot 0 if it began at z = 0
+      if (!SEL && (z == nz - 1 || st == s1 - 1)) {  // segment end: slot 0 if it began at z = 0
         // slot: this segment's place among the item's segments (0 if it
         // began at z = 0); L >= nz / 3 keeps it below kYzSlots
         const int item_start = st - z;
@@ -3163,7 +3176,8 @@ cudaError_t launch_yz512_tma(const void* tmap, int nx, int nz, int nf, const Geo
   const long long L0 = (T + n_sm - 1) / n_sm, Lmin = (nz + kYzSlots - 2) / (kYzSlots - 1);
   const long long L = L0 > Lmin ? L0 : Lmin;
   const long long grid = (T + L - 1) / L;
-  *L_out = L;
+  // SEL: every bin is stored once, in slot 0 (k_ewald_bins adds no other slot)
+  *L_out = is_sel ? T : L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 512 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;
   auto kern = is_sel ? k_yz512_tma<true> : k_yz512_tma<false>;
@@ -3196,7 +3210,8 @@ cudaError_t launch_yz_tma(const void* tmap, int nx, int ny, int nz, int nf, cons
   const long long L0 = (T + P0 - 1) / P0, Lmin = (nz + kYzSlots - 2) / (kYzSlots - 1);
   const long long L = L0 > Lmin ? L0 : Lmin;
   const long long groups = (T + L - 1) / L;
-  *L_out = L;
+  // SEL: every bin is stored once, in slot 0 (k_ewald_bins adds no other slot)
+  *L_out = is_sel ? T : L;
   const size_t smem = (2 * 8192 + 32 * 33 * 8 + 1024 + (size_t)nz) * sizeof(float2) +
                       8192 * sizeof(unsigned short) + 2 * 8;
   auto kern = y2k ? (is_sel ? k_yz_tma<true, true> : k_yz_tma<true, false>)
