@@ -964,21 +964,26 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
 // angle k at out + k * kstride + f * fstride + s * nx * ny (+ y nx + x).
 //
 // Row buffers hold a field as XW lines of LS complex; sample z of line px
-// sits at px * LS + zf_pos(z >> 5, z & 31).  A transform warp takes one
-// field of one buffer, decimation in frequency with nz = 32 R,
-// n = n2 + 32 n1, k = R k2 + k1 (n2, k2 < 32; n1, k1 < R):
+// sits at px * LS + zf_pos(z >> 5, z & 31).  The z transform is a
+// decimation in frequency with nz = 32 R, n = n2 + 32 n1, k = R k2 + k1
+// (n2, k2 < 32; n1, k1 < R):
 //   X[R k2 + k1] = sum_n2 W32^(n2 k2) W_nz^(n2 k1) sum_n1 x[n2 + 32 n1] W_R^(n1 k1);
-//   stage 1: lane (px, r) takes n2 = r + R m: the R-point DFT over n1 of
-//            x[n2 + 32 n1] gives u[k1][n2], stored in place at zf_pos(k1, n2)
-//            (the R positions a lane reads are the R it writes);
-//   stage 2: lane (px, k1) loads u[k1][0..32) times W_nz^(n2 k1) (each
-//            twiddle used as it is read), does the 32-point DFT and stores
-//            X[R k2 + k1] over the same 32 positions, zf_pos(k1, k2);
+//   stage 1, in the polarisation warps: a thread's four voxels of one
+//            pixel (e = pt + 256 sl) sit at z = z0 + (256 / XW) sl, so
+//            for R = 4 they are the four n1 of n2 = z0 and for R = 2 the
+//            two n1 of n2 = z0 (sl = 0, 2) and of n2 = z0 + 16 (sl = 1, 3):
+//            the R-point DFT over n1 runs on each angle's p in registers,
+//            and u[k1][n2] is stored where x[n2 + 32 k1] would sit,
+//            zf_pos(k1, n2), so the buffer holds stage 1's output;
+//   stage 2: transform-warp lane (px, k1) loads u[k1][0..32) times
+//            W_nz^(n2 k1) (each twiddle used as it is read), does the
+//            32-point DFT and stores X[R k2 + k1] over the same 32
+//            positions, zf_pos(k1, k2);
 // then the warp copies the ns kept bins of its XW lines out (XW adjacent
 // pixels per plane row).  zf_pos(a, b) = 32 a + b, for R = 4 with b xor a
 // (the low bits swizzled by a); with LS = 130 (R = 4) or nz + 1 that keeps
-// the polarisation stores, both stages and the copy free of shared-memory
-// bank conflicts (checked per half-warp for R = 1, 2, 4).
+// the polarisation stores, stage 2 and the copy free of shared-memory bank
+// conflicts (checked per half-warp for R = 1, 2, 4).
 template <int R> struct ZfLayout {
   static constexpr int NZ = 32 * R, XW = 32 / R, LXW = R == 1 ? 5 : R == 2 ? 4 : 3;
   static constexpr int LS = R == 4 ? 130 : NZ + 1, FS = XW * LS;
@@ -987,6 +992,8 @@ template <int R> __device__ __forceinline__ int zf_pos(int a, int b) {
   return 32 * a + (R == 4 ? (b ^ a) : b);
 }
 
+// Stage 2 of the z transform of one field of a row buffer (stage 1 done by
+// the polarisation warps as they store p).
 template <int R>
 __device__ __forceinline__ void zfft_lines(float2* F, const float2* twt, int lane) {
   using C = float2;
@@ -995,26 +1002,8 @@ __device__ __forceinline__ void zfft_lines(float2* F, const float2* twt, int lan
   const int px = lane & (XW - 1), r = lane >> Lay::LXW;  // r < R
   C* Ln = F + px * LS;
   // zf_pos(a, b) for b = 4 j + c is base[c] + 4 j with base[c] = 32 a +
-  // (c xor a): four base addresses per lane and immediate offsets
-  if constexpr (R > 1) {
-    C* b1[R];  // stage 1: a = n1, c = r (n2 = r + R m)
-#pragma unroll
-    for (int n1 = 0; n1 < R; ++n1) b1[n1] = Ln + zf_pos<R>(n1, r);
-#pragma unroll
-    for (int m = 0; m < 32 / R; ++m) {
-      C u[R];
-#pragma unroll
-      for (int n1 = 0; n1 < R; ++n1) u[n1] = b1[n1][R * m];
-      if constexpr (R == 4)
-        dft4(u[0], u[1], u[2], u[3]);
-      else
-        dft2(u[0], u[1]);
-#pragma unroll
-      for (int k1 = 0; k1 < R; ++k1) b1[k1][R * m] = u[k1];
-    }
-    __syncwarp();
-  }
-  // stage 2: a = k1 = r, b = n2 (or k2)
+  // (c xor a): R base addresses per lane and immediate offsets
+  // (a = k1 = r, b = n2 or k2)
   C* b2[R];
 #pragma unroll
   for (int c = 0; c < R; ++c) b2[c] = Ln + zf_pos<R>(r, c);
@@ -1065,7 +1054,7 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
   constexpr int SV = 1024, TP = 32 * PW, SL = SV / TP, NB = TP + 96;
   static_assert(KMAX <= kMaxXAngles && SV % TP == 0 && 1 + 2 * NPB <= 16 && NPB % FG == 0,
                 "layout");
-  static_assert(PW == 8 && FG == 3, "role table");
+  static_assert(PW == 8 && FG == 3 && SL == 4, "role table, stage-1 voxel groups");
   constexpr unsigned kPoll = 1u << 22, kStageBytes = SV * sizeof(float4);
   extern __shared__ __align__(128) unsigned char smem_a128[];
   float4* stage = reinterpret_cast<float4*>(smem_a128);  // [S][NZ][XW] voxels
@@ -1172,15 +1161,28 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
         if (!failed) {
           C* Pi = P + i * 3 * FS;
           const float ce = ang_ce[k], se = ang_se[k];
+          C o[SL][3];
+#pragma unroll
+          for (int sl = 0; sl < SL; ++sl)
+            p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, o[sl]);
+          // stage 1 of the z transform: sl = g + (4 / R) n1 holds n1 of one n2
+#pragma unroll
+          for (int f = 0; f < 3; ++f) {
+            if constexpr (R == 4) {
+              dft4(o[0][f], o[1][f], o[2][f], o[3][f]);
+            } else if constexpr (R == 2) {
+              dft2(o[0][f], o[2][f]);
+              dft2(o[1][f], o[3][f]);
+            }
+          }
 #pragma unroll
           for (int sl = 0; sl < SL; ++sl) {
-            const int e = pt + sl * TP, z = e >> LXW;  // voxel (z, px) of the tile
+            // voxel (z, px) of the tile; after stage 1 its slot holds k1 = n1
+            const int e = pt + sl * TP, z = e >> LXW;
             const int at = (e & (XW - 1)) * LS + zf_pos<R>(z >> 5, z & 31);
-            C o3[3];
-            p_from_tacc(acc[sl].aw, acc[sl].as[1], acc[sl].t, ce, se, pp.literal != 0, o3);
-            Pi[at] = o3[0];
-            Pi[FS + at] = o3[1];
-            Pi[2 * FS + at] = o3[2];
+            Pi[at] = o[sl][0];
+            Pi[FS + at] = o[sl][1];
+            Pi[2 * FS + at] = o[sl][2];
           }
         }
         named_bar_arrive(1 + i, NB);
