@@ -40,6 +40,11 @@ __device__ __forceinline__ void cp_async_elem(double2* dst, const double2* src) 
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
+// Two adjacent complex floats (16 bytes, both addresses 16-byte aligned).
+__device__ __forceinline__ void cp_async_pair(float2* dst, const float2* src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // Wait until at most N of this thread's committed groups are still in flight.
 template <int N> __device__ __forceinline__ void cp_async_wait() {

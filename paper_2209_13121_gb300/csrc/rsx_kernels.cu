@@ -1217,7 +1217,8 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_zfft_multi(
 
 // x-FFT of contiguous rows of NX complex in place (the kept q_z planes of
 // the z-first path): one warp per row, the row staged in shared memory in
-// the layout xfft_row<NX> takes (2048 points: halves at 0 and 1056), then
+// the layout xfft_row<NX> takes (2048 points: halves at 0 and 1056; every
+// copy 16-byte aligned: rows of 8 NX bytes, FS and NTW even), then
 // xfft_row's four-step transform writes it back.  tw_g: the table xfft_row
 // uses (1024: W1024^(n1 k2) as [32][32]; 2048: that, then W2048^n, n < 1024;
 // 512: W512^j).
@@ -1230,17 +1231,23 @@ __global__ void __launch_bounds__(32 * W) k_xfft_rows(float2* __restrict__ data,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* tw = reinterpret_cast<C*>(smem_raw);
   C* F = tw + NTW + (threadIdx.x >> 5) * FS;
-  for (int i = threadIdx.x; i < NTW; i += 32 * W) tw[i] = tw_g[i];
-  __syncthreads();
   const int lane = threadIdx.x & 31;
   const long long row = (long long)blockIdx.x * W + (threadIdx.x >> 5);
-  if (row >= nrows) return;
   C* r = data + (size_t)row * NX;
-#pragma unroll 16
-  for (int j = 0; j < NX / 32; ++j) {
-    const int n = lane + 32 * j;
-    F[NX == 2048 && n >= 1024 ? n + 32 : n] = r[n];
+  // the row goes to shared memory by asynchronous 16-byte copies (a lane
+  // keeps all NX / 64 of its copies in flight, no registers held), issued
+  // before the twiddle table's loads so that the two overlap
+  if (row < nrows) {
+#pragma unroll
+    for (int j = 0; j < NX / 64; ++j) {
+      const int n = 2 * (lane + 32 * j);
+      cp_async_pair(F + (NX == 2048 && n >= 1024 ? n + 32 : n), r + n);
+    }
   }
+  for (int i = threadIdx.x; i < NTW; i += 32 * W) tw[i] = tw_g[i];
+  __syncthreads();
+  if (row >= nrows) return;
+  cp_async_wait_all();
   __syncwarp();
   xfft_row<NX>(F, tw, r, lane, [] {});
 }
@@ -3140,7 +3147,7 @@ static cudaError_t xfft_rows_impl(void* data, long long nrows, const void* tw, c
 
 cudaError_t launch_xfft_rows(void* data, int nx, long long nrows, const void* tw, cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
-  if (!tw || ((uintptr_t)data & 7)) return cudaErrorInvalidValue;
+  if (!tw || ((uintptr_t)data & 15)) return cudaErrorInvalidValue;  // 16-byte row copies
   // 8 warps (2 blocks per SM) for 512- and 1024-point rows; 2048-point rows
   // stage 17 KB per warp: 4 warps (2 blocks per SM)
   if (nx == 1024) return xfft_rows_impl<1024, 8>(data, nrows, tw, s);
