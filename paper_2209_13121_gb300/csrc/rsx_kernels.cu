@@ -954,7 +954,8 @@ __global__ void __launch_bounds__(32 * (PW + 3 * FG + 1), 1) k_pol_fft4s_tma_mul
 // kb, kb + 1, ..., kb + ns - 1 (mod nz) that ends at bin 1.  The 3-D DFT is
 // separable, so its z transform may come first; the nz - ns bins no pixel
 // reads are then dropped before the x and y transforms, which run on ns
-// planes instead of nz slices (P1 geometry: ns ~ 37 of 128).
+// planes instead of nz slices (P1 geometry, 5 nm voxels: ns = 36 of 128 at
+// 270 eV, 30 at 320 eV).
 //
 // This pass forms p as k_pol_fft4s_tma_multi does (same roles, ring and
 // arithmetic: the morphology sums once per voxel, then each angle's p) but
@@ -1020,10 +1021,11 @@ __device__ __forceinline__ void zfft_lines(float2* F, const float2* twt, int lan
   __syncwarp();
 }
 
-// Roles of the 18 warps of the z-first pass for nz = 128.  A transform warp
-// there does ~1.2x the per-tile work of a polarisation warp; over the four
-// schedulers (warp index mod 4) the split Prod T T T P | P P P P P | T T T P
-// | T T T P keeps every scheduler within ~7 % of the mean, and each
+// Roles of the 18 warps of the z-first pass for nz = 128.  The split was
+// set when a transform warp also ran the z transform's first radix stage
+// (~1.2x the per-tile work of a polarisation warp): over the four
+// schedulers (warp index mod 4) Prod T T T P | P P P P P | T T T P
+// | T T T P kept every scheduler within ~7 % of the mean, and each
 // transform group (three consecutive indices) spans three schedulers: warps
 // 0, 2, 3, 4, 6, 7, 8, 10, 11 transform (0..8), 16 produces, 1, 5, 9, 13,
 // 17, 12, 14, 15 polarise (0..7).  (P1: x pass 72.8 -> 72.2 ms per energy;
