@@ -713,7 +713,7 @@ def test_full_size_run_sampled_pixels_match_oracle(rsx):
     1024 x 128, c = 4, FP32, device output: the z-first path with its
     default batch (polarisation + z-FFT, x-FFT of the kept planes, the
     y-FFT selecting each pixel's bins), the Ewald image, the rotation into
-    the average), ten angles (a full batch and a partial one), against the
+    the average), ten angles (one pass of the z-first kernels), against the
     oracle's average at sampled output pixels (each angle's unrotated image
     at the corners the rotation reads, exact by linearity of the DFT)."""
     if torch.cuda.get_device_properties(0).total_memory < 100e9:
