@@ -142,6 +142,16 @@ int rsx_angle_batch(const rsx_context* ctx);
 int rsx_zfirst_plan(const rsx_context* ctx, int energy_index, int* n_planes, int* first_bin,
                     int* angles_per_pass);
 
+/* The same plan from a configuration and a photon energy in eV alone: the
+ * run a context created from cfg would use for that energy (with the angle
+ * batch cfg resolves to, see rsx_angle_batch, and a 16-byte aligned
+ * morphology).  Host arithmetic only: needs no GPU and allocates nothing.
+ * Outputs as for rsx_zfirst_plan (all 0 where the path does not serve cfg
+ * or the energy).  Errors: RSX_ERR_INVALID (cfg as for rsx_create, energy
+ * not finite or <= 0). */
+int rsx_zfirst_plan_for(const rsx_config* cfg, double energy_ev, int* n_planes, int* first_bin,
+                        int* angles_per_pass);
+
 /* Number of e-field angles in the inclusive list start:increment:end
  * (degrees, Algorithm 1 "E_Angle [start, increment, end]"); 1 when rotation
  * is 0.  Returns -1 for increment <= 0, end < start or non-finite input. */

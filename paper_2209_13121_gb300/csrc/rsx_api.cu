@@ -728,14 +728,11 @@ static int lowest_bin(const rsx_config& g, double k) {
   return (int)lo;
 }
 
-static bool zfirst_plan(const rsx_context* c, int ie, ZPlan* zp) {
-  const rsx_config& g = c->cfg;
-  if (!zfirst_ok(&g) || c->n_sm <= 0 || !c->part || !c->b0idx || ie < 0 ||
-      ie >= (int)c->energies.size() || (c->M && ((uintptr_t)c->M & 15)))
-    return false;
-  if ((g.nx == 1024 && !c->tw4) || (g.nx == 2048 && !c->tw2k) || (g.ny == 2048 && !c->twy))
-    return false;
-  const int blo = lowest_bin(g, wavenumber(c->energies[ie]));
+// The plan from the shape, the angle batch kx (p buffers of 3 nz planes
+// each) and the wavenumber k alone (host arithmetic, no device state).
+static bool zfirst_plan_of(const rsx_config& g, int kx, double k, ZPlan* zp) {
+  if (!zfirst_ok(&g)) return false;
+  const int blo = lowest_bin(g, k);
   const int ns = 2 - blo;
   // worth it while at most 3/4 of the bins are kept (the z transform costs
   // about what the dropped planes' x and y transforms save at ~0.8)
@@ -743,9 +740,19 @@ static bool zfirst_plan(const rsx_context* c, int ie, ZPlan* zp) {
   zp->ns = ns;
   zp->kb = ((blo % g.nz) + g.nz) % g.nz;
   // the kept planes of kz angles fit in the kx p buffers of 3 nz planes each
-  const int kz = (int)((long long)c->kx * g.nz / ns);
+  const int kz = (int)((long long)kx * g.nz / ns);
   zp->kz = kz < rsx::kMaxXAngles ? kz : rsx::kMaxXAngles;
   return zp->kz >= 1;
+}
+
+static bool zfirst_plan(const rsx_context* c, int ie, ZPlan* zp) {
+  const rsx_config& g = c->cfg;
+  if (!zfirst_ok(&g) || c->n_sm <= 0 || !c->part || !c->b0idx || ie < 0 ||
+      ie >= (int)c->energies.size() || (c->M && ((uintptr_t)c->M & 15)))
+    return false;
+  if ((g.nx == 1024 && !c->tw4) || (g.nx == 2048 && !c->tw2k) || (g.ny == 2048 && !c->twy))
+    return false;
+  return zfirst_plan_of(g, c->kx, wavenumber(c->energies[ie]), zp);
 }
 
 size_t rsx_workspace_bytes(const rsx_config* cfg) {
@@ -779,6 +786,20 @@ int rsx_zfirst_plan(const rsx_context* c, int ie, int* n_planes, int* first_bin,
     return fail(RSX_ERR_INVALID, "energy index %d out of range [0, %zu)", ie, c->energies.size());
   ZPlan zp;
   if (!zfirst_plan(c, ie, &zp)) zp = ZPlan();
+  if (n_planes) *n_planes = zp.ns;
+  if (first_bin) *first_bin = zp.kb;
+  if (angles_per_pass) *angles_per_pass = zp.kz;
+  return RSX_OK;
+}
+
+int rsx_zfirst_plan_for(const rsx_config* cfg, double energy_ev, int* n_planes, int* first_bin,
+                        int* angles_per_pass) {
+  const int rc = check_config(cfg);
+  if (rc) return rc;
+  if (!isfinite(energy_ev) || !(energy_ev > 0.0))
+    return fail(RSX_ERR_INVALID, "energy must be finite and > 0 (got %g eV)", energy_ev);
+  ZPlan zp;
+  if (!zfirst_plan_of(*cfg, angle_batch_of(cfg), wavenumber(energy_ev), &zp)) zp = ZPlan();
   if (n_planes) *n_planes = zp.ns;
   if (first_bin) *first_bin = zp.kb;
   if (angles_per_pass) *angles_per_pass = zp.kz;

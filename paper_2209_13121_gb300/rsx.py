@@ -33,6 +33,7 @@ EXPORTED = (
     "rsx_fft3d", "rsx_ewald", "rsx_rotate_accumulate", "rsx_scatter_angle",
     "rsx_set_timing", "rsx_phase_times", "rsx_scatter_angle_noalloc", "rsx_nt",
     "rsx_set_wait_limit", "rsx_check", "rsx_angle_batch", "rsx_zfirst_plan",
+    "rsx_zfirst_plan_for",
 )
 MAX_ANGLE_BATCH = 8
 NOALLOC_MAX_VOXELS = 1 << 20
@@ -88,6 +89,7 @@ def load_library(path: str | None = None) -> ctypes.CDLL:
         "rsx_check": (ci, [vp, vp]),
         "rsx_angle_batch": (ci, [vp]),
         "rsx_zfirst_plan": (ci, [vp, ci, vp, vp, vp]),
+        "rsx_zfirst_plan_for": (ci, [ctypes.POINTER(RsxConfig), cd, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -154,6 +156,16 @@ def make_config(nx, ny, nz, n_components, voxel_nm, precision=32, algorithm=1,
 
 def workspace_bytes(cfg: RsxConfig) -> int:
     return lib().rsx_workspace_bytes(ctypes.byref(cfg))
+
+
+def zfirst_plan_for(cfg: RsxConfig, energy_ev) -> tuple:
+    """rsx_zfirst_plan_for: (n_planes, first_bin, angles_per_pass) of the
+    z-first path for a context of this configuration at this energy (host
+    only, no GPU needed); n_planes = 0 when the path does not serve it."""
+    ns, kb, kz = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().rsx_zfirst_plan_for(ctypes.byref(cfg), float(energy_ev), ctypes.byref(ns),
+                                     ctypes.byref(kb), ctypes.byref(kz)))
+    return ns.value, kb.value, kz.value
 
 
 class Context:
