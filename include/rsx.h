@@ -142,7 +142,8 @@ int rsx_angle_batch(const rsx_context* ctx);
 int rsx_zfirst_plan(const rsx_context* ctx, int energy_index, int* n_planes, int* first_bin,
                     int* angles_per_pass);
 
-/* The same plan from a configuration and a photon energy in eV alone: the
+/* The same plan (the q_z bins of Eq. (Ewald) that Algorithm 1's detector
+ * pixels read) from a configuration and a photon energy in eV alone: the
  * run a context created from cfg would use for that energy (with the angle
  * batch cfg resolves to, see rsx_angle_batch, and a 16-byte aligned
  * morphology).  Host arithmetic only: needs no GPU and allocates nothing.
