@@ -46,3 +46,15 @@ def test_reference_arm_prints_its_line():
     assert out["unit"] == "Gvoxel-angle/s" and out["higher_is_better"] is True
     assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["cores"] >= 1
     assert out["e2e"]["h2d_bytes_per_step"] == 0 and out["e2e"]["value"] == out["value"]
+
+
+def test_roofline_traffic_comes_from_the_committed_profiles():
+    """The DRAM bytes per launch that the benchmark line reports beside its
+    roofline are the ncu figures recorded in profiles/traffic.txt: the
+    z-first polarisation + z-FFT launch at 1024 x 1024 x 128 (its dominant
+    kernel), and nothing for a kernel whose capture is no longer current."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench._traffic_from_profiles("p1-1024", "zfirst-pol_fftx", 32) == 29215200000.0
+    assert bench._traffic_from_profiles("p1-1024", "zfirst-fftx", 32) is None
+    assert bench._traffic_from_profiles("p1-1024", "zfirst-pol_fftx", 64) is None
