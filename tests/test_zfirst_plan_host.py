@@ -1,5 +1,6 @@
 """The z-first path's plan (rsx_zfirst_plan_for, host arithmetic only, no
-GPU): for every shape the path serves and energies from well below to well
+GPU): for every shape the path serves, voxel sizes of 2, 5 and 10 nm and
+energies from well below to well
 above the carbon edge, the run of q_z planes it keeps holds both bins
 (b0 = floor(t) and b0 + 1 of Eq. (Ewald)) of every detector pixel on the
 sphere as the oracle's geometry computes them, ends at bin 1, keeps no more
@@ -24,17 +25,17 @@ def rsx():
     return R
 
 
-def _bins_read(shape, E):
+def _bins_read(shape, E, dv=VOXEL):
     """The q_z bins b0 and b0 + 1 (mod nz) that the pixels on the Ewald
     sphere read, from the oracle's q grid and Eq. (Ewald), and the lowest
     b0 (unreduced)."""
     nz, ny, nx = shape
     k = O.wavenumber(E)
-    qx = O.q_axis(nx, VOXEL)[None, :]
-    qy = O.q_axis(ny, VOXEL)[:, None]
+    qx = O.q_axis(nx, dv)[None, :]
+    qy = O.q_axis(ny, dv)[:, None]
     rad = k * k - qx * qx - qy * qy
     on = rad >= 0.0
-    t = (-k + np.sqrt(np.where(on, rad, 0.0))) / (2.0 * math.pi / (nz * VOXEL))
+    t = (-k + np.sqrt(np.where(on, rad, 0.0))) / (2.0 * math.pi / (nz * dv))
     z0 = np.floor(t[on]).astype(np.int64)
     return set(np.mod(z0, nz).tolist()) | set(np.mod(z0 + 1, nz).tolist()), int(z0.min())
 
@@ -46,14 +47,15 @@ ENERGIES = [150.0, 170.0, 200.0, 250.0, 270.0, 285.0, 300.0, 320.0, 400.0, 700.0
 
 @pytest.mark.parametrize("shape", SHAPES, ids=["x".join(map(str, s)) for s in SHAPES])
 @pytest.mark.parametrize("batch", [0, 1, 3])
-def test_plan_covers_every_bin_read(rsx, shape, batch):
+@pytest.mark.parametrize("dv", [VOXEL, 2.0, 10.0])
+def test_plan_covers_every_bin_read(rsx, shape, batch, dv):
     nz, ny, nx = shape
-    cfg = rsx.make_config(nx, ny, nz, 4, VOXEL, angle_batch=batch)
+    cfg = rsx.make_config(nx, ny, nz, 4, dv, angle_batch=batch)
     kx = batch if batch else min(8, max(1, int((32 << 30) / (3.0 * nx * ny * nz * 8))))
     served = 0
     for E in ENERGIES:
         ns, kb, kz = rsx.zfirst_plan_for(cfg, E)
-        need, lowest = _bins_read(shape, E)
+        need, lowest = _bins_read(shape, E, dv)
         want_ns = 2 - lowest   # bins lowest .. 1 (one more below near a bin edge)
         if ns == 0:   # most bins read: the path steps aside
             assert kz == 0 and kb == 0 and 4 * (want_ns + 1) > 3 * nz, (E, want_ns)
@@ -64,7 +66,7 @@ def test_plan_covers_every_bin_read(rsx, shape, batch):
         assert need <= run, (E, sorted(need - run))
         assert (kb + ns - 1) % nz == 1   # the run ends at bin 1
         assert kz == min(32, kx * nz // ns) and kz * ns <= kx * nz
-    assert served >= 5
+    assert served >= (5 if dv == VOXEL else 1)
 
 
 def test_benchmark_plan(rsx):
