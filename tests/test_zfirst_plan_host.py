@@ -1,12 +1,11 @@
 """The z-first path's plan (rsx_zfirst_plan_for, host arithmetic only, no
 GPU): for every shape the path serves, voxel sizes of 2, 5 and 10 nm and
 energies from well below to well above the carbon edge, the run of q_z
-planes it keeps holds both bins
-(b0 = floor(t) and b0 + 1 of Eq. (Ewald)) of every detector pixel on the
-sphere as the oracle's geometry computes them, ends at bin 1, keeps no more
-than one bin beyond the lowest one read, and fits the angle batch; shapes,
-precisions and algorithms the path does not serve get no plan, and bad
-arguments are refused."""
+planes it keeps holds both bins (b0 = floor(t) and b0 + 1 of Eq. (Ewald))
+of every detector pixel on the sphere as the oracle's geometry computes
+them, ends at bin 1, keeps no more than one bin beyond the lowest one read,
+and fits the angle batch; shapes, precisions and algorithms the path does
+not serve get no plan, and bad arguments are refused."""
 import math
 
 import numpy as np
